@@ -1,0 +1,365 @@
+"""Seeded synthetic problems and acquisitions (input generator).
+
+This module builds the inputs that both the CUDA library and the oracle
+consume: the geometry of a curvilinear array with a lens, the image patches,
+the slowness grid, the hyperparameters of the paper's Table II, and demodulated
+full-synthetic-aperture channel data simulated from point scatterers in a
+layered medium.  It holds none of the autofocusing method's arithmetic.
+
+Every geometric quantity is rounded to the nearest float32 value (and kept as
+float64), so that a float32 device copy and the float64 oracle see exactly the
+same positions.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libsynth.so")
+_lib = None
+
+C_REF = 1540.0  # beamforming reference speed (m/s); lambda/2 pixel spacing uses it
+
+
+def build(force: bool = False) -> str:
+    """Compile synth.c into libsynth.so (OpenMP, portable x86-64 code)."""
+    src = os.path.join(_HERE, "synth.c")
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
+        subprocess.check_call(["gcc", "-O3", "-fopenmp", "-shared", "-fPIC", "-o", _LIB_PATH, src, "-lm"])
+    return _LIB_PATH
+
+
+class _Medium(ctypes.Structure):
+    _fields_ = [("n_if", ctypes.c_int),
+                ("base", ctypes.c_double * 8), ("amp", ctypes.c_double * 8),
+                ("period", ctypes.c_double * 8), ("phase", ctypes.c_double * 8),
+                ("slow", ctypes.c_double * 9)]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        dp = ctypes.POINTER(ctypes.c_double)
+        lib.sy_oneway_times.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                        ctypes.POINTER(_Medium), ctypes.c_int, dp, dp, dp]
+        lib.sy_echoes.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                  ctypes.POINTER(ctypes.c_float)]
+        lib.sy_segment_time.argtypes = [ctypes.POINTER(_Medium), ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double]
+        lib.sy_segment_time.restype = ctypes.c_double
+        lib.sy_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def f32(x):
+    """Round to the nearest float32 value, returned as float64."""
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+@dataclasses.dataclass
+class Medium:
+    """True layered medium: interface i at z = base + amp sin(2 pi x / period + phase)."""
+    speeds: list
+    base: list = dataclasses.field(default_factory=list)
+    amp: list = dataclasses.field(default_factory=list)
+    period: list = dataclasses.field(default_factory=list)
+    phase: list = dataclasses.field(default_factory=list)
+    cysts: list = dataclasses.field(default_factory=list)   # (x, z, radius): no scatterers inside
+
+    def to_c(self) -> _Medium:
+        m = _Medium()
+        m.n_if = len(self.base)
+        for i in range(m.n_if):
+            m.base[i] = self.base[i]
+            m.amp[i] = self.amp[i]
+            m.period[i] = self.period[i] if self.period[i] else 1.0
+            m.phase[i] = self.phase[i]
+        for i, c in enumerate(self.speeds):
+            m.slow[i] = 1.0 / c
+        return m
+
+    def speed_at(self, x, z):
+        x = np.asarray(x, np.float64)
+        z = np.asarray(z, np.float64)
+        layer = np.zeros(np.broadcast(x, z).shape, np.int64)
+        for i in range(len(self.base)):
+            zi = self.base[i] + self.amp[i] * np.sin(2 * np.pi * x / (self.period[i] or 1.0) + self.phase[i])
+            layer = np.where(z > zi, i + 1, layer)
+        return np.asarray(self.speeds, np.float64)[layer]
+
+
+@dataclasses.dataclass
+class Problem:
+    """Everything an autofocus run needs besides the channel data and the slowness map."""
+    name: str
+    # array and lens (Sec. II-A, II-B, III-B; Table I)
+    elem_x: np.ndarray
+    elem_z: np.ndarray
+    arc_cx: float
+    arc_cz: float
+    arc_radius: float
+    d_lens: float
+    c_lens: float
+    t_ttp: float
+    lens_mode: int            # 0 bent-ray, 1 no lens
+    # apodization (Eq. 4)
+    fnum: float
+    apod_mode: int            # 0 |x'| <= z'/(2F), 1 printed (F/2) z'
+    # image patches (patch-major pixels)
+    n_patch: int
+    patch_npix: int
+    pix_x: np.ndarray
+    pix_z: np.ndarray
+    # slowness grid (Sec. III-A)
+    nx: int
+    nz: int
+    x0: float
+    z0: float
+    dx: float
+    dz: float
+    nseg: int
+    # channel data
+    ns: int
+    fs: float
+    fd: float
+    fc: float
+    t0: float
+    sub_width: int
+    # Table II
+    rho_thresh: float
+    w1: float
+    kx1: float
+    kz1: float
+    w2: float
+    kx2: float
+    kz2: float
+    lr: float
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+    c_ref: float = C_REF
+    medium: Optional[Medium] = None
+    sector_half_angle: float = 0.0
+    depth_range: tuple = (0.0, 0.0)
+
+    @property
+    def ne(self) -> int:
+        return int(self.elem_x.shape[0])
+
+    @property
+    def npix(self) -> int:
+        return int(self.n_patch * self.patch_npix)
+
+    @property
+    def nsub(self) -> int:
+        return self.ne // self.sub_width
+
+    @property
+    def lens_radius(self) -> float:
+        return float(f32(self.arc_radius + self.d_lens))
+
+    def initial_slowness(self, c: float = C_REF) -> np.ndarray:
+        """Uniform slowness grid [nz][nx] (float32) at speed c."""
+        return np.full((self.nz, self.nx), 1.0 / c, dtype=np.float32)
+
+    def true_speed_grid(self) -> np.ndarray:
+        gx = self.x0 + self.dx * np.arange(self.nx)
+        gz = self.z0 + self.dz * np.arange(self.nz)
+        X, Z = np.meshgrid(gx, gz)
+        return self.medium.speed_at(X, Z)
+
+
+# Table II (phantom C5-2v and in vivo C5-2v columns)
+TABLE2 = {
+    "phantom_c5": dict(lr=0.0030, w1=10.0, kx1=0.0100, kz1=0.0100, w2=100.0, kx2=0.0010,
+                       kz2=0.0010, rho_thresh=0.9, fnum=0.5, nseg=32),
+    "invivo_c5": dict(lr=0.0500, w1=100.0, kx1=0.0100, kz1=0.0100, w2=100.0, kx2=0.0020,
+                      kz2=0.0020, rho_thresh=0.9, fnum=0.4, nseg=64),
+}
+
+
+def curvilinear_problem(name: str, *, ne: int, radius: float, pitch: float, fc: float,
+                        d_lens: float, c_lens: float, ns: int, fs: float, nx: int, nz: int,
+                        n_ang: int, n_rad: int, patch_w: int, depth_min: float, depth_max: float,
+                        sub_width: int, hyper: dict, medium: Optional[Medium] = None,
+                        t_ttp: float = 0.0, t0: float = 0.0, lens_mode: int = 0,
+                        apod_mode: int = 0, sector_frac: float = 0.8,
+                        grid_margin: float = 2e-3) -> Problem:
+    """Curvilinear array on an arc of `radius` about (0, -radius) (apex at the origin),
+    a concentric lens shell of thickness d_lens, and a regular polar grid of square
+    patches of patch_w x patch_w pixels at lambda/2 (lambda at 1540 m/s)."""
+    th = (np.arange(ne) - (ne - 1) / 2.0) * pitch / radius
+    ex = f32(radius * np.sin(th))
+    ez = f32(radius * np.cos(th) - radius)
+    cx, cz = 0.0, float(f32(-radius))
+    RL = radius + d_lens
+    half = sector_frac * abs(th[-1]) if ne > 1 else 0.2
+    ang = np.linspace(-half, half, n_ang) if n_ang > 1 else np.zeros(1)
+    rad = RL + (np.linspace(depth_min, depth_max, n_rad) if n_rad > 1 else np.array([depth_min]))
+    step = C_REF / fc / 2.0
+    h = (patch_w - 1) / 2.0
+    px, pz = [], []
+    for r in rad:
+        for a in ang:
+            ur = np.array([np.sin(a), np.cos(a)])       # radial unit vector
+            ut = np.array([np.cos(a), -np.sin(a)])      # tangential unit vector
+            c = np.array([cx, cz]) + r * ur
+            for b in range(patch_w):
+                for k in range(patch_w):
+                    q = c + (k - h) * step * ut + (b - h) * step * ur
+                    px.append(q[0])
+                    pz.append(q[1])
+    px = f32(np.array(px))
+    pz = f32(np.array(pz))
+    # grid: bounding box of the lens surface over the aperture and every pixel
+    lens_th = np.linspace(th[0], th[-1], 64) if ne > 1 else np.zeros(1)
+    lx = cx + RL * np.sin(lens_th)
+    lz = cz + RL * np.cos(lens_th)
+    xmin = min(px.min(), lx.min(), ex.min()) - grid_margin
+    xmax = max(px.max(), lx.max(), ex.max()) + grid_margin
+    zmin = min(pz.min(), lz.min(), ez.min()) - grid_margin
+    zmax = max(pz.max(), lz.max()) + grid_margin
+    dx = float(f32((xmax - xmin) / (nx - 1)))
+    dz = float(f32((zmax - zmin) / (nz - 1)))
+    return Problem(
+        name=name, elem_x=ex, elem_z=ez, arc_cx=cx, arc_cz=cz, arc_radius=float(f32(radius)),
+        d_lens=float(f32(d_lens)), c_lens=float(f32(c_lens)), t_ttp=float(f32(t_ttp)),
+        lens_mode=lens_mode, fnum=float(f32(hyper["fnum"])), apod_mode=apod_mode,
+        n_patch=n_ang * n_rad, patch_npix=patch_w * patch_w, pix_x=px, pix_z=pz,
+        nx=nx, nz=nz, x0=float(f32(xmin)), z0=float(f32(zmin)), dx=dx, dz=dz,
+        nseg=int(hyper["nseg"]), ns=ns, fs=float(f32(fs)), fd=float(f32(fc)), fc=fc,
+        t0=float(f32(t0)), sub_width=sub_width, rho_thresh=float(f32(hyper["rho_thresh"])),
+        w1=hyper["w1"], kx1=hyper["kx1"], kz1=hyper["kz1"], w2=hyper["w2"],
+        kx2=hyper["kx2"], kz2=hyper["kz2"], lr=hyper["lr"], medium=medium,
+        sector_half_angle=float(half), depth_range=(depth_min, depth_max))
+
+
+def config_tiny(**over) -> Problem:
+    """32-element, 40 mm-radius, 0.4 mm-pitch, 3 MHz array; 1.0 mm lens at 1000 m/s;
+    32 x 32 x 1024 samples at 12 MHz; 16 x 16 grid; 64 patches of 5 x 5 pixels;
+    two-layer medium (15 mm at 1450 m/s over 1570 m/s)."""
+    kw = dict(ne=32, radius=40e-3, pitch=0.4e-3, fc=3e6, d_lens=1.0e-3, c_lens=1000.0,
+              ns=1024, fs=12e6, nx=16, nz=16, n_ang=8, n_rad=8, patch_w=5,
+              depth_min=8e-3, depth_max=50e-3, sub_width=4, hyper=TABLE2["phantom_c5"],
+              medium=Medium(speeds=[1450.0, 1570.0], base=[15e-3], amp=[0.0], period=[0.0],
+                            phase=[0.0]))
+    kw.update(over)
+    return curvilinear_problem("c32_fsa1024", **kw)
+
+
+def config_full(seed: int = 20261204, **over) -> Problem:
+    """128-element, 60 mm-radius, 0.35 mm-pitch, 3.5 MHz array; 1.2 mm lens at 1000 m/s;
+    128 x 128 x 3072 samples at 14 MHz; 128 x 128 grid; 400 patches of 9 x 9 pixels;
+    skin 3 mm (1600) / fat 10-25 mm (1440) with a 3 mm wavy lower interface / liver
+    (1560) with two 8 mm anechoic cysts."""
+    rng = np.random.default_rng(seed)
+    h_fat = rng.uniform(10e-3, 25e-3)
+    ph = rng.uniform(0, 2 * np.pi)
+    medium = Medium(speeds=[1600.0, 1440.0, 1560.0], base=[3e-3, 3e-3 + h_fat],
+                    amp=[0.0, 3e-3], period=[0.0, 20e-3], phase=[0.0, ph])
+    kw = dict(ne=128, radius=60e-3, pitch=0.35e-3, fc=3.5e6, d_lens=1.2e-3, c_lens=1000.0,
+              ns=3072, fs=14e6, nx=128, nz=128, n_ang=20, n_rad=20, patch_w=9,
+              depth_min=10e-3, depth_max=140e-3, sub_width=8, hyper=TABLE2["invivo_c5"],
+              medium=medium)
+    kw.update(over)
+    p = curvilinear_problem("c128_fsa3072", **kw)
+    # cysts: 8 mm diameter, seeded positions in the liver inside the sector
+    cysts = []
+    for _ in range(2):
+        a = rng.uniform(-0.6, 0.6) * p.sector_half_angle
+        d = rng.uniform(max(40e-3, 3e-3 + h_fat + 10e-3), 120e-3)
+        r = p.lens_radius + d
+        cysts.append((p.arc_cx + r * math.sin(a), p.arc_cz + r * math.cos(a), 4e-3))
+    medium.cysts = cysts
+    return p
+
+
+def pulse_sigma(fc: float, frac_bw: float = 0.7) -> float:
+    """Std of the Gaussian envelope whose -6 dB bandwidth is frac_bw * fc."""
+    sigma_f = frac_bw * fc / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    return 1.0 / (2.0 * math.pi * sigma_f)
+
+
+def sector_scatterers(problem: Problem, n: int, seed: int, depth=(2e-3, None),
+                      half_angle: Optional[float] = None):
+    """n scatterers uniform in area over the imaging sector, N(0,1) amplitudes,
+    none inside the medium's cysts."""
+    rng = np.random.default_rng(seed)
+    RL = problem.lens_radius
+    d0 = depth[0]
+    d1 = depth[1] if depth[1] is not None else problem.depth_range[1] + 10e-3
+    half = half_angle if half_angle is not None else 1.15 * problem.sector_half_angle
+    r = np.sqrt(rng.uniform((RL + d0) ** 2, (RL + d1) ** 2, n))
+    a = rng.uniform(-half, half, n)
+    x = problem.arc_cx + r * np.sin(a)
+    z = problem.arc_cz + r * np.cos(a)
+    amp = rng.standard_normal(n)
+    keep = np.ones(n, bool)
+    if problem.medium is not None:
+        for (cxs, czs, rad) in problem.medium.cysts:
+            keep &= (x - cxs) ** 2 + (z - czs) ** 2 > rad ** 2
+    return x[keep], z[keep], amp[keep]
+
+
+def oneway_times(problem: Problem, kx: np.ndarray, kz: np.ndarray,
+                 medium: Optional[Medium] = None) -> np.ndarray:
+    """True one-way times [ne][nk] element -> scatterer through lens and medium."""
+    lib = _load()
+    med = (medium or problem.medium or Medium(speeds=[C_REF])).to_c()
+    kx = np.ascontiguousarray(kx, np.float64)
+    kz = np.ascontiguousarray(kz, np.float64)
+    ex = np.ascontiguousarray(problem.elem_x, np.float64)
+    ez = np.ascontiguousarray(problem.elem_z, np.float64)
+    T = np.empty((problem.ne, kx.shape[0]), np.float64)
+    lib.sy_oneway_times(problem.ne, _dp(ex), _dp(ez), problem.arc_cx, problem.arc_cz,
+                        problem.lens_radius, problem.c_lens,
+                        1 if problem.lens_mode == 0 else 0, ctypes.byref(med),
+                        kx.shape[0], _dp(kx), _dp(kz), _dp(T))
+    return T
+
+
+def echoes(problem: Problem, T: np.ndarray, amp: np.ndarray, sigma: Optional[float] = None) -> np.ndarray:
+    """Demodulated FSA data Psi[t][r][n] (complex64) for one-way times T[e][k]."""
+    lib = _load()
+    T = np.ascontiguousarray(T, np.float64)
+    amp = np.ascontiguousarray(amp, np.float64)
+    sig = pulse_sigma(problem.fc) if sigma is None else sigma
+    out = np.empty((problem.ne, problem.ne, problem.ns), np.complex64)
+    lib.sy_echoes(problem.ne, T.shape[1], _dp(T), _dp(amp), problem.ns, problem.fs, problem.fd,
+                  problem.t0, problem.t_ttp, sig,
+                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    return out
+
+
+def simulate(problem: Problem, n_scatterers: int, seed: int,
+             medium: Optional[Medium] = None) -> np.ndarray:
+    """Speckle acquisition: n_scatterers random scatterers in the (true) medium."""
+    x, z, a = sector_scatterers(problem, n_scatterers, seed)
+    T = oneway_times(problem, x, z, medium)
+    return echoes(problem, T, a)
+
+
+def segment_time(medium: Medium, ax, az, bx, bz) -> float:
+    lib = _load()
+    m = medium.to_c()
+    return lib.sy_segment_time(ctypes.byref(m), ax, az, bx, bz)
+
+
+def threads() -> int:
+    return _load().sy_threads()

@@ -1,0 +1,471 @@
+"""Pins of the FP64 oracle to the paper and to mathematics (CPU only).
+
+Each test checks the oracle against something other than itself: a closed
+form, an invariant, a brute-force search, finite differences, or a special
+case that reduces to a textbook result.  A plausible slip in the oracle (a
+dropped term, a wrong sign, a transposed operand, a wrong index) fails at
+least one of them.
+"""
+import dataclasses
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def small(**over):
+    kw = dict(n_ang=3, n_rad=3, patch_w=3)
+    kw.update(over)
+    return synth.config_tiny(**kw)
+
+
+# ---------------------------------------------------------------- geometry
+def test_table_values_match_paper():
+    """Table I/II values as printed in the paper drive the configs."""
+    t2 = json.load(open(os.path.join(GOLDEN, "table2_hyperparameters.json")))
+    for col in ("phantom_c5", "invivo_c5"):
+        for k, v in t2[col].items():
+            assert synth.TABLE2[col][k] == pytest.approx(v, rel=0, abs=0), (col, k)
+    t1 = json.load(open(os.path.join(GOLDEN, "table1_lens_calibration.json")))
+    assert t1["C5-2v (Phantoms)"]["c_lens"] == 999.4
+
+
+def test_eq3_orientation_exact_on_uniform_arc(tiny):
+    """Eq. 3 central difference on a uniform arc equals the polar angle exactly."""
+    o = oracle.Oracle(tiny)
+    th = o.element_angles()
+    ref = np.arctan2(tiny.elem_x - tiny.arc_cx, tiny.elem_z - tiny.arc_cz)
+    # element positions are float32-rounded, so agreement is to ~1e-7 rad
+    np.testing.assert_allclose(th, ref, atol=2e-6)
+    # exact arc in float64
+    R = 0.04
+    a = (np.arange(9) - 4) * 0.01
+    ex, ez = R * np.sin(a), R * np.cos(a) - R
+    th2 = np.empty(9)
+    o.lib.or_element_angles(9, oracle._d(ex), oracle._d(ez), oracle._d(th2))
+    np.testing.assert_allclose(th2, a, atol=1e-14)
+
+
+def test_eq4_apodization_cone():
+    """Eq. 2+4: a pixel on the element normal is inside, one beyond the f-number cone is out;
+    the printed form (F/2) z' gives the narrower cone."""
+    p = small()
+    o = oracle.Oracle(p)
+    e = 5
+    th = o.element_angles()[e]
+    n = np.array([math.sin(th), math.cos(th)])
+    t = np.array([math.cos(th), -math.sin(th)])
+    r0 = np.array([p.elem_x[e], p.elem_z[e]])
+    zp = 0.02
+    half = zp / (2 * p.fnum)
+    inside = r0 + zp * n + 0.99 * half * t
+    outside = r0 + zp * n + 1.01 * half * t
+    assert o.apod(e, *inside) == 1
+    assert o.apod(e, *outside) == 0
+    assert o.apod(e, *(r0 - zp * n)) == 0           # behind the element
+    pp = small(apod_mode=1)
+    op = oracle.Oracle(pp)
+    narrow = r0 + zp * n + 1.01 * (0.5 * pp.fnum * zp) * t
+    assert op.apod(e, *narrow) == 0
+    assert op.apod(e, *(r0 + zp * n + 0.99 * (0.5 * pp.fnum * zp) * t)) == 1
+
+
+# ---------------------------------------------------------------- lens (Eq. 8)
+def _brute_exit(p, e, x, z, sbar, n=1_000_001):
+    """Dense search over the lens surface with positions computed directly."""
+    the = math.atan2(p.elem_x[e] - p.arc_cx, p.elem_z[e] - p.arc_cz)
+    thp = math.atan2(x - p.arc_cx, z - p.arc_cz)
+    lo, hi = min(the, thp) - 0.05, max(the, thp) + 0.05
+    phi = np.linspace(lo, hi, n)
+    RL = p.lens_radius
+    qx = p.arc_cx + RL * np.sin(phi)
+    qz = p.arc_cz + RL * np.cos(phi)
+    T = np.hypot(qx - p.elem_x[e], qz - p.elem_z[e]) / p.c_lens + np.hypot(x - qx, z - qz) * sbar
+    k = int(np.argmin(T))
+    # refine on a finer grid around the best sample
+    phi2 = np.linspace(phi[max(k - 1, 0)], phi[min(k + 1, n - 1)], 200_001)
+    qx = p.arc_cx + RL * np.sin(phi2)
+    qz = p.arc_cz + RL * np.cos(phi2)
+    T2 = np.hypot(qx - p.elem_x[e], qz - p.elem_z[e]) / p.c_lens + np.hypot(x - qx, z - qz) * sbar
+    k2 = int(np.argmin(T2))
+    return phi2[k2], T2[k2]
+
+
+def test_exit_point_matches_brute_force_and_snell():
+    p = synth.config_full()
+    o = oracle.Oracle(p)
+    rng = np.random.default_rng(3)
+    sbar = 1.0 / 1480.0
+    for _ in range(12):
+        e = int(rng.integers(p.ne))
+        k = int(rng.integers(p.npix))
+        x, z = p.pix_x[k], p.pix_z[k]
+        phi, tl, qx, qz, it = o.exit_point(e, x, z, sbar)
+        assert it > 0
+        T = tl + math.hypot(x - qx, z - qz) * sbar
+        bphi, bT = _brute_exit(p, e, x, z, sbar)
+        assert T <= bT * (1 + 1e-14)
+        assert abs(T - bT) <= 1e-12 * bT
+        assert abs(phi - bphi) < 1e-6
+        # Snell's law at q: sin(theta_lens) / c_lens = sin(theta_tissue) / c_med
+        nrm = np.array([qx - p.arc_cx, qz - p.arc_cz]) / p.lens_radius
+        a = np.array([qx - p.elem_x[e], qz - p.elem_z[e]])
+        b = np.array([x - qx, z - qz])
+        sl = (a[0] * nrm[1] - a[1] * nrm[0]) / np.linalg.norm(a)
+        st = (b[0] * nrm[1] - b[1] * nrm[0]) / np.linalg.norm(b)
+        assert abs(sl / p.c_lens - st * sbar) < 1e-12 * sbar
+
+
+def test_exit_straight_line_when_lens_matches_medium():
+    """c_lens = c_med: the Fermat path is the straight line, T = |r_e - r| / c."""
+    c = 1500.0
+    p = small(c_lens=c)
+    o = oracle.Oracle(p)
+    for e in (0, 7, 31):
+        for k in (0, 40, 80):
+            x, z = p.pix_x[k], p.pix_z[k]
+            phi, tl, qx, qz, _ = o.exit_point(e, x, z, 1.0 / c)
+            T = tl + math.hypot(x - qx, z - qz) / c
+            assert T == pytest.approx(math.hypot(x - p.elem_x[e], z - p.elem_z[e]) / c, rel=1e-14)
+
+
+def test_zero_thickness_lens_reduces_to_straight_ray():
+    p0 = small(d_lens=0.0)
+    pn = dataclasses.replace(p0, lens_mode=1)
+    s = p0.initial_slowness(1470.0).astype(np.float64)
+    T0, _, _ = oracle.Oracle(p0).delays(s)
+    Tn, _, _ = oracle.Oracle(pn).delays(s)
+    # float32-rounded element positions sit within 1e-8 m of the arc: <= 1e-8 / c_lens
+    np.testing.assert_allclose(T0, Tn, rtol=0, atol=1e-8 / p0.c_lens)
+
+
+def test_homogeneous_delay_is_distance_over_speed():
+    """Uniform s: the ray sum is L*s exactly, so T = T_lens + |q - r| / c;
+    without a lens T = |r_e - r| / c."""
+    pn = small(lens_mode=1)
+    c = 1530.0
+    s = pn.initial_slowness(c).astype(np.float64)
+    s[:] = 1.0 / c
+    T, _, _ = oracle.Oracle(pn).delays(s)
+    D = np.hypot(pn.pix_x[None, :] - pn.elem_x[:, None], pn.pix_z[None, :] - pn.elem_z[:, None])
+    np.testing.assert_allclose(T, D / c, rtol=1e-14)
+    p = small()
+    o = oracle.Oracle(p)
+    T, _, phi = o.delays(s)
+    for e in (3, 20):
+        for k in (5, 33):
+            tl, qx, qz = o.exit_from_angle(e, phi[e, k])
+            assert T[e, k] == pytest.approx(tl + math.hypot(p.pix_x[k] - qx, p.pix_z[k] - qz) / c,
+                                            rel=1e-14)
+
+
+# ---------------------------------------------------------------- bicubic + ray sum (Eq. 1)
+def test_keys_weights_partition_and_interpolation():
+    o = oracle.Oracle(small())
+    for t in (0.0, 0.13, 0.5, 0.999):
+        w = o.keys_weights(t)
+        assert w.sum() == pytest.approx(1.0, abs=1e-15)
+        # reproduces linear and quadratic functions sampled at -1, 0, 1, 2
+        xs = np.array([-1.0, 0.0, 1.0, 2.0])
+        assert (w * xs).sum() == pytest.approx(t, abs=1e-15)
+        assert (w * xs ** 2).sum() == pytest.approx(t * t, abs=1e-14)
+    np.testing.assert_allclose(o.keys_weights(0.0), [0, 1, 0, 0], atol=0)
+
+
+def _grid_xy(p):
+    gx = p.x0 + p.dx * np.arange(p.nx)
+    gz = p.z0 + p.dz * np.arange(p.nz)
+    return np.meshgrid(gx, gz)
+
+
+def test_bicubic_reproduces_quadratic_field_interior():
+    p = small()
+    o = oracle.Oracle(p)
+    X, Z = _grid_xy(p)
+    f = lambda x, z: 1e-3 + 0.02 * x - 0.013 * z + 0.7 * x * z + 0.4 * x * x - 0.3 * z * z
+    s = f(X, Z)
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        x = p.x0 + p.dx * rng.uniform(1.0, p.nx - 2.0)
+        z = p.z0 + p.dz * rng.uniform(1.0, p.nz - 2.0)
+        assert o.bicubic(s, x, z) == pytest.approx(f(x, z), abs=1e-15)
+
+
+def test_ray_sum_linear_field_closed_form():
+    """Mean of N+1 equally spaced samples of a linear field is its midpoint value."""
+    p = small()
+    o = oracle.Oracle(p)
+    X, Z = _grid_xy(p)
+    a, bx, bz = 6.4e-4, 1e-3, -2e-3
+    s = a + bx * X + bz * Z
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        qx, x = p.x0 + p.dx * rng.uniform(1, p.nx - 2, 2)
+        qz, z = p.z0 + p.dz * rng.uniform(1, p.nz - 2, 2)
+        L = math.hypot(x - qx, z - qz)
+        ref = L * (a + bx * 0.5 * (qx + x) + bz * 0.5 * (qz + z))
+        assert o.ray_time(s, qx, qz, x, z) == pytest.approx(ref, rel=1e-13)
+
+
+def test_layered_vertical_ray_matches_sum_of_thicknesses():
+    """Fine grid of a two-layer medium: vertical ray time ~ sum h_k / c_k (interpolation error only)."""
+    p = small(nx=64, nz=400)
+    o = oracle.Oracle(p)
+    X, Z = _grid_xy(p)
+    zi = 0.015
+    s = np.where(Z < zi, 1 / 1450.0, 1 / 1570.0)
+    z0, z1 = 0.002, 0.045
+    x = 0.0
+    ref = (zi - z0) / 1450.0 + (z1 - zi) / 1570.0
+    p2 = dataclasses.replace(p, nseg=4000)
+    t = oracle.Oracle(p2).ray_time(s, x, z0, x, z1)
+    # the bicubic smears the step over ~2 cells: error <= jump * 2 dz
+    assert abs(t - ref) < abs(1 / 1450.0 - 1 / 1570.0) * 2 * p.dz
+
+
+# ---------------------------------------------------------------- DAS (Eq. 5) + CMPE
+def _point_problem(c=1540.0, **over):
+    p = small(**over)
+    p.medium = synth.Medium(speeds=[c])
+    return p
+
+
+def _point_data(p, x, z, amp=1.0):
+    T = synth.oneway_times(p, np.array([x]), np.array([z]))
+    return synth.echoes(p, T, np.array([amp]))
+
+
+def test_point_scatterer_focuses_with_zero_phase_error():
+    """Homogeneous medium at the true speed: every subaperture image is real-positive at the
+    scatterer, so a one-pixel patch on it has zero CMPE; the 3x3 patch around it has a
+    CMPE far below the one seen at a 3 % speed error."""
+    c = 1540.0
+    p = _point_problem(c)
+    o = oracle.Oracle(p)
+    P = 4                                                  # centre patch of the 3x3 grid
+    centre = P * p.patch_npix + p.patch_npix // 2
+    x, z = p.pix_x[centre], p.pix_z[centre]
+    psi = _point_data(p, x, z)
+    s = np.full((p.nz, p.nx), 1.0 / c)
+    T, apod, _ = o.delays(s)
+    B = o.das(psi, T, apod)
+    Bc = B[:, centre]
+    live = np.abs(Bc) > 1e-3 * np.abs(Bc).max()
+    assert live.sum() > 0.5 * len(Bc)
+    assert np.all(np.abs(np.angle(Bc[live])) < 1e-7)
+    assert np.all(Bc[live].real > 0)
+    # focus: the compounded image peaks at the scatterer among the patch pixels
+    tot = np.abs(B.sum(0))[P * p.patch_npix:(P + 1) * p.patch_npix]
+    assert int(np.argmax(tot)) == p.patch_npix // 2
+    # one-pixel patch on the scatterer: exactly zero phase error
+    p1 = dataclasses.replace(p, n_patch=1, patch_npix=1, pix_x=np.array([x]), pix_z=np.array([z]))
+    o1 = oracle.Oracle(p1)
+    T1, a1, _ = o1.delays(s)
+    L1, z1, r1, m1, M1 = o1.cmpe(o1.das(psi, T1, a1))
+    assert M1 > 0 and L1 < 1e-7
+    # 3x3 patch: true speed vs 3 % off
+    L, zc, rho, mask, M = o.cmpe(B, mask_in=np.ones((p.n_patch, o.npair), np.uint8))
+    err_true = np.abs(np.angle(zc[P])).mean()
+    s_bad = np.full((p.nz, p.nx), 1.0 / (1.03 * c))
+    Tb, apb, _ = o.delays(s_bad)
+    Bb = o.das(psi, Tb, apb)
+    Lb, zb, rb, mb, Mb = o.cmpe(Bb, mask_in=np.ones_like(mask))
+    err_bad = np.abs(np.angle(zb[P])).mean()
+    assert err_bad > 1e-2
+    assert err_true < 0.05 * err_bad
+
+
+def test_reciprocity_and_global_phase_invariance(tiny):
+    o = oracle.Oracle(tiny)
+    psi = synth.simulate(tiny, 300, seed=5)
+    assert np.array_equal(psi, psi.transpose(1, 0, 2))
+    s = tiny.initial_slowness().astype(np.float64)
+    T, apod, _ = o.delays(s)
+    B = o.das(psi, T, apod)
+    n = o.nsub
+    Bm = B.reshape(n, n, -1)
+    np.testing.assert_allclose(Bm, Bm.transpose(1, 0, 2), rtol=1e-12, atol=1e-12 * np.abs(B).max())
+    rot = np.exp(1j * 0.7).astype(np.complex64)
+    B2 = o.das(psi * rot, T, apod)
+    L1, z1, r1, m1, M1 = o.cmpe(B)
+    L2, z2, r2, m2, M2 = o.cmpe(B2, mask_in=m1)
+    assert L2 == pytest.approx(L1, rel=1e-5)   # psi*rot is rounded to complex64
+    np.testing.assert_allclose(r2, r1, atol=1e-5)
+
+
+def test_das_single_constant_trace_closed_form():
+    """Psi_{t,r} = const for one pair only: B = const * exp(j 2 pi fd tau) in that block."""
+    p = small(n_ang=1, n_rad=1, patch_w=1)
+    o = oracle.Oracle(p)
+    psi = np.zeros((p.ne, p.ne, p.ns), np.complex64)
+    t, r = 9, 22
+    psi[t, r, :] = 0.5 - 0.25j
+    s = np.full((p.nz, p.nx), 1 / 1500.0)
+    T, apod, _ = o.delays(s)
+    B = o.das(psi, T, apod)
+    tau = T[t, 0] + T[r, 0] + p.t_ttp
+    b = (t // p.sub_width) * o.nsub + r // p.sub_width
+    ref = (0.5 - 0.25j) * np.exp(2j * np.pi * p.fd * tau) * apod[t, 0] * apod[r, 0]
+    assert abs(B[b, 0] - ref) < 1e-12
+    others = np.delete(B[:, 0], b)
+    assert np.all(others == 0)
+
+
+def test_cmpe_closed_form_phase_shift():
+    """B2 = B1 exp(j a) on a patch: z = exp(-j a) sum|B1|^2, rho = 1, loss = |a|."""
+    p = small(n_ang=1, n_rad=1, patch_w=3)
+    o = oracle.Oracle(p)
+    rng = np.random.default_rng(2)
+    nb, npix = o.nsub ** 2, p.npix
+    B = rng.standard_normal((nb, npix)) + 1j * rng.standard_normal((nb, npix))
+    pairs = o.pairs()
+    a = 0.37
+    # make only the first pair fully correlated
+    B[pairs[0, 1]] = B[pairs[0, 0]] * np.exp(1j * a)
+    L, z, rho, mask, M = o.cmpe(B)
+    assert rho[0, 0] == pytest.approx(1.0, abs=1e-14)
+    assert np.angle(z[0, 0]) == pytest.approx(-a, abs=1e-14)
+    only = np.zeros_like(mask)
+    only[0, 0] = 1
+    L1, *_ = o.cmpe(B, mask_in=only)
+    assert L1 == pytest.approx(a, abs=1e-14)
+
+
+def test_cmpe_pairs_are_common_midpoint_and_skip_reciprocal():
+    p = small()
+    o = oracle.Oracle(p)
+    n = o.nsub
+    pr = o.pairs()
+    assert len(pr) == (n - 1) * (n - 2)
+    for b1, b2 in pr:
+        i1, j1 = divmod(int(b1), n)
+        i2, j2 = divmod(int(b2), n)
+        assert i1 + j1 == i2 + j2 and i2 == i1 + 1
+        assert not (i2 == j1 and j2 == i1)
+
+
+# ---------------------------------------------------------------- regularisers (Eq. 10-11)
+def test_regularizers_closed_form_linear_and_quadratic_speed():
+    p = small()
+    o = oracle.Oracle(p)
+    X, Z = _grid_xy(p)
+    hx = p.dx * 1e3
+    gam = 2.0                                    # m/s per mm along x
+    c = 1500.0 + gam * (X - p.x0) * 1e3
+    rtv, rsv = o.regularizers(1.0 / c)
+    nt = (p.nx - 1) * p.nz + p.nx * (p.nz - 1)
+    assert rtv == pytest.approx((p.nx - 1) * p.nz * (gam - p.kx1) / nt, rel=1e-9)
+    assert rsv == pytest.approx(0.0, abs=1e-9)
+    beta = 0.05                                  # c = c0 + beta x^2 (x in mm): d2c = 2 beta
+    c2 = 1500.0 + beta * ((Z - p.z0) * 1e3) ** 2
+    rtv2, rsv2 = o.regularizers(1.0 / c2)
+    ns_ = (p.nx - 2) * p.nz + p.nx * (p.nz - 2)
+    assert rsv2 == pytest.approx(p.nx * (p.nz - 2) * (2 * beta - p.kz2) / ns_, rel=1e-7)
+    del hx
+
+
+def test_regularizer_gradient_matches_finite_differences():
+    p = small(nx=7, nz=6)
+    o = oracle.Oracle(p)
+    rng = np.random.default_rng(4)
+    s = 1.0 / (1500.0 + 30.0 * rng.standard_normal((p.nz, p.nx)))
+    g = o.regularizer_grad(s)
+
+    def R(sv):
+        a, b = o.regularizers(sv)
+        return p.w1 * a + p.w2 * b
+
+    for k in rng.choice(s.size, 12, replace=False):
+        h = 1e-9 * s.flat[k]
+        sp, sm = s.copy(), s.copy()
+        sp.flat[k] += h
+        sm.flat[k] -= h
+        fd = (R(sp) - R(sm)) / (2 * h)
+        assert g.flat[k] == pytest.approx(fd, rel=1e-5, abs=1e-6 * np.abs(g).max())
+
+
+# ---------------------------------------------------------------- adjoint (Fig. 1g)
+def test_cmpe_adjoint_matches_finite_differences():
+    p = small(n_ang=1, n_rad=2, patch_w=3)
+    o = oracle.Oracle(p)
+    rng = np.random.default_rng(7)
+    nb, npix = o.nsub ** 2, p.npix
+    B = rng.standard_normal((nb, npix)) + 1j * rng.standard_normal((nb, npix))
+    ones = np.ones((p.n_patch, o.npair), np.uint8)
+    L, z, rho, mask, M = o.cmpe(B, mask_in=ones)
+    G = o.cmpe_adjoint(B, z, ones, M)
+    for _ in range(15):
+        b, q = int(rng.integers(nb)), int(rng.integers(npix))
+        for d, part in ((1e-7, "re"), (1e-7j, "im")):
+            Bp, Bm = B.copy(), B.copy()
+            Bp[b, q] += d
+            Bm[b, q] -= d
+            fd = (o.cmpe(Bp, mask_in=ones)[0] - o.cmpe(Bm, mask_in=ones)[0]) / 2e-7
+            an = G[b, q].real if part == "re" else G[b, q].imag
+            assert an == pytest.approx(fd, rel=1e-5, abs=1e-9)
+
+
+def test_ray_adjoint_dot_product(tiny):
+    """<A v, w> = <v, A^T w> for the linear map s -> ray sums (exit angles frozen)."""
+    o = oracle.Oracle(tiny)
+    rng = np.random.default_rng(8)
+    s0 = tiny.initial_slowness().astype(np.float64)
+    T0, apod, phi = o.delays(s0)
+    v = 1e-5 * rng.standard_normal(s0.shape)
+    Tv, _, _ = o.delays(s0 + v, apod_in=apod, phi_in=phi)
+    Av = Tv - T0
+    w = rng.standard_normal(T0.shape) * apod
+    ATw = o.ray_adjoint(s0, phi, apod, w)
+    lhs = float((Av * w).sum())
+    rhs = float((v * ATw).sum())
+    assert lhs == pytest.approx(rhs, rel=1e-9)
+
+
+def test_full_gradient_matches_central_differences():
+    """dL/ds of Eq. 12 vs central differences, with apodization, CMPE mask and exit
+    angles frozen (the constants of the adjoint)."""
+    p = small(n_ang=2, n_rad=2, patch_w=3, nx=8, nz=8)
+    o = oracle.Oracle(p)
+    psi = synth.simulate(p, 400, seed=11)
+    rng = np.random.default_rng(9)
+    s = (1.0 / (1510.0 + 20.0 * rng.standard_normal((p.nz, p.nx))))
+    parts, g, mask, M = o.loss_grad(psi, s)
+    _, apod, phi = o.delays(s)
+    assert M > 0
+
+    def loss(sv):
+        return o.loss_grad(psi, sv, apod_in=apod, mask_in=mask, phi_in=phi, grad=False)[0][0]
+
+    checked = 0
+    for k in np.argsort(-np.abs(g).ravel())[:10]:
+        h = 1e-8 * s.flat[k]
+        sp, sm = s.copy(), s.copy()
+        sp.flat[k] += h
+        sm.flat[k] -= h
+        fd = (loss(sp) - loss(sm)) / (2 * h)
+        assert g.flat[k] == pytest.approx(fd, rel=1e-5), k
+        checked += 1
+    assert checked == 10
+
+
+# ---------------------------------------------------------------- optimiser (Eq. 9)
+def test_adam_first_step_is_signed_learning_rate():
+    """Step 1 of Adam: m_hat = g, v_hat = g^2, so u moves by lr * g / (|g| + eps)."""
+    o = oracle.Oracle(small())
+    s = np.full(5, 1 / 1540.0)
+    g = np.array([3.0, -2.0, 1e-3, -5e4, 0.0])
+    lr = 0.01
+    s1, m, v = o.adam(s, g, np.zeros(5), np.zeros(5), 1, lr)
+    du = (s1 - s) * 1540.0
+    gu = g / 1540.0
+    np.testing.assert_allclose(du, -lr * gu / (np.abs(gu) + 1e-8), rtol=1e-9, atol=1e-15)
+    # beta1 = beta2 = 0 keeps it a sign step at every iteration
+    s2, _, _ = o.adam(s1, -g, m, v, 2, lr, beta1=0.0, beta2=0.0)
+    np.testing.assert_allclose((s2 - s1) * 1540.0, lr * gu / (np.abs(gu) + 1e-8), rtol=1e-9, atol=1e-15)
