@@ -1,0 +1,341 @@
+"""Benchmark: autofocus iterations/s (forward + adjoint + Adam step) on the
+128-element, 128 x 128 x 3072-sample full-synthetic-aperture acquisition with a
+128 x 128 slowness grid and 400 patches of 9 x 9 pixels.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype c64|bf16|f16]
+    python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
+
+One JSON line on rank 0.  Under torchrun each rank runs its own seeded
+acquisition (independent problems, no data-path collective: weak scaling);
+timing is bracketed by a barrier and synchronisation and the max over ranks
+is taken.  The channel data (384 MiB) is larger than L2, so no extra flush is
+done between iterations.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "autofocus iterations/s (fwd+adjoint), 128×128-FSA; GB/s vs HBM peak; vs plain FP32"
+WORKLOAD = ("128-element curvilinear FSA 128x128x3072 complex IQ at 14 MHz, 60 mm radius, 1.2 mm lens at "
+            "1000 m/s, 128x128 slowness grid, 400 patches of 9x9 pixels, 64 ray segments, 3-layer medium")
+SEED = 20261203
+N_SCATTERERS = 150_000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="c64", choices=["c64", "bf16", "f16"])
+    ap.add_argument("--scatterers", type=int, default=N_SCATTERERS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-jobs", type=int, default=2)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(gpu_index), "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(problem, psi, s, n_patches, seed=0):
+    """One forward + adjoint + Adam step of the FP64 oracle on n_patches of the
+    workload's patches; returns (seconds, fraction of the per-iteration work)."""
+    import dataclasses
+
+    import oracle
+    rng = np.random.default_rng(seed)
+    patches = np.sort(rng.choice(problem.n_patch, n_patches, replace=False))
+    pix = np.concatenate([np.arange(P * problem.patch_npix, (P + 1) * problem.patch_npix) for P in patches])
+    sub = dataclasses.replace(problem, n_patch=len(patches), pix_x=problem.pix_x[pix], pix_z=problem.pix_z[pix])
+    o = oracle.Oracle(sub)
+    sd = s.astype(np.float64)
+    t0 = time.perf_counter()
+    parts, g, _, _ = o.loss_grad(psi, sd)
+    o.adam(sd, g, np.zeros_like(sd), np.zeros_like(sd), 1, problem.lr)
+    dt = time.perf_counter() - t0
+    return dt, n_patches / problem.n_patch
+
+
+def make_problem(rank: int, n_scat: int):
+    import synth
+    p = synth.config_full()
+    psi = synth.simulate(p, n_scat, seed=SEED + rank)
+    return p, psi
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the oracle as it stands, on the host cores, rank 0 only."""
+    if rank != 0:
+        return
+    import synth
+    p, psi = make_problem(0, args.scatterers)
+    s = p.initial_slowness()
+    n_patches = 4
+    for _ in range(args.warmup):
+        oracle_sample(p, psi, s, n_patches)
+    units = 0.0
+    t_total = 0.0
+    for k in range(args.steps):
+        dt, frac = oracle_sample(p, psi, s, n_patches, seed=k)
+        t_total += dt
+        units += frac
+    value = units / t_total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded speckle, 3-layer medium)",
+        "config": {"workload": WORKLOAD, "sample": f"{n_patches} of 400 patches per step"},
+        "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": 1, "kind": "oracle",
+                         "sample": f"one forward+adjoint+step on {n_patches} of 400 patches per step, "
+                                   "scaled by the pixel fraction"},
+        "e2e": {"value": value, "unit": "iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- roofline
+def stage_roofline(stage, ms, launches, p, iq_bytes, pk):
+    """Roofline entry of one stage: algorithmic bytes (or lane operations) per launch
+    divided by its average launch time."""
+    ne, npix = p.ne, p.npix
+    nsub = p.nsub
+    nb = nsub * nsub
+    avg_s = ms / launches * 1e-3
+    hbm = pk.get("hbm_gbs", 6400.0)
+    if stage in ("das_forward", "das_adjoint"):
+        # channel data once + one-way tables + images (+ dL/dB and dL/dT for the adjoint)
+        bytes_ = iq_bytes + ne * npix * 16 + nb * npix * 8
+        if stage == "das_adjoint":
+            bytes_ += ne * npix * 4
+        achieved = bytes_ / avg_s / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "kernel": stage,
+                "algorithmic_bytes": bytes_, "avg_launch_ms": ms / launches}
+    # FP32 lane-operation bound: SMs x 128 lanes x max SM clock
+    lanes = 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6
+    pts = ne * npix * (p.nseg + 1)
+    ops_per_point = {"delays": 44, "ray_adjoint": 40}.get(stage, 0)
+    ops = pts * ops_per_point
+    achieved = ops / avg_s / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": lanes / 1e12, "unit": "Tlane-op/s",
+            "frac": achieved / (lanes / 1e12), "traffic": None, "kernel": stage,
+            "algorithmic_ops": ops, "avg_launch_ms": ms / launches}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2608_06853_b300 as af
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=dev)
+    p, psi = make_problem(rank, args.scatterers)
+    dtype = {"c64": af.AF_IQ_C64, "bf16": af.AF_IQ_BF16, "f16": af.AF_IQ_F16}[args.dtype]
+    stream = torch.cuda.Stream(device=dev)
+    plan = af.Plan(p, iq_dtype=dtype, stream=stream)
+    with torch.cuda.stream(stream):
+        x = torch.from_numpy(psi).to(dev)
+        if dtype == af.AF_IQ_C64:
+            iq, scale = x, None
+            iq_bytes = psi.nbytes
+        else:
+            r = torch.view_as_real(x)
+            scale = r.abs().amax(dim=(1, 2, 3)).clamp_min(1e-30).float().contiguous()
+            iq = (r / scale[:, None, None, None]).to(torch.bfloat16 if dtype == af.AF_IQ_BF16 else torch.float16)
+            iq = iq.contiguous()
+            iq_bytes = psi.nbytes // 2
+        del x
+        s0 = torch.from_numpy(p.initial_slowness()).to(dev)
+        s = s0.clone()
+        m, v, g = torch.zeros_like(s), torch.zeros_like(s), torch.zeros_like(s)
+        loss = torch.zeros(4, device=dev)
+    stream.synchronize()
+    for it in range(1, args.warmup + 1):
+        plan.af_iterate(iq, s, g, m, v, it, loss, scale)
+    stream.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    plan.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for it in range(args.warmup + 1, args.warmup + args.steps + 1):
+        plan.af_iterate(iq, s, g, m, v, it, loss, scale)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    stages = plan.stage_times()
+    plan.set_timing(False)
+    clk = clocks.stop() if clocks else None
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * args.steps / (ms_max * 1e-3)
+    final_loss = loss.cpu().numpy().tolist()
+
+    # end to end: one autofocus job = upload of the acquisition and the initial map from
+    # pinned host memory, N_i = 100 iterations, read back of the final map and loss
+    n_iter = 100
+    h_iq = torch.view_as_real(torch.from_numpy(psi)).pin_memory() if dtype == af.AF_IQ_C64 else iq.cpu().pin_memory()
+    h_scale = scale.cpu().pin_memory() if scale is not None else None
+    h_s0 = torch.from_numpy(p.initial_slowness()).pin_memory()
+    h_out = torch.empty_like(h_s0).pin_memory()
+    h_loss = torch.empty(4).pin_memory()
+    d_iq = torch.empty(h_iq.shape, dtype=h_iq.dtype, device=dev)
+    d_scale = torch.empty(h_scale.shape, device=dev) if h_scale is not None else None
+    h2d = h_iq.numel() * h_iq.element_size() + h_s0.numel() * 4 + (h_scale.numel() * 4 if h_scale is not None else 0)
+    d2h = h_out.numel() * 4 + 16
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for job in range(args.e2e_jobs):
+        with torch.cuda.stream(stream):
+            d_iq.copy_(h_iq, non_blocking=True)
+            if d_scale is not None:
+                d_scale.copy_(h_scale, non_blocking=True)
+            s.copy_(h_s0, non_blocking=True)
+            m.zero_()
+            v.zero_()
+        iq_arg = torch.view_as_complex(d_iq) if dtype == af.AF_IQ_C64 else d_iq
+        for it in range(1, n_iter + 1):
+            plan.af_iterate(iq_arg, s, g, m, v, it, loss, d_scale)
+        with torch.cuda.stream(stream):
+            h_out.copy_(s, non_blocking=True)
+            h_loss.copy_(loss, non_blocking=True)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * args.e2e_jobs * n_iter / float(te.item())
+
+    if rank != 0:
+        return
+    pk = peaks()
+    ranked = sorted(((v_[0], k) for k, v_ in stages.items() if v_[1] > 0), reverse=True)
+    dom = ranked[0][1]
+    roof = stage_roofline(dom, stages[dom][0], stages[dom][1], p, iq_bytes, pk)
+    # achieved HBM GB/s of the whole iteration by algorithmic bytes (channel data read twice)
+    it_bytes = 2 * iq_bytes
+    line = {
+        "metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"c64": "f32", "bf16": "bf16-storage/f32", "f16": "f16-storage/f32"}[args.dtype],
+        "data": "synthetic (seeded speckle, 3-layer medium); inputs larger than L2, no flush",
+        "config": {"workload": WORKLOAD, "iq_dtype": args.dtype, "scatterers": args.scatterers,
+                   "l2": "inputs larger than L2 (384 MiB channel data), no flush",
+                   "parallelism": f"independent acquisitions x{world}"},
+        "gpu_launches": sum(v_[1] for v_ in stages.values()) + stages["ray_adjoint"][1]
+                        + stages["cmpe_forward"][1],
+        "stage_ms": {k: v_[0] / max(v_[1], 1) for k, v_ in stages.items()},
+        "hbm_gbs_algorithmic": it_bytes / (ms_max / args.steps * 1e-3) / 1e9,
+        "roofline": roof,
+        "loss": final_loss,
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": "iterations/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h),
+                "step": f"one autofocus job: upload + {n_iter} iterations + read back"},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        n_patches = 40
+        dt, frac = oracle_sample(p, psi, p.initial_slowness(), n_patches)
+        line["cpu_baseline"] = {"value": frac / dt, "unit": "iterations/s", "cores": 1, "kind": "oracle",
+                                "sample": f"one forward+adjoint+step on {n_patches} of 400 patches "
+                                          f"({100 * frac:.0f} % of pixels, {dt:.1f} s), scaled by the pixel fraction"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    import paper_2608_06853_b300.build as b
+    import oracle
+    import synth
+    if rank == 0:
+        b.build()
+        oracle.build()
+        synth.build()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * af.h - C ABI of the B300 (sm_103a) lens-aware differentiable-beamforming
+ * autofocus library.
+ *
+ * The library runs one autofocus iteration of Frey et al., "Lens-Aware
+ * Differentiable Beamforming for In Vivo Distributed Aberration Correction
+ * with Curvilinear Transducers", on one GPU:
+ *
+ *   af_forward : Sec. III-A exit points at c_med (Eq. 8, Fermat), Eq. 1 ray
+ *                sums through the slowness grid, Eq. 2-4 apodization, Eq. 5
+ *                subaperture DAS with phase rotation, the CMPE focusing loss
+ *                (Sec. II-D) and Eq. 10-12 regularisation.
+ *   af_adjoint : dL/ds by a hand-written adjoint of af_forward (Fig. 1g),
+ *                exit points and masks held constant.
+ *   af_step    : the Eq. 9 update, run as Adam on u = s * c_ref.
+ *
+ * Conventions shared by every entry point
+ *  - Units are SI (m, s, s/m, Hz).  z grows into the tissue.
+ *  - Host pointers (const double* in af_config) are read during af_plan only.
+ *  - Every d_* pointer is caller-owned DEVICE memory on the current device;
+ *    the library never frees it.  The plan owns its own workspaces.
+ *  - Calls are asynchronous on the plan's stream (the cudaStream_t passed to
+ *    af_plan; NULL = legacy default stream).  Outputs are valid once that
+ *    stream has reached the call.
+ *  - Errors are returned as af_status codes and never thrown; af_last_error()
+ *    returns a message for the last failing call of the calling thread.
+ *    Argument and shape errors are detected on the host before any launch.
+ *  - A plan is not thread-safe; use one plan per host thread.
+ */
+#ifndef AF_H
+#define AF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct af_plan_s *af_plan_t;
+
+typedef enum {
+    AF_OK = 0,
+    AF_ERR_ARG = 1,          /* NULL pointer, non-finite or out-of-range scalar */
+    AF_ERR_SHAPE = 2,        /* inconsistent sizes (e.g. n_elem % sub_width != 0) */
+    AF_ERR_DTYPE = 3,        /* unknown iq_dtype, or a scale array missing for a 16-bit dtype */
+    AF_ERR_CUDA = 4,         /* a CUDA runtime call failed (message names it) */
+    AF_ERR_NUMERIC = 5,      /* non-positive or non-finite slowness seen on the device */
+    AF_ERR_TIMEOUT = 6,      /* reserved for bounded device waits */
+    AF_ERR_UNSUPPORTED = 7,  /* valid but outside what this build implements */
+    AF_ERR_STATE = 8         /* call order violated (e.g. af_adjoint before af_forward) */
+} af_status;
+
+/* storage of the demodulated channel data Psi */
+enum { AF_IQ_C64 = 0,        /* interleaved float32 (re, im) */
+       AF_IQ_BF16 = 1,       /* interleaved bfloat16 (re, im), times a per-transmit float scale */
+       AF_IQ_F16 = 2 };      /* interleaved float16 (re, im), times a per-transmit float scale */
+
+/* lens model */
+enum { AF_LENS_BENT_RAY = 0, /* Eq. 7-8: Fermat exit point on the lens surface */
+       AF_LENS_NONE = 1 };   /* Eq. 1 straight rays from the element */
+
+/* apodization */
+enum { AF_APOD_FNUMBER = 0,  /* |x'| <= z' / (2F), z' > 0 (usual f-number reading of Eq. 4) */
+       AF_APOD_PRINTED = 1 };/* |x'| <= (F/2) z', z' > 0 (Eq. 4 as printed) */
+
+/*
+ * Problem description (host memory, copied by af_plan).
+ *
+ * Array (Sec. II-A): element a at (elem_x[a], elem_z[a]); its orientation is
+ *   Eq. 3 from its neighbours (end elements: linear extrapolation).
+ * Lens (Sec. II-B, III-B, Table I): outer surface = arc of radius lens_radius
+ *   about (arc_cx, arc_cz), concentric with the elements; sound speed c_lens;
+ *   t_ttp is added to every round-trip delay (Eq. 6-7).
+ * Image points r_Omega: n_patch patches of patch_npix pixels, patch-major
+ *   (pixel p belongs to patch p / patch_npix), at (pix_x[p], pix_z[p]).
+ * Slowness grid (Sec. III-A): node (i, j) at (x0 + i dx, z0 + j dz),
+ *   stored row-major s[j * nx + i]; Keys bicubic interpolation; nseg ray
+ *   segments (nseg + 1 endpoints) from the exit point to the pixel.
+ *   Every pixel and the lens surface over the aperture must lie inside the
+ *   grid box.
+ * Channel data Psi[t][r][n] (Eq. 5): n_samp samples per (transmit, receive)
+ *   pair, sample n at time t0 + n / fs, demodulation frequency fd.
+ * Subapertures: blocks of sub_width consecutive elements; image
+ *   B_ij = transmit block i, receive block j.
+ * Table II: rho_thresh, fnum, nseg, w1, kx1, kz1, w2, kx2, kz2, lr.
+ * Adam (Eq. 9 as Adam): beta1, beta2, eps on u = s * c_ref.
+ */
+typedef struct {
+    int n_elem;
+    const double *elem_x, *elem_z;
+    int lens_mode;
+    double arc_cx, arc_cz, lens_radius, c_lens, t_ttp;
+    int apod_mode;
+    double fnum;
+    int n_patch, patch_npix;
+    const double *pix_x, *pix_z;
+    int nx, nz;
+    double x0, z0, dx, dz;
+    int nseg;
+    int n_samp;
+    double fs, fd, t0;
+    int iq_dtype;
+    int sub_width;
+    double rho_thresh;
+    double w1, kx1, kz1, w2, kx2, kz2;
+    double lr, beta1, beta2, eps, c_ref;
+} af_config;
+
+/* Host-only validation of a configuration (no CUDA call).  Returns AF_OK or
+ * the first error found; af_last_error() names it. */
+af_status af_check_config(const af_config *cfg);
+
+/* Host-only: device bytes af_plan will allocate for this configuration. */
+af_status af_workspace_bytes(const af_config *cfg, size_t *bytes);
+
+/* Validate cfg, copy the geometry to the device of the calling thread and
+ * allocate the plan's workspaces.  stream: a cudaStream_t (or NULL). */
+af_status af_plan(const af_config *cfg, void *stream, af_plan_t *out);
+
+/* Forward pass (spec steps a-e): loss of Eq. 12 at slowness d_slowness.
+ *  d_iq        Psi, [n_elem][n_elem][n_samp] complex, layout per iq_dtype.
+ *              Must stay valid and unchanged until the matching af_adjoint.
+ *  d_iq_scale  [n_elem] float per-transmit scale for 16-bit dtypes, else NULL.
+ *  d_slowness  [nz][nx] float, s/m, all > 0.
+ *  d_loss      [4] float written: {L, L_CMPE, R_TV, R_SV}. */
+af_status af_forward(af_plan_t plan, const void *d_iq, const float *d_iq_scale,
+                     const float *d_slowness, float *d_loss);
+
+/* Adjoint of the last af_forward (Fig. 1g): d_grad [nz][nx] = dL/ds (s/m)^-1.
+ * Delays are recomputed from the stored one-way tables, not stored per pair. */
+af_status af_adjoint(af_plan_t plan, float *d_grad);
+
+/* Eq. 9 update as Adam on u = s * c_ref (step counts from 1):
+ * updates d_slowness, d_adam_m, d_adam_v ([nz][nx] float each) in place. */
+af_status af_step(af_plan_t plan, const float *d_grad, float *d_slowness,
+                  float *d_adam_m, float *d_adam_v, int step);
+
+/* One whole iteration: af_forward + af_adjoint + af_step. */
+af_status af_iterate(af_plan_t plan, const void *d_iq, const float *d_iq_scale,
+                     float *d_slowness, float *d_grad, float *d_adam_m,
+                     float *d_adam_v, int step, float *d_loss);
+
+/* Release the plan's device memory.  NULL is accepted. */
+af_status af_destroy(af_plan_t plan);
+
+/* Waits for the plan's stream and returns AF_ERR_NUMERIC if a kernel flagged
+ * a non-positive or non-finite slowness since the last call, else AF_OK. */
+af_status af_sync_status(af_plan_t plan);
+
+/* ---- introspection of the last af_forward / af_adjoint (device outputs) ---- */
+
+/* One-way delays T[e][p] (s, element -> lens -> pixel, Eq. 7-8 + Eq. 1) as
+ * double, and the apodization bits h_e(r_p) (Eq. 4), both [n_elem][npix].
+ * Either pointer may be NULL. */
+af_status af_get_delays(af_plan_t plan, double *d_T, uint8_t *d_apod);
+
+/* Lens exit angles phi[e][p] (rad, about the arc centre), [n_elem][npix]. */
+af_status af_get_exit_angles(af_plan_t plan, float *d_phi);
+
+/* Subaperture images B[b][p] as interleaved float (re, im), b = i*nsub + j,
+ * [nsub*nsub][npix][2]. */
+af_status af_get_images(af_plan_t plan, float *d_B);
+
+/* CMPE cross terms z[P][k] ([n_patch][npair][2] float) and correlation mask
+ * bits ([n_patch][npair] uint8); *h_n_active (host) = number of set bits.
+ * Any pointer may be NULL.  Synchronises the plan's stream. */
+af_status af_get_cmpe(af_plan_t plan, float *d_z, uint8_t *d_mask, int *h_n_active);
+
+/* dL/dB[b][p] (= dL/dRe B + j dL/dIm B) of the last af_adjoint,
+ * [nsub*nsub][npix][2] float. */
+af_status af_get_image_grad(af_plan_t plan, float *d_G);
+
+/* dL/dT[e][p] of the last af_adjoint, [n_elem][npix] float. */
+af_status af_get_delay_grad(af_plan_t plan, float *d_g);
+
+/* Host: counters of the last af_forward (synchronises the stream):
+ *  [0] apodized (element, pixel) pairs, [1] exit solves that fell back to
+ *  float64, [2] active CMPE terms, [3] number of CMPE pairs per patch. */
+af_status af_get_counters(af_plan_t plan, long long *h_counters);
+
+/* Per-stage device timing with CUDA events recorded on the plan's stream.
+ * af_set_timing(plan, 1) clears the record and starts recording every kernel
+ * stage of later calls; 0 stops.  af_get_stage_times synchronises the stream
+ * and writes, per stage, the summed milliseconds (h_ms) and launch counts
+ * (h_count) since recording started.  Stages (AF_NSTAGES = 8):
+ *  0 grid statistics (c_med, Eq. 10-11)   1 delays (Eq. 1-4, 8)
+ *  2 DAS forward (Eq. 5)                   3 CMPE forward + loss
+ *  4 CMPE adjoint                          5 DAS adjoint
+ *  6 ray adjoint + gradient reduction      7 Adam update (Eq. 9) */
+#define AF_NSTAGES 8
+af_status af_set_timing(af_plan_t plan, int enable);
+af_status af_get_stage_times(af_plan_t plan, float *h_ms, int *h_count);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *af_last_error(void);
+
+/* Static name of a status code. */
+const char *af_status_string(af_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AF_H */

@@ -1,0 +1,324 @@
+"""B300 (sm_103a) lens-aware differentiable-beamforming autofocus.
+
+Thin ctypes binding of the C ABI in include/af.h (libaf.so, built in-tree by
+`paper_2608_06853_b300.build.build()`).  The binding only marshals arguments:
+every step of the hot path runs in the library's CUDA kernels.  PyTorch
+provides device memory and streams.  There is no CPU fallback: if libaf.so is
+missing or no CUDA device is present, the calls raise.
+
+Main entry points (same names as the C ABI):
+    Plan(problem, iq_dtype=AF_IQ_C64, stream=None)
+    plan.af_forward(iq, s, loss, iq_scale=None)   -> loss[4] = {L, L_CMPE, R_TV, R_SV}
+    plan.af_adjoint(grad)                          -> dL/ds
+    plan.af_step(grad, s, m, v, step)              -> Adam update (Eq. 9)
+    plan.af_iterate(iq, s, grad, m, v, step, loss, iq_scale=None)
+    AutofocusLoss.apply(s, plan, iq, iq_scale)     -> torch.autograd.Function
+
+A `problem` is any object with the attributes of the library's problem
+description (elem_x, elem_z, arc_cx, ..., see `ProblemFields`).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libaf.so")
+
+AF_OK, AF_ERR_ARG, AF_ERR_SHAPE, AF_ERR_DTYPE, AF_ERR_CUDA = 0, 1, 2, 3, 4
+AF_ERR_NUMERIC, AF_ERR_TIMEOUT, AF_ERR_UNSUPPORTED, AF_ERR_STATE = 5, 6, 7, 8
+AF_IQ_C64, AF_IQ_BF16, AF_IQ_F16 = 0, 1, 2
+AF_LENS_BENT_RAY, AF_LENS_NONE = 0, 1
+AF_APOD_FNUMBER, AF_APOD_PRINTED = 0, 1
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class AfConfig(ctypes.Structure):
+    """Mirror of af_config (include/af.h)."""
+    _fields_ = [
+        ("n_elem", ctypes.c_int), ("elem_x", _dp), ("elem_z", _dp),
+        ("lens_mode", ctypes.c_int), ("arc_cx", ctypes.c_double), ("arc_cz", ctypes.c_double),
+        ("lens_radius", ctypes.c_double), ("c_lens", ctypes.c_double), ("t_ttp", ctypes.c_double),
+        ("apod_mode", ctypes.c_int), ("fnum", ctypes.c_double),
+        ("n_patch", ctypes.c_int), ("patch_npix", ctypes.c_int), ("pix_x", _dp), ("pix_z", _dp),
+        ("nx", ctypes.c_int), ("nz", ctypes.c_int), ("x0", ctypes.c_double), ("z0", ctypes.c_double),
+        ("dx", ctypes.c_double), ("dz", ctypes.c_double), ("nseg", ctypes.c_int),
+        ("n_samp", ctypes.c_int), ("fs", ctypes.c_double), ("fd", ctypes.c_double),
+        ("t0", ctypes.c_double), ("iq_dtype", ctypes.c_int), ("sub_width", ctypes.c_int),
+        ("rho_thresh", ctypes.c_double),
+        ("w1", ctypes.c_double), ("kx1", ctypes.c_double), ("kz1", ctypes.c_double),
+        ("w2", ctypes.c_double), ("kx2", ctypes.c_double), ("kz2", ctypes.c_double),
+        ("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+        ("eps", ctypes.c_double), ("c_ref", ctypes.c_double),
+    ]
+
+
+ProblemFields = ("elem_x", "elem_z", "lens_mode", "arc_cx", "arc_cz", "lens_radius", "c_lens",
+                 "t_ttp", "apod_mode", "fnum", "n_patch", "patch_npix", "pix_x", "pix_z", "nx",
+                 "nz", "x0", "z0", "dx", "dz", "nseg", "ns", "fs", "fd", "t0", "sub_width",
+                 "rho_thresh", "w1", "kx1", "kz1", "w2", "kx2", "kz2", "lr", "beta1", "beta2",
+                 "eps", "c_ref")
+
+_lib = None
+
+# name -> (restype, argtypes) of every exported entry point of include/af.h
+_VP = ctypes.c_void_p
+_SIGNATURES = {
+    "af_check_config": (ctypes.c_int, [ctypes.POINTER(AfConfig)]),
+    "af_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(AfConfig), ctypes.POINTER(ctypes.c_size_t)]),
+    "af_plan": (ctypes.c_int, [ctypes.POINTER(AfConfig), _VP, ctypes.POINTER(_VP)]),
+    "af_forward": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "af_adjoint": (ctypes.c_int, [_VP, _VP]),
+    "af_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int]),
+    "af_iterate": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
+    "af_destroy": (ctypes.c_int, [_VP]),
+    "af_sync_status": (ctypes.c_int, [_VP]),
+    "af_get_delays": (ctypes.c_int, [_VP, _VP, _VP]),
+    "af_get_exit_angles": (ctypes.c_int, [_VP, _VP]),
+    "af_get_images": (ctypes.c_int, [_VP, _VP]),
+    "af_get_cmpe": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_int)]),
+    "af_get_image_grad": (ctypes.c_int, [_VP, _VP]),
+    "af_get_delay_grad": (ctypes.c_int, [_VP, _VP]),
+    "af_get_counters": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
+    "af_set_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "af_get_stage_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]),
+    "af_last_error": (ctypes.c_char_p, []),
+    "af_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+class AfError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = load()
+        name = lib.af_status_string(status).decode()
+        msg = lib.af_last_error().decode()
+        super().__init__(f"{where}: {name}: {msg}")
+        self.status = status
+
+
+def load():
+    """Load libaf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2608_06853_b300.build.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != AF_OK:
+        raise AfError(status, where)
+
+
+def make_config(problem, iq_dtype: int = AF_IQ_C64):
+    """af_config for a problem description; returns (config, arrays kept alive)."""
+    keep = []
+
+    def arr(a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        keep.append(a)
+        return a.ctypes.data_as(_dp)
+
+    c = AfConfig()
+    c.n_elem = int(len(problem.elem_x))
+    c.elem_x, c.elem_z = arr(problem.elem_x), arr(problem.elem_z)
+    c.lens_mode = int(problem.lens_mode)
+    c.arc_cx, c.arc_cz = float(problem.arc_cx), float(problem.arc_cz)
+    c.lens_radius, c.c_lens, c.t_ttp = float(problem.lens_radius), float(problem.c_lens), float(problem.t_ttp)
+    c.apod_mode, c.fnum = int(problem.apod_mode), float(problem.fnum)
+    c.n_patch, c.patch_npix = int(problem.n_patch), int(problem.patch_npix)
+    c.pix_x, c.pix_z = arr(problem.pix_x), arr(problem.pix_z)
+    c.nx, c.nz = int(problem.nx), int(problem.nz)
+    c.x0, c.z0, c.dx, c.dz = float(problem.x0), float(problem.z0), float(problem.dx), float(problem.dz)
+    c.nseg = int(problem.nseg)
+    c.n_samp, c.fs, c.fd, c.t0 = int(problem.ns), float(problem.fs), float(problem.fd), float(problem.t0)
+    c.iq_dtype = int(iq_dtype)
+    c.sub_width = int(problem.sub_width)
+    c.rho_thresh = float(problem.rho_thresh)
+    c.w1, c.kx1, c.kz1 = float(problem.w1), float(problem.kx1), float(problem.kz1)
+    c.w2, c.kx2, c.kz2 = float(problem.w2), float(problem.kx2), float(problem.kz2)
+    c.lr, c.beta1, c.beta2 = float(problem.lr), float(problem.beta1), float(problem.beta2)
+    c.eps, c.c_ref = float(problem.eps), float(problem.c_ref)
+    return c, keep
+
+
+def check_config(problem, iq_dtype: int = AF_IQ_C64) -> int:
+    """Host-only validation (no CUDA call); returns the af_status code."""
+    c, keep = make_config(problem, iq_dtype)
+    return load().af_check_config(ctypes.byref(c))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("device tensors only (torch.Tensor on cuda)")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def iq_view(iq):
+    """The raw storage of channel data: complex64 tensors are passed as interleaved float32."""
+    import torch
+    if iq.dtype == torch.complex64:
+        return torch.view_as_real(iq)
+    return iq
+
+
+class Plan:
+    """An af_plan_t: device geometry and workspaces for one problem on one stream."""
+
+    def __init__(self, problem, iq_dtype: int = AF_IQ_C64, stream=None):
+        import torch
+        self.lib = load()
+        self.problem = problem
+        self.iq_dtype = iq_dtype
+        self.ne = int(len(problem.elem_x))
+        self.npix = int(problem.n_patch) * int(problem.patch_npix)
+        self.nsub = self.ne // int(problem.sub_width)
+        self.npair = (self.nsub - 1) * (self.nsub - 2) if self.nsub >= 3 else 0
+        self.nx, self.nz = int(problem.nx), int(problem.nz)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        cfg, keep = make_config(problem, iq_dtype)
+        h = ctypes.c_void_p()
+        _check(self.lib.af_plan(ctypes.byref(cfg), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
+               "af_plan")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.af_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- the four calls of one iteration ----
+    def af_forward(self, iq, s, loss, iq_scale=None):
+        _check(self.lib.af_forward(self.handle, _ptr(iq_view(iq)), _ptr(iq_scale), _ptr(s), _ptr(loss)),
+               "af_forward")
+        return loss
+
+    def af_adjoint(self, grad):
+        _check(self.lib.af_adjoint(self.handle, _ptr(grad)), "af_adjoint")
+        return grad
+
+    def af_step(self, grad, s, m, v, step: int):
+        _check(self.lib.af_step(self.handle, _ptr(grad), _ptr(s), _ptr(m), _ptr(v), int(step)), "af_step")
+
+    def af_iterate(self, iq, s, grad, m, v, step: int, loss, iq_scale=None):
+        _check(self.lib.af_iterate(self.handle, _ptr(iq_view(iq)), _ptr(iq_scale), _ptr(s), _ptr(grad),
+                                   _ptr(m), _ptr(v), int(step), _ptr(loss)), "af_iterate")
+        return loss
+
+    def af_sync_status(self) -> int:
+        return self.lib.af_sync_status(self.handle)
+
+    # ---- introspection ----
+    def _dev(self):
+        import torch
+        return torch.device("cuda", torch.cuda.current_device())
+
+    def delays(self):
+        """(T [ne][npix] float64 seconds, apod [ne][npix] uint8) of the last forward."""
+        import torch
+        T = torch.empty((self.ne, self.npix), dtype=torch.float64, device=self._dev())
+        a = torch.empty((self.ne, self.npix), dtype=torch.uint8, device=self._dev())
+        _check(self.lib.af_get_delays(self.handle, _ptr(T), _ptr(a)), "af_get_delays")
+        return T, a
+
+    def exit_angles(self):
+        import torch
+        phi = torch.empty((self.ne, self.npix), dtype=torch.float32, device=self._dev())
+        _check(self.lib.af_get_exit_angles(self.handle, _ptr(phi)), "af_get_exit_angles")
+        return phi
+
+    def images(self):
+        """B [nsub*nsub][npix] complex64."""
+        import torch
+        B = torch.empty((self.nsub * self.nsub, self.npix, 2), dtype=torch.float32, device=self._dev())
+        _check(self.lib.af_get_images(self.handle, _ptr(B)), "af_get_images")
+        return torch.view_as_complex(B)
+
+    def cmpe(self):
+        """(z [n_patch][npair] complex64, mask [n_patch][npair] uint8, n_active)."""
+        import torch
+        P = int(self.problem.n_patch)
+        z = torch.empty((P, max(self.npair, 1), 2), dtype=torch.float32, device=self._dev())
+        m = torch.empty((P, max(self.npair, 1)), dtype=torch.uint8, device=self._dev())
+        n = ctypes.c_int()
+        _check(self.lib.af_get_cmpe(self.handle, _ptr(z), _ptr(m), ctypes.byref(n)), "af_get_cmpe")
+        return torch.view_as_complex(z)[:, : self.npair], m[:, : self.npair], n.value
+
+    def image_grad(self):
+        """dL/dB [nsub*nsub][npix] complex64 of the last adjoint."""
+        import torch
+        G = torch.empty((self.nsub * self.nsub, self.npix, 2), dtype=torch.float32, device=self._dev())
+        _check(self.lib.af_get_image_grad(self.handle, _ptr(G)), "af_get_image_grad")
+        return torch.view_as_complex(G)
+
+    def delay_grad(self):
+        import torch
+        g = torch.empty((self.ne, self.npix), dtype=torch.float32, device=self._dev())
+        _check(self.lib.af_get_delay_grad(self.handle, _ptr(g)), "af_get_delay_grad")
+        return g
+
+    STAGES = ("grid_stats", "delays", "das_forward", "cmpe_forward", "cmpe_adjoint",
+              "das_adjoint", "ray_adjoint", "adam")
+
+    def set_timing(self, enable: bool):
+        _check(self.lib.af_set_timing(self.handle, 1 if enable else 0), "af_set_timing")
+
+    def stage_times(self):
+        """{stage: (total ms, launches)} recorded since set_timing(True)."""
+        ms = (ctypes.c_float * 8)()
+        n = (ctypes.c_int * 8)()
+        _check(self.lib.af_get_stage_times(self.handle, ms, n), "af_get_stage_times")
+        return {name: (ms[k], n[k]) for k, name in enumerate(self.STAGES)}
+
+    def counters(self):
+        """{apodized pairs, float64 exit solves, active CMPE terms, CMPE pairs per patch}."""
+        c = (ctypes.c_longlong * 4)()
+        _check(self.lib.af_get_counters(self.handle, c), "af_get_counters")
+        return dict(n_apod=c[0], fp64_solves=c[1], n_active=c[2], npair=c[3])
+
+
+try:
+    import torch as _torch
+
+    class AutofocusLoss(_torch.autograd.Function):
+        """L(s) of Eq. 12 with the hand-written adjoint as its backward.
+
+        forward: af_forward; backward: af_adjoint (delays are recomputed from the
+        one-way tables, not stored per transmit/receive pair)."""
+
+        @staticmethod
+        def forward(ctx, s, plan, iq, iq_scale=None):
+            s = s.contiguous()
+            loss = _torch.empty(4, dtype=_torch.float32, device=s.device)
+            plan.af_forward(iq, s, loss, iq_scale)
+            ctx.plan = plan
+            return loss[0].clone()
+
+        @staticmethod
+        def backward(ctx, gout):
+            plan = ctx.plan
+            grad = _torch.empty((plan.nz, plan.nx), dtype=_torch.float32, device=gout.device)
+            plan.af_adjoint(grad)
+            return grad * gout, None, None, None
+except ImportError:  # pragma: no cover - torch is part of the image
+    pass

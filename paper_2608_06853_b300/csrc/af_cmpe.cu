@@ -1,0 +1,204 @@
+// Common-midpoint phase error (Sec. II-D; the focusing loss of Simson et al.
+// that the paper keeps unchanged).  Reading used by this library: per patch
+// and per pair of common-midpoint subaperture images (i, j) ~ (i+1, j-1),
+// with the reciprocal pair j = i + 1 skipped,
+//   z   = sum_p B_ij(p) conj(B_i+1,j-1(p)),
+//   rho = |z| / sqrt(sum |B_ij|^2 sum |B_i+1,j-1|^2),  m = [rho >= rho_thresh],
+//   L_CMPE = sum m |arg z| / max(1, sum m),
+// with m held constant in the adjoint.  Total loss of Eq. 12 adds w1 R_TV +
+// w2 R_SV from the grid-statistics kernel.
+#include <math.h>
+
+#include "af_internal.cuh"
+
+namespace {
+
+// pair k of a patch -> (i, j) of its first image; the second is (i+1, j-1)
+__device__ __forceinline__ void pair_ij(int k, int n, int &i, int &j)
+{
+    i = k / (n - 2);
+    int jj = k - i * (n - 2);
+    j = jj < i ? jj + 1 : jj + 2;
+}
+// index of the pair whose first image is (i, j), or -1
+__device__ __forceinline__ int pair_index(int i, int j, int n)
+{
+    if (i < 0 || i > n - 2 || j < 1 || j > n - 1 || j == i + 1) return -1;
+    return i * (n - 2) + (j - 1) - (j > i + 1 ? 1 : 0);
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// one CTA per patch; warp w takes pairs w, w + 8, ...
+__global__ void __launch_bounds__(256) cmpe_forward_kernel(AfGeom g, const float2 *__restrict__ B,
+                                                           float2 *__restrict__ z,
+                                                           uint8_t *__restrict__ mask,
+                                                           double *__restrict__ patch_sum,
+                                                           int *__restrict__ patch_cnt)
+{
+    __shared__ double s_sum[8];
+    __shared__ int s_cnt[8];
+    const int P = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int base = P * g.patch_npix;
+    double lsum = 0.0;
+    int cnt = 0;
+    for (int k = w; k < g.npair; k += 8) {
+        int i, j;
+        pair_ij(k, g.nsub, i, j);
+        const float2 *B1 = B + (long)(i * g.nsub + j) * g.npix + base;
+        const float2 *B2 = B + (long)((i + 1) * g.nsub + (j - 1)) * g.npix + base;
+        float zr = 0.f, zi = 0.f, e1 = 0.f, e2 = 0.f;
+        for (int q = lane; q < g.patch_npix; q += 32) {
+            const float2 a = B1[q], c = B2[q];
+            zr = fmaf(a.x, c.x, fmaf(a.y, c.y, zr));
+            zi = fmaf(a.y, c.x, fmaf(-a.x, c.y, zi));
+            e1 = fmaf(a.x, a.x, fmaf(a.y, a.y, e1));
+            e2 = fmaf(c.x, c.x, fmaf(c.y, c.y, e2));
+        }
+        zr = warp_sum(zr); zi = warp_sum(zi); e1 = warp_sum(e1); e2 = warp_sum(e2);
+        if (lane == 0) {
+            const double den = sqrt((double)e1 * (double)e2);
+            const double rho = den > 0.0 ? hypot((double)zr, (double)zi) / den : 0.0;
+            const int m = rho >= (double)g.rho_thresh;
+            const long o = (long)P * g.npair + k;
+            z[o] = make_float2(zr, zi);
+            mask[o] = (uint8_t)m;
+            if (m) {
+                lsum += fabs(atan2((double)zi, (double)zr));
+                ++cnt;
+            }
+        }
+    }
+    if (lane == 0) { s_sum[w] = lsum; s_cnt[w] = cnt; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        int c = 0;
+        for (int k = 0; k < 8; ++k) { a += s_sum[k]; c += s_cnt[k]; }
+        patch_sum[P] = a;
+        patch_cnt[P] = c;
+    }
+}
+
+// fixed-order sums over patches; loss = {L, L_CMPE, R_TV, R_SV}
+__global__ void __launch_bounds__(256) cmpe_finalize_kernel(AfGeom g, const double *__restrict__ patch_sum,
+                                                            const int *__restrict__ patch_cnt,
+                                                            AfScal *scal, float *__restrict__ loss)
+{
+    __shared__ double s_a[256];
+    __shared__ int s_c[256];
+    double a = 0.0;
+    int c = 0;
+    for (int P = threadIdx.x; P < g.n_patch; P += 256) { a += patch_sum[P]; c += patch_cnt[P]; }
+    s_a[threadIdx.x] = a;
+    s_c[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) { s_a[threadIdx.x] += s_a[threadIdx.x + o]; s_c[threadIdx.x] += s_c[threadIdx.x + o]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int M = s_c[0];
+        const double lc = s_a[0] / (M > 1 ? M : 1);
+        scal->lcmpe = (float)lc;
+        scal->n_active = M;
+        scal->inv_m = (float)(1.0 / (M > 1 ? M : 1));
+        if (loss) {
+            loss[0] = (float)(lc + (double)g.w1 * scal->rtv + (double)g.w2 * scal->rsv);
+            loss[1] = (float)lc;
+            loss[2] = scal->rtv;
+            loss[3] = scal->rsv;
+        }
+    }
+}
+
+// sign of arg z as atan2 defines it (arg in (-pi, pi])
+__device__ __forceinline__ float arg_sign(float2 z)
+{
+    const float a = atan2f(z.y, z.x);
+    return a > 0.0f ? 1.0f : (a < 0.0f ? -1.0f : 0.0f);
+}
+
+// G[b][p] = dL_CMPE/dB_b(p): an image is the first member of at most one pair
+// ((i,j) ~ (i+1,j-1)) and the second member of at most one ((i-1,j+1) ~ (i,j)).
+//   first:  w j z B2 / |z|^2     second: -w j conj(z) B1 / |z|^2,  w = sgn(arg z) / max(1, M)
+__global__ void __launch_bounds__(256) cmpe_backward_kernel(AfGeom g, const float2 *__restrict__ B,
+                                                            const float2 *__restrict__ z,
+                                                            const uint8_t *__restrict__ mask,
+                                                            const AfScal *scal,
+                                                            float2 *__restrict__ G)
+{
+    const long total = (long)g.nb * g.npix;
+    const float inv_m = scal->inv_m;
+    const int n = g.nsub;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long)gridDim.x * blockDim.x) {
+        const int b = (int)(idx / g.npix), p = (int)(idx - (long)b * g.npix);
+        const int i = b / n, j = b - i * n, P = p / g.patch_npix;
+        float gr = 0.0f, gi = 0.0f;
+        int k = pair_index(i, j, n);
+        if (k >= 0) {
+            const long o = (long)P * g.npair + k;
+            if (mask[o]) {
+                const float2 zz = z[o];
+                const float mag2 = zz.x * zz.x + zz.y * zz.y;
+                const float sg = arg_sign(zz);
+                if (sg != 0.0f && mag2 > 0.0f) {
+                    const float w = sg * inv_m / mag2;
+                    const float2 c = B[(long)((i + 1) * n + (j - 1)) * g.npix + p];
+                    const float tr = zz.x * c.x - zz.y * c.y, ti = zz.x * c.y + zz.y * c.x;
+                    gr += -w * ti;
+                    gi += w * tr;
+                }
+            }
+        }
+        k = pair_index(i - 1, j + 1, n);
+        if (k >= 0) {
+            const long o = (long)P * g.npair + k;
+            if (mask[o]) {
+                const float2 zz = z[o];
+                const float mag2 = zz.x * zz.x + zz.y * zz.y;
+                const float sg = arg_sign(zz);
+                if (sg != 0.0f && mag2 > 0.0f) {
+                    const float w = sg * inv_m / mag2;
+                    const float2 a = B[(long)((i - 1) * n + (j + 1)) * g.npix + p];
+                    const float ur = zz.x * a.x + zz.y * a.y, ui = zz.x * a.y - zz.y * a.x;
+                    gr += w * ui;
+                    gi += -w * ur;
+                }
+            }
+        }
+        G[idx] = make_float2(gr, gi);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_cmpe_forward(af_plan_t pl, float *loss)
+{
+    if (pl->g.n_patch > 0 && pl->g.npair > 0) {
+        cmpe_forward_kernel<<<pl->g.n_patch, 256, 0, pl->stream>>>(pl->g, pl->B, pl->z, pl->mask,
+                                                                  pl->patch_sum, pl->patch_cnt);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    AfGeom g = pl->g;
+    if (g.npair == 0) g.n_patch = 0;     // no terms: L_CMPE = 0
+    cmpe_finalize_kernel<<<1, 256, 0, pl->stream>>>(g, pl->patch_sum, pl->patch_cnt, pl->scal, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cmpe_backward(af_plan_t pl)
+{
+    const long total = (long)pl->g.nb * pl->g.npix;
+    if (total == 0) return cudaSuccess;
+    long blocks = (total + 255) / 256;
+    if (blocks > 65535L * 8) blocks = 65535L * 8;
+    if (pl->g.npair == 0) return cudaMemsetAsync(pl->G, 0, total * sizeof(float2), pl->stream);
+    cmpe_backward_kernel<<<(int)blocks, 256, 0, pl->stream>>>(pl->g, pl->B, pl->z, pl->mask, pl->scal, pl->G);
+    return cudaGetLastError();
+}

@@ -1,0 +1,219 @@
+// Subaperture delay-and-sum (Eq. 5) and its adjoint with respect to the
+// one-way delays (Fig. 1g).  Delays are generated inside the gather from the
+// one-way tables (tau = T_t + T_r + t_ttp, never materialised per pair).
+//
+// CTA = 32 consecutive pixels x 8 warps.  Warp w takes receive blocks j = w,
+// w + 8, ...; a lane owns a pixel.  The receive-side delays and phasors of
+// block j live in registers, the transmit side is re-read per transmit
+// (shared by the warps of the CTA through L1).  Phase rotation is separable:
+//   exp(j 2 pi fd tau) = P_t P_r,  P_e = exp(j 2 pi fd (T_e + t_ttp / 2)).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "af_internal.cuh"
+
+namespace {
+
+template <int DT> struct Sample;
+template <> struct Sample<AF_IQ_C64> {
+    using T = float2;
+    static __device__ __forceinline__ float2 load(const T *p) { return __ldg(p); }
+};
+template <> struct Sample<AF_IQ_BF16> {
+    using T = __nv_bfloat162;
+    static __device__ __forceinline__ float2 load(const T *p) { return __bfloat1622float2(__ldg(p)); }
+};
+template <> struct Sample<AF_IQ_F16> {
+    using T = __half2;
+    static __device__ __forceinline__ float2 load(const T *p) { return __half22float2(__ldg(p)); }
+};
+
+constexpr int kWarps = 8;   // warps per CTA; warp w takes receive blocks w, w + 8, ...
+
+template <int W, int DT>
+__global__ void __launch_bounds__(256, 4) das_forward_kernel(AfGeom g, const void *__restrict__ iq,
+                                                             const float *__restrict__ scale,
+                                                             const float4 *__restrict__ D,
+                                                             float2 *__restrict__ B)
+{
+    using S = Sample<DT>;
+    const int lane = threadIdx.x & 31;
+    const int p = blockIdx.x * 32 + lane;
+    if (p >= g.npix) return;
+    const typename S::T *psi = reinterpret_cast<const typename S::T *>(iq);
+    const int lim = g.ns - 1;
+    for (int j = threadIdx.x >> 5; j < g.nsub; j += kWarps) {
+        int nr[W];
+        float fr[W];
+        float2 pr[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const float4 d = D[(long)(j * W + k) * g.npix + p];
+            nr[k] = __float_as_int(d.x);
+            fr[k] = d.y;
+            pr[k] = make_float2(d.z, d.w);
+        }
+        for (int i = 0; i < g.nsub; ++i) {
+            float ar = 0.0f, ai = 0.0f;
+            for (int tt = 0; tt < W; ++tt) {
+                const int t = i * W + tt;
+                const float4 dt = D[(long)t * g.npix + p];
+                const int nt = __float_as_int(dt.x);
+                if (nt == AF_APOD_OFF) continue;
+                const typename S::T *base = psi + ((long)t * g.ne + j * W) * g.ns;
+                float sr = 0.0f, si = 0.0f;
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    int n = nt + nr[k];
+                    float f = dt.y + fr[k];
+                    if (f >= 1.0f) { f -= 1.0f; ++n; }
+                    if ((unsigned)n < (unsigned)lim) {
+                        const float2 a = S::load(base + (long)k * g.ns + n);
+                        const float2 b = S::load(base + (long)k * g.ns + n + 1);
+                        const float vr = fmaf(f, b.x - a.x, a.x), vi = fmaf(f, b.y - a.y, a.y);
+                        sr = fmaf(pr[k].x, vr, fmaf(-pr[k].y, vi, sr));
+                        si = fmaf(pr[k].x, vi, fmaf(pr[k].y, vr, si));
+                    }
+                }
+                float cr = dt.z, ci = dt.w;
+                if (DT != AF_IQ_C64) { const float sc = scale[t]; cr *= sc; ci *= sc; }
+                ar = fmaf(cr, sr, fmaf(-ci, si, ar));
+                ai = fmaf(cr, si, fmaf(ci, sr, ai));
+            }
+            B[(long)(i * g.nsub + j) * g.npix + p] = make_float2(ar, ai);
+        }
+    }
+}
+
+// dL/dtau for one gather: Re(conj(G) exp(j 2 pi fd tau) (fs dPsi/du + j 2 pi fd Psi(u)));
+// it is added to dL/dT_t and to dL/dT_r.  Both roles meet in a per-CTA table
+// gE[e][lane] in shared memory, so each dL/dT[e][p] is written exactly once.
+template <int W, int DT>
+__global__ void __launch_bounds__(256, 3) das_adjoint_kernel(AfGeom g, const void *__restrict__ iq,
+                                                             const float *__restrict__ scale,
+                                                             const float4 *__restrict__ D,
+                                                             const float2 *__restrict__ G,
+                                                             float *__restrict__ gdel)
+{
+    using S = Sample<DT>;
+    extern __shared__ float gE[];                 // [ne][32]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * 32 + lane;
+    const bool valid = p < g.npix;
+    for (int k = threadIdx.x; k < g.ne * 32; k += blockDim.x) gE[k] = 0.0f;
+    __syncthreads();
+    const typename S::T *psi = reinterpret_cast<const typename S::T *>(iq);
+    const int lim = g.ns - 1;
+    if (valid) {
+        for (int j = warp; j < g.nsub; j += kWarps) {
+            int nr[W];
+            float fr[W];
+            float2 pr[W];
+            float gr[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                const float4 d = D[(long)(j * W + k) * g.npix + p];
+                nr[k] = __float_as_int(d.x);
+                fr[k] = d.y;
+                pr[k] = make_float2(d.z, d.w);
+                gr[k] = 0.0f;
+            }
+            for (int i = 0; i < g.nsub; ++i) {
+                const float2 Gv = G[(long)(i * g.nsub + j) * g.npix + p];
+                if (Gv.x == 0.0f && Gv.y == 0.0f) continue;
+                for (int tt = 0; tt < W; ++tt) {
+                    const int t = i * W + tt;
+                    const float4 dt = D[(long)t * g.npix + p];
+                    const int nt = __float_as_int(dt.x);
+                    if (nt == AF_APOD_OFF) continue;
+                    float sc = 1.0f;
+                    if (DT != AF_IQ_C64) sc = scale[t];
+                    // X = conj(G) P_t (scaled)
+                    const float xr = sc * fmaf(Gv.x, dt.z, Gv.y * dt.w);
+                    const float xi = sc * fmaf(Gv.x, dt.w, -Gv.y * dt.z);
+                    const typename S::T *base = psi + ((long)t * g.ne + j * W) * g.ns;
+                    float gt = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < W; ++k) {
+                        int n = nt + nr[k];
+                        float f = dt.y + fr[k];
+                        if (f >= 1.0f) { f -= 1.0f; ++n; }
+                        if ((unsigned)n < (unsigned)lim) {
+                            const float2 a = S::load(base + (long)k * g.ns + n);
+                            const float2 b = S::load(base + (long)k * g.ns + n + 1);
+                            const float sx = b.x - a.x, sy = b.y - a.y;
+                            const float vr = fmaf(f, sx, a.x), vi = fmaf(f, sy, a.y);
+                            const float yr = fmaf(xr, pr[k].x, -xi * pr[k].y);
+                            const float yi = fmaf(xr, pr[k].y, xi * pr[k].x);
+                            const float dr = fmaf(g.fs, sx, -g.wd * vi);
+                            const float di = fmaf(g.fs, sy, g.wd * vr);
+                            const float q = fmaf(yr, dr, -yi * di);
+                            gt += q;
+                            gr[k] += q;
+                        }
+                    }
+                    if (gt != 0.0f) atomicAdd(&gE[t * 32 + lane], gt);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+                if (gr[k] != 0.0f) atomicAdd(&gE[(j * W + k) * 32 + lane], gr[k]);
+        }
+    }
+    __syncthreads();
+    if (valid)
+        for (int e = warp; e < g.ne; e += kWarps) gdel[(long)e * g.npix + p] = gE[e * 32 + lane];
+}
+
+template <int W, int DT>
+cudaError_t launch_fwd_t(af_plan_t pl)
+{
+    const int blocks = (pl->g.npix + 31) / 32;
+    das_forward_kernel<W, DT><<<blocks, 32 * kWarps, 0, pl->stream>>>(
+        pl->g, pl->iq, pl->iq_scale, pl->D, pl->B);
+    return cudaGetLastError();
+}
+
+template <int W, int DT>
+cudaError_t launch_adj_t(af_plan_t pl)
+{
+    const int blocks = (pl->g.npix + 31) / 32;
+    const size_t smem = (size_t)pl->g.ne * 32 * sizeof(float);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(das_adjoint_kernel<W, DT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    das_adjoint_kernel<W, DT><<<blocks, 32 * kWarps, smem, pl->stream>>>(
+        pl->g, pl->iq, pl->iq_scale, pl->D, pl->G, pl->gdel);
+    return cudaGetLastError();
+}
+
+template <int DT>
+cudaError_t dispatch_w(af_plan_t pl, bool adj)
+{
+    switch (pl->g.W) {
+    case 1: return adj ? launch_adj_t<1, DT>(pl) : launch_fwd_t<1, DT>(pl);
+    case 2: return adj ? launch_adj_t<2, DT>(pl) : launch_fwd_t<2, DT>(pl);
+    case 4: return adj ? launch_adj_t<4, DT>(pl) : launch_fwd_t<4, DT>(pl);
+    case 8: return adj ? launch_adj_t<8, DT>(pl) : launch_fwd_t<8, DT>(pl);
+    case 16: return adj ? launch_adj_t<16, DT>(pl) : launch_fwd_t<16, DT>(pl);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t dispatch(af_plan_t pl, bool adj)
+{
+    if (pl->g.npix == 0) return cudaSuccess;
+    switch (pl->iq_dtype) {
+    case AF_IQ_C64: return dispatch_w<AF_IQ_C64>(pl, adj);
+    case AF_IQ_BF16: return dispatch_w<AF_IQ_BF16>(pl, adj);
+    case AF_IQ_F16: return dispatch_w<AF_IQ_F16>(pl, adj);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_das_forward(af_plan_t pl) { return dispatch(pl, false); }
+cudaError_t launch_das_adjoint(af_plan_t pl) { return dispatch(pl, true); }

@@ -1,0 +1,307 @@
+// Delay generation: grid statistics (c_med, Eq. 10-11) and the fused
+// one-way delay kernel (Eq. 2-4 apodization, Eq. 8 lens exit point by
+// Fermat's principle, Eq. 1 straight-ray bicubic slowness sum, Sec. III-A).
+#include <math.h>
+
+#include "af_internal.cuh"
+
+namespace {
+
+// deadzone D_k(x) = max(0, |x| - k)  (Sec. II-D)
+__device__ __forceinline__ float deadzone(float x, float k) { return fmaxf(fabsf(x) - k, 0.0f); }
+
+// One CTA: c_med = mean(1/s) in double, the two regularisers of Eq. 10-11 on
+// c = 1/s, and the numeric check of the slowness map.
+__global__ void __launch_bounds__(1024) grid_stats_kernel(AfGeom g, const float *__restrict__ s,
+                                                          AfScal *scal)
+{
+    __shared__ double red[3][32];
+    double acc_c = 0.0, acc_a = 0.0, acc_b = 0.0;
+    int bad = 0;
+    for (int k = threadIdx.x; k < g.ng; k += blockDim.x) {
+        int j = k / g.nx, i = k - j * g.nx;
+        float sv = s[k];
+        if (!(sv > 0.0f) || !isfinite(sv)) bad = 1;
+        float c0 = 1.0f / sv;
+        acc_c += (double)c0;
+        if (i + 1 < g.nx) acc_a += deadzone((1.0f / s[k + 1] - c0) / g.hx_mm, g.kx1);
+        if (j + 1 < g.nz) acc_a += deadzone((1.0f / s[k + g.nx] - c0) / g.hz_mm, g.kz1);
+        if (i >= 1 && i + 1 < g.nx)
+            acc_b += deadzone((1.0f / s[k + 1] - 2.0f * c0 + 1.0f / s[k - 1]) / (g.hx_mm * g.hx_mm), g.kx2);
+        if (j >= 1 && j + 1 < g.nz)
+            acc_b += deadzone((1.0f / s[k + g.nx] - 2.0f * c0 + 1.0f / s[k - g.nx]) / (g.hz_mm * g.hz_mm), g.kz2);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        acc_c += __shfl_xor_sync(0xffffffffu, acc_c, o);
+        acc_a += __shfl_xor_sync(0xffffffffu, acc_a, o);
+        acc_b += __shfl_xor_sync(0xffffffffu, acc_b, o);
+    }
+    bad = __syncthreads_or(bad);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { red[0][w] = acc_c; red[1][w] = acc_a; red[2][w] = acc_b; }
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        acc_c = l < nw ? red[0][l] : 0.0;
+        acc_a = l < nw ? red[1][l] : 0.0;
+        acc_b = l < nw ? red[2][l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            acc_c += __shfl_xor_sync(0xffffffffu, acc_c, o);
+            acc_a += __shfl_xor_sync(0xffffffffu, acc_a, o);
+            acc_b += __shfl_xor_sync(0xffffffffu, acc_b, o);
+        }
+        if (l == 0) {
+            double cmed = acc_c / g.ng;
+            scal->sbar = (float)(1.0 / cmed);
+            scal->rtv = (float)(acc_a * g.na_inv);
+            scal->rsv = (float)(acc_b * g.nb_inv);
+            scal->fp64_solves = 0;
+            scal->n_apod = 0;
+            if (bad) scal->numeric_flag = 1;
+        }
+    }
+}
+
+// chord length between radius r1 at angle 0 and radius r2 at angle d, with
+// its first two derivatives in d; sh = sin(d/2), ch = cos(d/2)
+struct Chord { float len, d1, d2; };
+__device__ __forceinline__ Chord chord(float r1, float r2, float d)
+{
+    float sh, ch;
+    sincosf(0.5f * d, &sh, &ch);
+    float k = r1 * r2, dr = r1 - r2;
+    float len = sqrtf(fmaf(dr, dr, 4.0f * k * sh * sh));
+    float sd = 2.0f * sh * ch, cd = fmaf(-2.0f * sh, sh, 1.0f);
+    float inv = 1.0f / len;
+    float ks = k * sd * inv;
+    return {len, ks, (k * cd - ks * ks) * inv};
+}
+
+struct ChordD { double len, d1, d2; };
+__device__ ChordD chord_d(double r1, double r2, double d)
+{
+    double sh, ch;
+    sincos(0.5 * d, &sh, &ch);
+    double k = r1 * r2, dr = r1 - r2;
+    double len = sqrt(dr * dr + 4.0 * k * sh * sh);
+    double ks = k * 2.0 * sh * ch / len;
+    return {len, ks, (k * (1.0 - 2.0 * sh * sh) - ks * ks) / len};
+}
+
+// float64 safeguarded Newton / bisection on dT/dd = 0 over [lo, hi]
+__device__ double exit_solve_fp64(double re, double rp, double RL, double dp, double inv_cl,
+                                  double sbar)
+{
+    double lo = fmin(0.0, dp), hi = fmax(0.0, dp), x = 0.0;
+    for (int it = 0; it < 100; ++it) {
+        ChordD a = chord_d(re, RL, x), b = chord_d(rp, RL, x - dp);
+        double f = a.d1 * inv_cl + b.d1 * sbar;
+        double fp = a.d2 * inv_cl + b.d2 * sbar;
+        if (f < 0.0) lo = x; else hi = x;
+        double xn = fp > 0.0 ? x - f / fp : 0.5 * (lo + hi);
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        double step = fabs(xn - x);
+        x = xn;
+        if (step < 1e-13 || hi - lo < 1e-13) break;
+    }
+    return x;
+}
+
+// One thread per (element e, pixel p), grid-stride over e * npix + p, with the
+// slowness deviation s - sbar staged once per CTA in shared memory, padded by
+// two edge-replicated nodes on every side so that each of the 16 taps of a
+// point inside the grid box reads the clamp-to-edge value without a branch.
+__global__ void __launch_bounds__(256) delays_kernel(AfGeom g, const float *__restrict__ s,
+                                                     const float4 *__restrict__ elem,
+                                                     const float2 *__restrict__ elem_pol,
+                                                     const float2 *__restrict__ pix,
+                                                     const float2 *__restrict__ pix_pol,
+                                                     float *__restrict__ phi, int warm,
+                                                     float4 *__restrict__ D, AfScal *scal)
+{
+    extern __shared__ float sm[];
+    const float sbar = scal->sbar;
+    const int P = g.pitch, rows = g.nz + 4;
+    for (int k = threadIdx.x; k < P * rows; k += blockDim.x) {
+        int jj = k / P, ii = k - jj * P;
+        int i = min(max(ii - 2, 0), g.nx - 1), j = min(max(jj - 2, 0), g.nz - 1);
+        sm[k] = s[j * g.nx + i] - sbar;           // exact (Sterbenz) for s within 2x of sbar
+    }
+    __syncthreads();
+
+    const ff sfs = ff_two_prod(sbar, g.fs);       // sbar * fs, exact
+    const ff fscl = {g.fs_clens_hi, g.fs_clens_lo};
+    const ff off = {g.off_hi, g.off_lo};
+    int n_apod = 0, n_fp64 = 0;
+    const long total = (long)g.ne * g.npix;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long)gridDim.x * blockDim.x) {
+        const int e = (int)(idx / g.npix), p = (int)(idx - (long)e * g.npix);
+        const float4 el = elem[e];
+        const float2 px = pix[p];
+        // Eq. 2: pixel in the element frame; Eq. 4: constant f-number cone
+        const float ddx = px.x - el.x, ddz = px.y - el.y;
+        const float xp = el.z * ddx - el.w * ddz, zp = el.w * ddx + el.z * ddz;
+        const float lim = g.apod_mode == AF_APOD_PRINTED ? zp * g.fnum_half : zp * g.fnum_inv2;
+        if (!(zp > 0.0f && fabsf(xp) <= lim)) {
+            D[idx] = make_float4(__int_as_float(AF_APOD_OFF), 0.0f, 0.0f, 0.0f);
+            continue;
+        }
+        ++n_apod;
+        // Eq. 8 / Sec. III-A: exit point at c_med by Fermat's principle
+        float qx = el.x, qz = el.y, ph = 0.0f;
+        ff tl = {0.0f, 0.0f};
+        if (g.lens_mode == AF_LENS_BENT_RAY) {
+            const float2 ep = elem_pol[e], pp = pix_pol[p];
+            const float dp = pp.x - ep.x;
+            float lo = fminf(0.0f, dp), hi = fmaxf(0.0f, dp);
+            float x = warm ? fminf(fmaxf(phi[idx] - ep.x, lo), hi) : 0.0f;
+            bool conv = (lo == hi);
+            for (int it = 0; it < 16 && !conv; ++it) {
+                Chord a = chord(ep.y, g.RL, x), b = chord(pp.y, g.RL, x - dp);
+                float f = fmaf(b.d1, sbar, a.d1 * g.inv_c_lens);
+                float fp = fmaf(b.d2, sbar, a.d2 * g.inv_c_lens);
+                if (f < 0.0f) lo = x; else hi = x;
+                float xn = fp > 0.0f ? x - f / fp : 0.5f * (lo + hi);
+                if (!(xn > lo && xn < hi)) xn = 0.5f * (lo + hi);
+                conv = fabsf(xn - x) < 1e-6f || hi - lo < 1e-6f;
+                x = xn;
+            }
+            // grazing exit (tissue ray beyond ~80 deg from the lens normal) or no
+            // convergence: solve again in float64
+            float c_t;
+            {
+                float sd, cd;
+                sincosf(x - dp, &sd, &cd);
+                Chord b = chord(pp.y, g.RL, x - dp);
+                c_t = (pp.y * cd - g.RL) / b.len;
+            }
+            if (!conv || c_t < 0.17f) {
+                x = (float)exit_solve_fp64(ep.y, pp.y, g.RL, (double)dp, (double)g.inv_c_lens,
+                                           (double)sbar);
+                ++n_fp64;
+            }
+            ph = ep.x + x;
+            phi[idx] = ph;
+            float sn, cs;
+            sincosf(ph, &sn, &cs);
+            qx = fmaf(g.RL, sn, g.arc_cx);
+            qz = fmaf(g.RL, cs, g.arc_cz);
+            tl = ff_mul(ff_dist(qx, qz, el.x, el.y), fscl);      // lens leg in samples
+        }
+        // Eq. 1 discretised: L * (sbar + mean_k interp(s - sbar)) over N+1 endpoints
+        const ff L = ff_dist(px.x, px.y, qx, qz);
+        const float gx0 = (qx - g.x0) * g.inv_dx, gz0 = (qz - g.z0) * g.inv_dz;
+        const float gdx = (px.x - qx) * g.inv_dx * g.inv_nseg;
+        const float gdz = (px.y - qz) * g.inv_dz * g.inv_nseg;
+        float sum = 0.0f, comp = 0.0f;
+        for (int k = 0; k <= g.nseg; ++k) {
+            const float gx = fmaf((float)k, gdx, gx0), gz = fmaf((float)k, gdz, gz0);
+            const float fx = floorf(gx), fz = floorf(gz);
+            const int i0 = min(max((int)fx, -1), g.nx - 1), j0 = min(max((int)fz, -1), g.nz - 1);
+            float wx[4], wz[4];
+            keys_weights(gx - fx, wx);
+            keys_weights(gz - fz, wz);
+            const float *row = sm + (j0 + 1) * P + (i0 + 1);   // padded node (i0-1, j0-1)
+            float v = 0.0f;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const float *r = row + b * P;
+                float h = wx[0] * r[0];
+                h = fmaf(wx[1], r[1], h);
+                h = fmaf(wx[2], r[2], h);
+                h = fmaf(wx[3], r[3], h);
+                v = fmaf(wz[b], h, v);
+            }
+            // Kahan summation of the N+1 endpoint values
+            const float y = v - comp;
+            const float t = sum + y;
+            comp = (t - sum) - y;
+            sum = t;
+        }
+        const float mean_fs = (sum - comp) * g.inv_nseg1 * g.fs;
+        // one-way delay in samples, shifted by (t_ttp - t0) fs / 2
+        ff U = ff_mul(L, sfs);
+        U = ff_add(U, tl);
+        U = ff_add_f(U, L.hi * mean_fs);
+        U = ff_add(U, off);
+        float n = floorf(U.hi);
+        float fr = (U.hi - n) + U.lo;
+        if (fr < 0.0f) { fr += 1.0f; n -= 1.0f; }
+        if (fr >= 1.0f) { fr -= 1.0f; n += 1.0f; }
+        const int ni = (int)n;
+        // phasor exp(j 2 pi fd (T + t_ttp / 2)) = exp(j 2 pi (rfd (n + fr) + cyc0))
+        ff a = ff_two_prod(g.rfd_hi, n);
+        float cyc = a.hi - rintf(a.hi);
+        cyc += a.lo + g.rfd_lo * n + fmaf(g.rfd_hi, fr, g.cyc0);
+        cyc -= rintf(cyc);
+        float ps, pc;
+        sincospif(2.0f * cyc, &ps, &pc);
+        D[idx] = make_float4(__int_as_float(ni), fr, pc, ps);
+    }
+    // counters
+    for (int o = 16; o > 0; o >>= 1) {
+        n_apod += __shfl_xor_sync(0xffffffffu, n_apod, o);
+        n_fp64 += __shfl_xor_sync(0xffffffffu, n_fp64, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (n_apod) atomicAdd(&scal->n_apod, n_apod);
+        if (n_fp64) atomicAdd(&scal->fp64_solves, n_fp64);
+    }
+}
+
+// T[e][p] in seconds (double) from the stored sample index and fraction
+__global__ void export_delays_kernel(AfGeom g, const float4 *__restrict__ D, double t_shift,
+                                     double inv_fs, double *__restrict__ T,
+                                     uint8_t *__restrict__ apod)
+{
+    long total = (long)g.ne * g.npix;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long)gridDim.x * blockDim.x) {
+        float4 d = D[idx];
+        int n = __float_as_int(d.x);
+        bool on = n != AF_APOD_OFF;
+        if (T) T[idx] = on ? ((double)n + (double)d.y) * inv_fs - t_shift : 0.0;
+        if (apod) apod[idx] = on ? 1 : 0;
+    }
+}
+
+}  // namespace
+
+int delays_blocks_per_sm(size_t smem)
+{
+    int n = 0;
+    cudaFuncSetAttribute(delays_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, delays_kernel, 256, smem);
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_grid_stats(af_plan_t pl, const float *s)
+{
+    grid_stats_kernel<<<1, 1024, 0, pl->stream>>>(pl->g, s, pl->scal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_delays(af_plan_t pl, const float *s)
+{
+    if ((long)pl->g.ne * pl->g.npix == 0) return cudaSuccess;
+    delays_kernel<<<pl->delay_blocks, 256, pl->smem_grid, pl->stream>>>(
+        pl->g, s, pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->have_phi ? 1 : 0,
+        pl->D, pl->scal);
+    cudaError_t err = cudaGetLastError();
+    if (err == cudaSuccess) pl->have_phi = true;
+    return err;
+}
+
+cudaError_t launch_export_delays(af_plan_t pl, double *T, uint8_t *apod)
+{
+    long total = (long)pl->g.ne * pl->g.npix;
+    if (total == 0) return cudaSuccess;
+    // U = (T + (t_ttp - t0) / 2) fs  =>  T = U / fs - (t_ttp - t0) / 2
+    double shift = ((double)pl->g.off_hi + (double)pl->g.off_lo) / (double)pl->g.fs;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 65535) blocks = 65535;
+    export_delays_kernel<<<blocks, 256, 0, pl->stream>>>(pl->g, pl->D, shift, 1.0 / (double)pl->g.fs,
+                                                          T, apod);
+    return cudaGetLastError();
+}

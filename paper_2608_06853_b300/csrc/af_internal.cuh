@@ -1,0 +1,161 @@
+// Internal declarations of the sm_103a autofocus library: device geometry,
+// the plan, float-float helpers and the host-side launchers of each kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "af.h"
+
+// Apodization-off sentinel stored in the integer sample field of a one-way
+// delay entry: any round trip that uses it lands below sample 0 and is
+// skipped by the gather, so h_t h_r = 0 needs no separate mask lookup.
+#define AF_APOD_OFF (-(1 << 29))
+
+// Geometry and scalars every kernel reads (passed by value).
+struct AfGeom {
+    int ne, npix, nsub, W, nb, npair, n_patch, patch_npix;
+    int ns, nx, nz, ng, nseg, pitch;         // pitch = padded grid row length nx + 4
+    int lens_mode, apod_mode;
+    float arc_cx, arc_cz, RL, fnum_inv2, fnum_half;
+    float x0, z0, inv_dx, inv_dz;
+    float inv_c_lens;                        // for the FP64 fallback solve
+    float fs, wd;                            // sample rate, 2 pi fd
+    float fs_clens_hi, fs_clens_lo;          // fs / c_lens as float-float
+    float off_hi, off_lo;                    // (t_ttp - t0) fs / 2 as float-float
+    float rfd_hi, rfd_lo;                    // fd / fs as float-float
+    float cyc0;                              // frac(fd t0 / 2)
+    float rho_thresh;
+    float inv_nseg, inv_nseg1;               // 1/N, 1/(N+1)
+    // regularisation (Eq. 10-11), units of m/s per mm
+    float w1, kx1, kz1, w2, kx2, kz2, hx_mm, hz_mm;
+    float na_inv, nb_inv;                    // 1 / number of difference terms
+    float c_ref, lr, beta1, beta2, eps;
+};
+
+constexpr int kTimingCap = 4096;   // recorded stage launches per timing window
+
+// Plan-owned device scalars.
+struct AfScal {
+    float sbar;          // 1 / c_med, c_med = mean(1/s)  (Sec. III-A)
+    float rtv, rsv;      // Eq. 10, Eq. 11
+    float lcmpe;         // CMPE loss
+    float inv_m;         // 1 / max(1, number of active CMPE terms)
+    int n_active;
+    int numeric_flag;    // set when a slowness is non-positive or non-finite
+    int fp64_solves;     // exit solves that fell back to float64
+    int n_apod;          // apodized (element, pixel) pairs
+};
+
+struct af_plan_s {
+    AfGeom g;
+    cudaStream_t stream;
+    int device, sm_count;
+    size_t smem_grid;    // bytes of the padded slowness grid in shared memory
+    int delay_blocks, rayadj_blocks;
+    // geometry
+    float4 *elem;        // (x, z, cos theta_a, sin theta_a)  theta_a from Eq. 3
+    float2 *elem_pol;    // (polar angle about the arc centre, radius)
+    float2 *pix;         // (x, z)
+    float2 *pix_pol;     // (polar angle, radius)
+    // workspaces
+    float *phi;          // [ne][npix] exit angles
+    float4 *D;           // [ne][npix] {sample index (int bits), fraction, Re P, Im P}
+    float2 *B, *G;       // [nb][npix] images and dL/dB
+    float2 *z;           // [n_patch][npair] CMPE cross terms
+    uint8_t *mask;       // [n_patch][npair]
+    double *patch_sum;   // [n_patch] sum m |arg z|
+    int *patch_cnt;      // [n_patch] sum m
+    float *gdel;         // [ne][npix] dL/dT
+    float *gpart;        // [rayadj_blocks][ng] per-CTA partial gradients
+    AfScal *scal;
+    float *loss_out;     // last caller loss buffer
+    const void *iq;      // last forward's inputs (kept for the adjoint)
+    const float *iq_scale;
+    const float *slowness;
+    int iq_dtype;
+    bool have_phi, have_fwd, have_adj;
+    // stage timing: a ring of (start, stop) event pairs per recorded launch
+    bool timing;
+    int n_rec;
+    int rec_stage[kTimingCap];
+    cudaEvent_t ev[2 * kTimingCap];
+};
+
+// ---- float-float arithmetic (Dekker / Knuth error-free transformations) ----
+struct ff { float hi, lo; };
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b)
+{
+    float s = a + b;
+    float bb = s - a;
+    float err = (a - (s - bb)) + (b - bb);
+    return {s, err};
+}
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b)   // |a| >= |b|
+{
+    float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff ff_two_prod(float a, float b)
+{
+    float p = a * b;
+    return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    ff s = ff_two_sum(a.hi, b.hi);
+    float lo = s.lo + a.lo + b.lo;
+    return ff_fast_two_sum(s.hi, lo);
+}
+__device__ __forceinline__ ff ff_add_f(ff a, float b)
+{
+    ff s = ff_two_sum(a.hi, b);
+    return ff_fast_two_sum(s.hi, s.lo + a.lo);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    ff p = ff_two_prod(a.hi, b.hi);
+    float lo = p.lo + fmaf(a.hi, b.lo, a.lo * b.hi);
+    return ff_fast_two_sum(p.hi, lo);
+}
+// sqrt(a) for a > 0 (one Newton correction of the float32 root)
+__device__ __forceinline__ ff ff_sqrt(ff a)
+{
+    float r = sqrtf(a.hi);
+    float e = fmaf(-r, r, a.hi) + a.lo;
+    return ff_fast_two_sum(r, e / (2.0f * r));
+}
+// |(ax - bx, az - bz)| with float32 inputs, exact differences
+__device__ __forceinline__ ff ff_dist(float ax, float az, float bx, float bz)
+{
+    ff dx = ff_two_sum(ax, -bx), dz = ff_two_sum(az, -bz);
+    ff x2 = ff_two_prod(dx.hi, dx.hi);
+    x2.lo = fmaf(2.0f * dx.hi, dx.lo, x2.lo);
+    ff z2 = ff_two_prod(dz.hi, dz.hi);
+    z2.lo = fmaf(2.0f * dz.hi, dz.lo, z2.lo);
+    return ff_sqrt(ff_add(x2, z2));
+}
+
+// Keys cubic-convolution weights (a = -1/2) for taps -1, 0, 1, 2 at fraction t
+__device__ __forceinline__ void keys_weights(float t, float w[4])
+{
+    float t2 = t * t, t3 = t2 * t;
+    w[0] = -0.5f * t3 + t2 - 0.5f * t;
+    w[1] = 1.5f * t3 - 2.5f * t2 + 1.0f;
+    w[2] = -1.5f * t3 + 2.0f * t2 + 0.5f * t;
+    w[3] = 0.5f * t3 - 0.5f * t2;
+}
+
+// ---- launchers (each in its own .cu file) ----
+cudaError_t launch_grid_stats(af_plan_t pl, const float *s);
+cudaError_t launch_delays(af_plan_t pl, const float *s);
+cudaError_t launch_das_forward(af_plan_t pl);
+cudaError_t launch_cmpe_forward(af_plan_t pl, float *loss);
+cudaError_t launch_cmpe_backward(af_plan_t pl);
+cudaError_t launch_das_adjoint(af_plan_t pl);
+cudaError_t launch_ray_adjoint(af_plan_t pl, const float *s, float *grad);
+cudaError_t launch_adam(af_plan_t pl, const float *grad, float *s, float *m, float *v, int step);
+cudaError_t launch_export_delays(af_plan_t pl, double *T, uint8_t *apod);
+int delays_blocks_per_sm(size_t smem);
+int rayadj_blocks_per_sm(size_t smem);

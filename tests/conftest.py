@@ -17,3 +17,14 @@ def pytest_configure(config):
 def tiny():
     import synth
     return synth.config_tiny()
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built():
+    """Compile the CUDA library, the oracle and the input generator if stale."""
+    from paper_2608_06853_b300 import build as b
+    import oracle
+    import synth
+    b.build()
+    oracle.build()
+    synth.build()

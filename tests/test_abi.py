@@ -1,0 +1,103 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry point
+declared in include/af.h, and its host-side validation returns the documented
+status codes.  No compute call is made here."""
+import ctypes
+import dataclasses
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2608_06853_b300 as af
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(af_[a-z_]+)\s*\(", src))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = af.load()
+    names = declared_symbols()
+    assert {"af_plan", "af_forward", "af_adjoint", "af_step"} <= names
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    assert set(af._SIGNATURES) == names
+
+
+def test_status_strings():
+    lib = af.load()
+    assert lib.af_status_string(af.AF_OK) == b"AF_OK"
+    assert lib.af_status_string(af.AF_ERR_STATE) == b"AF_ERR_STATE"
+
+
+@pytest.mark.parametrize("maker", [synth.config_tiny, synth.config_full])
+def test_valid_configs_pass_host_validation(maker):
+    p = maker()
+    assert af.check_config(p) == af.AF_OK
+    for dt in (af.AF_IQ_BF16, af.AF_IQ_F16):
+        assert af.check_config(p, dt) == af.AF_OK
+    c, keep = af.make_config(p)
+    nbytes = ctypes.c_size_t()
+    assert af.load().af_workspace_bytes(ctypes.byref(c), ctypes.byref(nbytes)) == af.AF_OK
+    assert nbytes.value > 0
+
+
+def test_invalid_configs_are_rejected_with_codes():
+    p = synth.config_tiny()
+    R = dataclasses.replace
+    lib = af.load()
+    assert af.check_config(R(p, sub_width=3)) == af.AF_ERR_SHAPE
+    assert af.check_config(R(p, sub_width=32)) == af.AF_ERR_UNSUPPORTED   # width 32 not built
+    assert af.check_config(p, iq_dtype=7) == af.AF_ERR_DTYPE
+    assert af.check_config(R(p, fnum=0.0)) == af.AF_ERR_ARG
+    assert af.check_config(R(p, nseg=0)) == af.AF_ERR_ARG
+    assert af.check_config(R(p, nx=1)) == af.AF_ERR_SHAPE
+    assert af.check_config(R(p, nx=400, nz=400)) == af.AF_ERR_UNSUPPORTED
+    assert af.check_config(R(p, ns=1)) == af.AF_ERR_SHAPE
+    assert af.check_config(R(p, fs=-1.0)) == af.AF_ERR_ARG
+    assert af.check_config(R(p, lr=float("nan"))) == af.AF_ERR_ARG
+    bad = p.pix_x.copy()
+    bad[3] = 1.0                                  # far outside the grid
+    assert af.check_config(R(p, pix_x=bad)) == af.AF_ERR_ARG
+    assert b"outside" in lib.af_last_error()
+    inside_lens = p.pix_z.copy()
+    inside_lens[0] = p.arc_cz + 0.5 * p.lens_radius
+    inside_lens_x = p.pix_x.copy()
+    inside_lens_x[0] = p.arc_cx
+    assert af.check_config(R(p, pix_x=inside_lens_x, pix_z=inside_lens)) == af.AF_ERR_ARG
+    assert af.check_config(R(p, c_lens=0.0)) == af.AF_ERR_ARG
+    assert af.check_config(R(p, beta1=1.0)) == af.AF_ERR_ARG
+    assert lib.af_check_config(None) == af.AF_ERR_ARG
+
+
+def test_degenerate_but_valid_shapes():
+    p = synth.config_tiny()
+    R = dataclasses.replace
+    # no patches: loss is the regulariser only
+    assert af.check_config(R(p, n_patch=0, pix_x=np.zeros(0), pix_z=np.zeros(0))) == af.AF_OK
+    # fewer than three subapertures: no common-midpoint pairs
+    assert af.check_config(R(p, sub_width=16)) == af.AF_OK
+    # straight-ray model (no lens)
+    assert af.check_config(R(p, lens_mode=af.AF_LENS_NONE)) == af.AF_OK
+
+
+def test_plan_without_gpu_fails_cleanly():
+    """Without a CUDA device af_plan reports AF_ERR_CUDA instead of crashing."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    c, keep = af.make_config(synth.config_tiny())
+    h = ctypes.c_void_p()
+    st = af.load().af_plan(ctypes.byref(c), None, ctypes.byref(h))
+    assert st == af.AF_ERR_CUDA
+    assert not h.value

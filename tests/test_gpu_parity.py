@@ -1,0 +1,357 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Same seeded inputs on both sides.  Where floating point takes a discrete
+decision (apodization bit, CMPE correlation mask), the GPU's decision is
+injected into the oracle and every disagreement is checked to lie within
+rounding distance of the threshold.  Tolerances (stated per test):
+delays <= 0.1 ns absolute, images relative L2 <= 1e-4, loss relative <= 1e-4,
+gradient relative L2 <= 1e-3.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import paper_2608_06853_b300 as af  # noqa: E402
+import synth  # noqa: E402
+
+DELAY_TOL = 1e-10       # s
+IMG_TOL = 1e-4          # relative L2
+LOSS_TOL = 1e-4         # relative
+GRAD_TOL = 1e-3         # relative L2
+
+
+def rel_l2(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def smooth_speed(p, seed, amp=25.0):
+    """A smooth random speed map around 1540 m/s (float32 slowness)."""
+    rng = np.random.default_rng(seed)
+    f = rng.standard_normal((p.nz, p.nx))
+    # separable [1 2 1]^3 smoothing
+    for _ in range(3):
+        f = 0.25 * (np.roll(f, 1, 0) + 2 * f + np.roll(f, -1, 0))
+        f = 0.25 * (np.roll(f, 1, 1) + 2 * f + np.roll(f, -1, 1))
+    f /= np.abs(f).max()
+    return (1.0 / (1540.0 + amp * f)).astype(np.float32)
+
+
+def layered_speed(p):
+    return (1.0 / p.true_speed_grid()).astype(np.float32)
+
+
+class Run:
+    """One forward + adjoint on the GPU with everything copied back to the host."""
+
+    def __init__(self, p, psi, s, iq_dtype=af.AF_IQ_C64):
+        dev = torch.device("cuda")
+        self.plan = af.Plan(p, iq_dtype=iq_dtype)
+        if iq_dtype == af.AF_IQ_C64:
+            self.iq = torch.from_numpy(psi).to(dev)
+            self.scale = None
+        else:
+            x = torch.from_numpy(psi).to(dev)
+            sc = torch.view_as_real(x).abs().amax(dim=(1, 2, 3)).clamp_min(1e-30)
+            q = torch.view_as_real(x) / sc[:, None, None, None]
+            q = q.to(torch.bfloat16 if iq_dtype == af.AF_IQ_BF16 else torch.float16).contiguous()
+            self.iq, self.scale = q, sc.float().contiguous()
+        self.s = torch.from_numpy(s).to(dev)
+        self.loss = torch.zeros(4, device=dev)
+        self.grad = torch.zeros_like(self.s)
+        self.plan.af_forward(self.iq, self.s, self.loss, self.scale)
+        self.plan.af_adjoint(self.grad)
+        torch.cuda.synchronize()
+        T, a = self.plan.delays()
+        self.T, self.apod = T.cpu().numpy(), a.cpu().numpy()
+        self.phi = self.plan.exit_angles().cpu().numpy().astype(np.float64)
+        self.B = self.plan.images().cpu().numpy().astype(np.complex128)
+        z, m, n = self.plan.cmpe()
+        self.z, self.mask, self.n_active = z.cpu().numpy(), m.cpu().numpy(), n
+        self.G = self.plan.image_grad().cpu().numpy().astype(np.complex128)
+        self.gdel = self.plan.delay_grad().cpu().numpy().astype(np.float64)
+        self.L = self.loss.cpu().numpy().astype(np.float64)
+        self.dLds = self.grad.cpu().numpy().astype(np.float64)
+        self.counters = self.plan.counters()
+
+
+def check_apod_disagreements(o, p, run):
+    """Apodization bits may differ only where |x'| is within rounding of the cone edge."""
+    _, apod_or, _ = o.delays(np.full((p.nz, p.nx), 1 / 1540.0))
+    diff = np.argwhere(apod_or != run.apod)
+    th = o.element_angles()
+    for e, k in diff[:200]:
+        c, s_ = math.cos(th[e]), math.sin(th[e])
+        dx, dz = p.pix_x[k] - p.elem_x[e], p.pix_z[k] - p.elem_z[e]
+        xp, zp = c * dx - s_ * dz, s_ * dx + c * dz
+        lim = zp / (2 * p.fnum) if p.apod_mode == 0 else 0.5 * p.fnum * zp
+        assert abs(abs(xp) - lim) < 1e-6 * max(abs(zp), 1e-3), (e, k)
+    return len(diff)
+
+
+def check_mask_disagreements(rho_or, mask_gpu, thresh):
+    diff = rho_or.ravel()[(rho_or >= thresh).ravel() != (mask_gpu.ravel() == 1)]
+    assert np.all(np.abs(diff - thresh) < 1e-4), diff
+    return diff.size
+
+
+# ------------------------------------------------------------------ fixtures
+@pytest.fixture(scope="module")
+def tiny_case():
+    p = synth.config_tiny()
+    psi = synth.simulate(p, 2000, seed=20261202)
+    return p, psi
+
+
+def full_parity(p, psi, s, iq_dtype=af.AF_IQ_C64):
+    run = Run(p, psi, s, iq_dtype)
+    o = oracle.Oracle(p)
+    sd = s.astype(np.float64)
+    T, apod, phi = o.delays(sd, apod_in=run.apod)
+    parts, g, mask, M = o.loss_grad(psi, sd, apod_in=run.apod, mask_in=run.mask)
+    B = o.das(psi, T, run.apod)
+    _, z, rho, _, _ = o.cmpe(B)
+    return run, o, dict(T=T, phi=phi, parts=parts, grad=g, B=B, z=z, rho=rho, M=M)
+
+
+# ------------------------------------------------------------------ tests
+@pytest.mark.parametrize("speed", ["uniform", "smooth", "layered"])
+def test_tiny_forward_adjoint_parity(tiny_case, speed):
+    p, psi = tiny_case
+    s = {"uniform": p.initial_slowness(), "smooth": smooth_speed(p, 1),
+         "layered": layered_speed(p)}[speed]
+    run, o, ref = full_parity(p, psi, s)
+    on = run.apod == 1
+    assert on.sum() > 0
+    # one-way delays (0.1 ns) and exit angles
+    err_T = np.abs(run.T - ref["T"])[on]
+    assert err_T.max() <= DELAY_TOL, err_T.max()
+    assert np.abs(run.phi - ref["phi"])[on].max() < 2e-5
+    # images
+    assert rel_l2(run.B, ref["B"]) <= IMG_TOL
+    # CMPE decisions and loss
+    check_mask_disagreements(ref["rho"], run.mask, p.rho_thresh)
+    assert run.n_active == ref["M"]
+    for k in range(4):
+        assert abs(run.L[k] - ref["parts"][k]) <= LOSS_TOL * max(abs(ref["parts"][k]), 1e-12), k
+    # gradient
+    assert rel_l2(run.dLds, ref["grad"]) <= GRAD_TOL
+    check_apod_disagreements(o, p, run)
+
+
+def test_tiny_stagewise_adjoint(tiny_case):
+    """Each adjoint stage on the GPU's own inputs: CMPE -> dL/dB, DAS -> dL/dT, rays -> dL/ds."""
+    p, psi = tiny_case
+    s = smooth_speed(p, 2)
+    run = Run(p, psi, s)
+    o = oracle.Oracle(p)
+    G = o.cmpe_adjoint(run.B, run.z.astype(np.complex128), run.mask, run.n_active)
+    assert rel_l2(run.G, G) <= 1e-4
+    gT = o.das_adjoint(psi, run.T, run.apod, run.G)
+    assert rel_l2(run.gdel, gT) <= 1e-4
+    ray = o.ray_adjoint(s.astype(np.float64), run.phi, run.apod, run.gdel)
+    reg = o.regularizer_grad(s.astype(np.float64))
+    assert rel_l2(run.dLds, ray + reg) <= 1e-4
+
+
+def test_adam_step_parity(tiny_case):
+    p, psi = tiny_case
+    s = smooth_speed(p, 3)
+    run = Run(p, psi, s)
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(5)
+    m0 = (1e-3 * rng.standard_normal(s.shape)).astype(np.float32)
+    v0 = (1e-6 * rng.random(s.shape)).astype(np.float32)
+    sg, mg, vg = (torch.from_numpy(x.copy()).to(dev) for x in (s, m0, v0))
+    run.plan.af_step(run.grad, sg, mg, vg, 3)
+    o = oracle.Oracle(p)
+    s1, m1, v1 = o.adam(s, run.dLds, m0, v0, 3, p.lr, p.beta1, p.beta2, p.eps, p.c_ref)
+    np.testing.assert_allclose(sg.cpu().numpy(), s1, rtol=1e-6)
+    np.testing.assert_allclose(mg.cpu().numpy(), m1, rtol=1e-5, atol=1e-12)
+    np.testing.assert_allclose(vg.cpu().numpy(), v1, rtol=1e-5, atol=1e-18)
+
+
+def test_ragged_and_variant_shapes():
+    """Pixel count not a multiple of 32, no lens, sub_width 2 and 8, printed Eq. 4."""
+    cases = [
+        dict(n_ang=3, n_rad=3, patch_w=3),                      # 81 pixels
+        dict(n_ang=5, n_rad=2, patch_w=5, lens_mode=1),         # straight rays, 250 pixels
+        dict(n_ang=2, n_rad=3, patch_w=3, sub_width=2),         # 16 subapertures
+        dict(n_ang=2, n_rad=2, patch_w=4, sub_width=8),         # 4 subapertures
+        dict(n_ang=3, n_rad=2, patch_w=3, apod_mode=1, fnum=3.0),
+    ]
+    for kw in cases:
+        p = synth.config_tiny(**kw)
+        psi = synth.simulate(p, 500, seed=7)
+        run, o, ref = full_parity(p, psi, smooth_speed(p, 4))
+        on = run.apod == 1
+        if on.any():
+            assert np.abs(run.T - ref["T"])[on].max() <= DELAY_TOL, kw
+        assert rel_l2(run.B, ref["B"]) <= IMG_TOL, kw
+        assert abs(run.L[0] - ref["parts"][0]) <= LOSS_TOL * max(abs(ref["parts"][0]), 1e-12), kw
+        assert rel_l2(run.dLds, ref["grad"]) <= GRAD_TOL, kw
+
+
+def test_degenerate_cases():
+    """No patches: loss and gradient are the regulariser's; < 3 subapertures: no CMPE terms."""
+    base = synth.config_tiny(n_ang=2, n_rad=2, patch_w=3)
+    psi = synth.simulate(base, 200, seed=8)
+    s = smooth_speed(base, 5, amp=60.0)
+    empty = dataclasses.replace(base, n_patch=0, pix_x=np.zeros(0), pix_z=np.zeros(0))
+    run = Run(empty, psi, s)
+    o = oracle.Oracle(empty)
+    rtv, rsv = o.regularizers(s.astype(np.float64))
+    assert run.L[1] == 0.0
+    assert run.L[0] == pytest.approx(empty.w1 * rtv + empty.w2 * rsv, rel=1e-4)
+    assert rel_l2(run.dLds, o.regularizer_grad(s.astype(np.float64))) <= 1e-4
+    few = dataclasses.replace(base, sub_width=16)
+    run2 = Run(few, psi, s)
+    assert run2.L[1] == 0.0 and run2.counters["npair"] == 0
+
+
+@pytest.mark.parametrize("dtype", [af.AF_IQ_BF16, af.AF_IQ_F16])
+def test_half_precision_storage_error_is_small(tiny_case, dtype):
+    """16-bit channel data with a per-transmit scale: error vs the FP64 oracle is reported
+    and bounded by the storage rounding (bf16: 2^-8, f16: 2^-11 relative)."""
+    p, psi = tiny_case
+    s = smooth_speed(p, 6)
+    run, o, ref = full_parity(p, psi, s, iq_dtype=dtype)
+    e_img = rel_l2(run.B, ref["B"])
+    e_loss = abs(run.L[0] - ref["parts"][0]) / abs(ref["parts"][0])
+    bound = 2 ** -8 if dtype == af.AF_IQ_BF16 else 2 ** -11
+    print(f"dtype {dtype}: image rel L2 {e_img:.2e}, loss rel {e_loss:.2e}")
+    assert e_img < bound
+    assert e_loss < 20 * bound
+
+
+def test_autograd_function_matches_adjoint(tiny_case):
+    p, psi = tiny_case
+    dev = torch.device("cuda")
+    plan = af.Plan(p)
+    iq = torch.from_numpy(psi).to(dev)
+    s = torch.from_numpy(smooth_speed(p, 7)).to(dev).requires_grad_(True)
+    L = af.AutofocusLoss.apply(s, plan, iq, None)
+    (2.0 * L).backward()
+    loss = torch.zeros(4, device=dev)
+    g = torch.zeros_like(s)
+    plan.af_forward(iq, s.detach(), loss, None)
+    plan.af_adjoint(g)
+    torch.testing.assert_close(s.grad, 2.0 * g)
+    assert float(L) == pytest.approx(float(loss[0]))
+
+
+def test_error_statuses():
+    p = synth.config_tiny(n_ang=2, n_rad=2, patch_w=3)
+    dev = torch.device("cuda")
+    plan = af.Plan(p)
+    g = torch.zeros((p.nz, p.nx), device=dev)
+    with pytest.raises(af.AfError) as ei:
+        plan.af_adjoint(g)
+    assert ei.value.status == af.AF_ERR_STATE
+    iq = torch.zeros((p.ne, p.ne, p.ns), dtype=torch.complex64, device=dev)
+    s = torch.full((p.nz, p.nx), 1 / 1540.0, device=dev)
+    s[3, 4] = float("nan")
+    loss = torch.zeros(4, device=dev)
+    plan.af_forward(iq, s, loss)
+    assert plan.af_sync_status() == af.AF_ERR_NUMERIC
+    assert plan.af_sync_status() == af.AF_OK          # flag cleared once reported
+    plan16 = af.Plan(p, iq_dtype=af.AF_IQ_BF16)
+    with pytest.raises(af.AfError) as ei:
+        plan16.af_forward(iq, s, loss, None)
+    assert ei.value.status == af.AF_ERR_DTYPE
+
+
+def test_autofocus_iterations_reduce_loss_and_error(tiny_case):
+    """100 Adam iterations (Table II phantom C5-2v column) on the two-layer medium lower
+    the CMPE and move the speed map toward the true one (Eq. 13 MAE)."""
+    p, psi = tiny_case
+    dev = torch.device("cuda")
+    plan = af.Plan(p)
+    iq = torch.from_numpy(psi).to(dev)
+    s = torch.from_numpy(p.initial_slowness()).to(dev)
+    m, v, g = torch.zeros_like(s), torch.zeros_like(s), torch.zeros_like(s)
+    loss = torch.zeros(4, device=dev)
+    truth = p.true_speed_grid()
+    region = np.zeros_like(truth, bool)
+    # nodes inside the imaged sector only
+    X, Z = np.meshgrid(p.x0 + p.dx * np.arange(p.nx), p.z0 + p.dz * np.arange(p.nz))
+    ang = np.arctan2(X - p.arc_cx, Z - p.arc_cz)
+    rad = np.hypot(X - p.arc_cx, Z - p.arc_cz) - p.lens_radius
+    region = (np.abs(ang) < p.sector_half_angle) & (rad > 8e-3) & (rad < 50e-3)
+    mae0 = np.abs(1540.0 - truth[region]).mean()
+    first = None
+    for it in range(1, 101):
+        plan.af_iterate(iq, s, g, m, v, it, loss)
+        if it == 1:
+            first = float(loss[1])
+    torch.cuda.synchronize()
+    last = float(loss[1])
+    c = 1.0 / s.cpu().numpy()
+    mae = np.abs(c - truth)[region].mean()
+    print(f"CMPE {first:.4f} -> {last:.4f}; MAE {mae0:.1f} -> {mae:.1f} m/s")
+    assert last < first
+    assert mae < mae0
+
+
+# ------------------------------------------------------------------ full size
+@pytest.fixture(scope="module")
+def full_case():
+    p = synth.config_full()
+    psi = synth.simulate(p, 150_000, seed=20261203)
+    return p, psi
+
+
+def test_full_size_sampled_parity(full_case):
+    """128 x 128 x 3072 acquisition, 400 patches of 9 x 9, 128^2 grid, in the launch
+    configuration of the benchmark.  The oracle checks sampled outputs: delays of random
+    (element, pixel) pairs, images, CMPE terms and dL/dT of sampled patches, and every
+    adjoint stage on the GPU's own intermediate values."""
+    p, psi = full_case
+    s = layered_speed(p)
+    run = Run(p, psi, s)
+    o_full = oracle.Oracle(p)
+    sd = s.astype(np.float64)
+    sbar = 1.0 / o_full.mean_speed(sd)
+    rng = np.random.default_rng(11)
+    # delays of 3000 random apodized pairs
+    ee, kk = np.nonzero(run.apod)
+    pick = rng.choice(len(ee), 3000, replace=False)
+    errs = []
+    for q in pick:
+        e, k = int(ee[q]), int(kk[q])
+        phi, tl, qx, qz, _ = o_full.exit_point(e, p.pix_x[k], p.pix_z[k], sbar)
+        T = tl + o_full.ray_time(sd, qx, qz, p.pix_x[k], p.pix_z[k])
+        errs.append(abs(T - run.T[e, k]))
+    assert max(errs) <= DELAY_TOL, max(errs)
+    # sampled patches as a sub-problem: per-pixel images and per-patch CMPE terms
+    patches = np.sort(rng.choice(p.n_patch, 6, replace=False))
+    pix = np.concatenate([np.arange(P * p.patch_npix, (P + 1) * p.patch_npix) for P in patches])
+    sub = dataclasses.replace(p, n_patch=len(patches), pix_x=p.pix_x[pix], pix_z=p.pix_z[pix])
+    o = oracle.Oracle(sub)
+    T, _, _ = o.delays(sd, apod_in=run.apod[:, pix])
+    B = o.das(psi, T, run.apod[:, pix])
+    assert rel_l2(run.B[:, pix], B) <= IMG_TOL
+    _, z, rho, _, _ = o.cmpe(B)
+    np.testing.assert_allclose(run.z[patches], z, rtol=1e-4, atol=1e-4 * np.abs(z).max())
+    check_mask_disagreements(rho, run.mask[patches], p.rho_thresh)
+    # adjoint stages on the GPU's own inputs
+    G = o_full.cmpe_adjoint(run.B, run.z.astype(np.complex128), run.mask, run.n_active)
+    assert rel_l2(run.G, G) <= 1e-4
+    gT = o.das_adjoint(psi, run.T[:, pix], run.apod[:, pix], run.G[:, pix])
+    assert rel_l2(run.gdel[:, pix], gT) <= 1e-4
+    ray = o_full.ray_adjoint(sd, run.phi, run.apod, run.gdel)
+    reg = o_full.regularizer_grad(sd)
+    assert rel_l2(run.dLds, ray + reg) <= 1e-4
+    # loss assembled from the oracle's terms with the GPU mask
+    L_or = float(np.sum(np.abs(np.angle(run.z.astype(np.complex128)))[run.mask == 1])) / max(run.n_active, 1)
+    assert abs(run.L[1] - L_or) <= LOSS_TOL * L_or
+    rtv, rsv = o_full.regularizers(sd)
+    assert run.L[2] == pytest.approx(rtv, rel=1e-4)
+    assert run.L[3] == pytest.approx(rsv, rel=1e-4, abs=1e-9)
