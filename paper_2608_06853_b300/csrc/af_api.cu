@@ -279,6 +279,8 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
     g.lr = (float)c->lr;
     g.beta1 = (float)c->beta1;
     g.beta2 = (float)c->beta2;
+    g.omb1 = (float)(1.0 - c->beta1);
+    g.omb2 = (float)(1.0 - c->beta2);
     g.eps = (float)c->eps;
 
     // host geometry: Eq. 3 orientation (end elements extrapolated), polar coordinates
@@ -421,19 +423,23 @@ af_status af_get_delays(af_plan_t pl, double *T, uint8_t *apod)
 
 af_status af_get_exit_angles(af_plan_t pl, float *phi)
 {
-    if (!pl || !phi) return fail(AF_ERR_ARG, "NULL argument");
+    if (!pl) return fail(AF_ERR_ARG, "plan is NULL");
     if (!pl->have_fwd) return fail(AF_ERR_STATE, "no forward pass yet");
-    AF_CUDA(cudaMemcpyAsync(phi, pl->phi, (size_t)pl->g.ne * pl->g.npix * sizeof(float),
-                            cudaMemcpyDeviceToDevice, pl->stream));
+    const size_t n = (size_t)pl->g.ne * pl->g.npix;
+    if (n == 0) return AF_OK;
+    if (!phi) return fail(AF_ERR_ARG, "d_phi is NULL");
+    AF_CUDA(cudaMemcpyAsync(phi, pl->phi, n * sizeof(float), cudaMemcpyDeviceToDevice, pl->stream));
     return AF_OK;
 }
 
 af_status af_get_images(af_plan_t pl, float *B)
 {
-    if (!pl || !B) return fail(AF_ERR_ARG, "NULL argument");
+    if (!pl) return fail(AF_ERR_ARG, "plan is NULL");
     if (!pl->have_fwd) return fail(AF_ERR_STATE, "no forward pass yet");
-    AF_CUDA(cudaMemcpyAsync(B, pl->B, (size_t)pl->g.nb * pl->g.npix * sizeof(float2),
-                            cudaMemcpyDeviceToDevice, pl->stream));
+    const size_t n = (size_t)pl->g.nb * pl->g.npix;
+    if (n == 0) return AF_OK;
+    if (!B) return fail(AF_ERR_ARG, "d_B is NULL");
+    AF_CUDA(cudaMemcpyAsync(B, pl->B, n * sizeof(float2), cudaMemcpyDeviceToDevice, pl->stream));
     return AF_OK;
 }
 
@@ -453,19 +459,23 @@ af_status af_get_cmpe(af_plan_t pl, float *z, uint8_t *mask, int *n_active)
 
 af_status af_get_image_grad(af_plan_t pl, float *G)
 {
-    if (!pl || !G) return fail(AF_ERR_ARG, "NULL argument");
+    if (!pl) return fail(AF_ERR_ARG, "plan is NULL");
     if (!pl->have_adj) return fail(AF_ERR_STATE, "no adjoint pass yet");
-    AF_CUDA(cudaMemcpyAsync(G, pl->G, (size_t)pl->g.nb * pl->g.npix * sizeof(float2),
-                            cudaMemcpyDeviceToDevice, pl->stream));
+    const size_t n = (size_t)pl->g.nb * pl->g.npix;
+    if (n == 0) return AF_OK;
+    if (!G) return fail(AF_ERR_ARG, "d_G is NULL");
+    AF_CUDA(cudaMemcpyAsync(G, pl->G, n * sizeof(float2), cudaMemcpyDeviceToDevice, pl->stream));
     return AF_OK;
 }
 
 af_status af_get_delay_grad(af_plan_t pl, float *gd)
 {
-    if (!pl || !gd) return fail(AF_ERR_ARG, "NULL argument");
+    if (!pl) return fail(AF_ERR_ARG, "plan is NULL");
     if (!pl->have_adj) return fail(AF_ERR_STATE, "no adjoint pass yet");
-    AF_CUDA(cudaMemcpyAsync(gd, pl->gdel, (size_t)pl->g.ne * pl->g.npix * sizeof(float),
-                            cudaMemcpyDeviceToDevice, pl->stream));
+    const size_t n = (size_t)pl->g.ne * pl->g.npix;
+    if (n == 0) return AF_OK;
+    if (!gd) return fail(AF_ERR_ARG, "d_g is NULL");
+    AF_CUDA(cudaMemcpyAsync(gd, pl->gdel, n * sizeof(float), cudaMemcpyDeviceToDevice, pl->stream));
     return AF_OK;
 }
 

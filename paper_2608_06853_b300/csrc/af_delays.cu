@@ -298,7 +298,7 @@ cudaError_t launch_export_delays(af_plan_t pl, double *T, uint8_t *apod)
     long total = (long)pl->g.ne * pl->g.npix;
     if (total == 0) return cudaSuccess;
     // U = (T + (t_ttp - t0) / 2) fs  =>  T = U / fs - (t_ttp - t0) / 2
-    double shift = ((double)pl->g.off_hi + (double)pl->g.off_lo) / (double)pl->g.fs;
+    const double shift = ((double)pl->g.off_hi + (double)pl->g.off_lo) / (double)pl->g.fs;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 65535) blocks = 65535;
     export_delays_kernel<<<blocks, 256, 0, pl->stream>>>(pl->g, pl->D, shift, 1.0 / (double)pl->g.fs,

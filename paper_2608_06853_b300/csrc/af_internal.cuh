@@ -30,7 +30,7 @@ struct AfGeom {
     // regularisation (Eq. 10-11), units of m/s per mm
     float w1, kx1, kz1, w2, kx2, kz2, hx_mm, hz_mm;
     float na_inv, nb_inv;                    // 1 / number of difference terms
-    float c_ref, lr, beta1, beta2, eps;
+    float c_ref, lr, beta1, beta2, omb1, omb2, eps;   // omb = 1 - beta, formed in double
 };
 
 constexpr int kTimingCap = 4096;   // recorded stage launches per timing window

@@ -125,8 +125,8 @@ __global__ void __launch_bounds__(256) adam_kernel(AfGeom g, const float *__rest
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.ng) return;
     const float gu = grad[k] / g.c_ref;
-    const float mk = fmaf(g.beta1, m[k], (1.0f - g.beta1) * gu);
-    const float vk = fmaf(g.beta2, v[k], (1.0f - g.beta2) * gu * gu);
+    const float mk = fmaf(g.beta1, m[k], g.omb1 * gu);
+    const float vk = fmaf(g.beta2, v[k], g.omb2 * gu * gu);
     m[k] = mk;
     v[k] = vk;
     const float u = s[k] * g.c_ref - g.lr * (mk / bc1) / (sqrtf(vk / bc2) + g.eps);
