@@ -238,6 +238,7 @@ def run_ours(args, rank, world, local_rank):
     ms = e0.elapsed_time(e1)
     stages = plan.stage_times()
     plan.set_timing(False)
+    counters = plan.counters()
     clk = clocks.stop() if clocks else None
     t = torch.tensor([ms], device=dev)
     if world > 1:
@@ -305,6 +306,7 @@ def run_ours(args, rank, world, local_rank):
         "hbm_gbs_algorithmic": it_bytes / (ms_max / args.steps * 1e-3) / 1e9,
         "roofline": roof,
         "loss": final_loss,
+        "counters": counters,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "iterations/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h),

@@ -51,9 +51,13 @@ long long n_pairs(const af_config *c)
     return n >= 3 ? (long long)(n - 1) * (n - 2) : 0;
 }
 
+// padded row length: two edge nodes on each side, rounded up to an odd number
+// of floats so that successive rows start in different shared-memory banks
+int padded_pitch(int nx) { return (nx + 4) | 1; }
+
 size_t padded_grid_bytes(const af_config *c)
 {
-    return (size_t)(c->nx + 4) * (size_t)(c->nz + 4) * sizeof(float);
+    return (size_t)padded_pitch(c->nx) * (size_t)(c->nz + 4) * sizeof(float);
 }
 
 constexpr size_t kMaxGridSmem = 200 * 1024;
@@ -236,7 +240,7 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
     g.nz = c->nz;
     g.ng = c->nx * c->nz;
     g.nseg = c->nseg;
-    g.pitch = c->nx + 4;
+    g.pitch = padded_pitch(c->nx);
     g.lens_mode = c->lens_mode;
     g.apod_mode = c->apod_mode;
     g.arc_cx = (float)c->arc_cx;

@@ -120,7 +120,6 @@ __global__ void __launch_bounds__(256, 3) das_adjoint_kernel(AfGeom g, const voi
             }
             for (int i = 0; i < g.nsub; ++i) {
                 const float2 Gv = G[(long)(i * g.nsub + j) * g.npix + p];
-                if (Gv.x == 0.0f && Gv.y == 0.0f) continue;
                 for (int tt = 0; tt < W; ++tt) {
                     const int t = i * W + tt;
                     const float4 dt = D[(long)t * g.npix + p];

@@ -15,7 +15,7 @@
 // Geometry and scalars every kernel reads (passed by value).
 struct AfGeom {
     int ne, npix, nsub, W, nb, npair, n_patch, patch_npix;
-    int ns, nx, nz, ng, nseg, pitch;         // pitch = padded grid row length nx + 4
+    int ns, nx, nz, ng, nseg, pitch;         // pitch = padded grid row length (>= nx + 4, odd)
     int lens_mode, apod_mode;
     float arc_cx, arc_cz, RL, fnum_inv2, fnum_half;
     float x0, z0, inv_dx, inv_dz;

@@ -7,11 +7,20 @@
 // padded copy of the grid in shared memory (shared-memory atomics only), folds
 // the padding back onto the edge nodes and writes one partial grid; a second
 // kernel sums the partials in a fixed order and adds the regulariser gradient.
+// The padded row pitch is odd, so consecutive grid rows start in different
+// shared-memory banks.
 #include <math.h>
 
 #include "af_internal.cuh"
 
 namespace {
+
+// Warp-cooperative scatter.  A warp takes 32 consecutive rays (element e,
+// pixels p..p+31), compacts the ones with a non-zero dL/dT into a per-warp
+// table, then walks their (N+1) points with lane = consecutive point index, so
+// the 16 taps of one atomic instruction land on 32 different stencils along a
+// ray (distinct addresses; the odd row pitch spreads them over the banks).
+constexpr int kRayWarps = 8;
 
 __global__ void __launch_bounds__(256) ray_adjoint_kernel(AfGeom g, const float4 *__restrict__ elem,
                                                           const float2 *__restrict__ pix,
@@ -20,33 +29,56 @@ __global__ void __launch_bounds__(256) ray_adjoint_kernel(AfGeom g, const float4
                                                           float *__restrict__ gpart)
 {
     extern __shared__ float acc[];
+    __shared__ float4 rays[kRayWarps][32];      // (gx0, gz0, gdx, gdz)
+    __shared__ float rayc[kRayWarps][32];       // dL/dT |q - r| / (N + 1)
     const int P = g.pitch, rows = g.nz + 4;
     for (int k = threadIdx.x; k < P * rows; k += blockDim.x) acc[k] = 0.0f;
     __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int npts = g.nseg + 1;
     const long total = (long)g.ne * g.npix;
-    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long)gridDim.x * blockDim.x) {
-        const float gv = gdel[idx];
-        if (gv == 0.0f) continue;
-        const int e = (int)(idx / g.npix), p = (int)(idx - (long)e * g.npix);
-        const float2 px = pix[p];
-        float qx, qz;
-        if (g.lens_mode == AF_LENS_BENT_RAY) {
-            float sn, cs;
-            sincosf(phi[idx], &sn, &cs);
-            qx = fmaf(g.RL, sn, g.arc_cx);
-            qz = fmaf(g.RL, cs, g.arc_cz);
-        } else {
-            const float4 el = elem[e];
-            qx = el.x;
-            qz = el.y;
+    const long nchunks = (total + 31) / 32;
+    for (long chunk = (long)blockIdx.x * kRayWarps + warp; chunk < nchunks;
+         chunk += (long)gridDim.x * kRayWarps) {
+        const long idx = chunk * 32 + lane;
+        float c = 0.0f;
+        float4 rp = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (idx < total) {
+            const float gv = gdel[idx];
+            if (gv != 0.0f) {
+                const int e = (int)(idx / g.npix), p = (int)(idx - (long)e * g.npix);
+                const float2 px = pix[p];
+                float qx, qz;
+                if (g.lens_mode == AF_LENS_BENT_RAY) {
+                    float sn, cs;
+                    sincosf(phi[idx], &sn, &cs);
+                    qx = fmaf(g.RL, sn, g.arc_cx);
+                    qz = fmaf(g.RL, cs, g.arc_cz);
+                } else {
+                    const float4 el = elem[e];
+                    qx = el.x;
+                    qz = el.y;
+                }
+                const float lx = px.x - qx, lz = px.y - qz;
+                c = gv * sqrtf(lx * lx + lz * lz) * g.inv_nseg1;
+                rp = make_float4((qx - g.x0) * g.inv_dx, (qz - g.z0) * g.inv_dz,
+                                 lx * g.inv_dx * g.inv_nseg, lz * g.inv_dz * g.inv_nseg);
+            }
         }
-        const float lx = px.x - qx, lz = px.y - qz;
-        const float c = gv * sqrtf(lx * lx + lz * lz) * g.inv_nseg1;
-        const float gx0 = (qx - g.x0) * g.inv_dx, gz0 = (qz - g.z0) * g.inv_dz;
-        const float gdx = lx * g.inv_dx * g.inv_nseg, gdz = lz * g.inv_dz * g.inv_nseg;
-        for (int k = 0; k <= g.nseg; ++k) {
-            const float gx = fmaf((float)k, gdx, gx0), gz = fmaf((float)k, gdz, gz0);
+        const unsigned live = __ballot_sync(0xffffffffu, c != 0.0f);
+        const int nlive = __popc(live);
+        if (c != 0.0f) {
+            const int slot = __popc(live & ((1u << lane) - 1u));
+            rays[warp][slot] = rp;
+            rayc[warp][slot] = c;
+        }
+        __syncwarp();
+        const int npt_total = nlive * npts;
+        for (int q = lane; q < npt_total; q += 32) {
+            const int r = q / npts, k = q - r * npts;
+            const float4 ry = rays[warp][r];
+            const float cr = rayc[warp][r];
+            const float gx = fmaf((float)k, ry.z, ry.x), gz = fmaf((float)k, ry.w, ry.y);
             const float fx = floorf(gx), fz = floorf(gz);
             const int i0 = min(max((int)fx, -1), g.nx - 1), j0 = min(max((int)fz, -1), g.nz - 1);
             float wx[4], wz[4];
@@ -55,11 +87,12 @@ __global__ void __launch_bounds__(256) ray_adjoint_kernel(AfGeom g, const float4
             float *row = acc + (j0 + 1) * P + (i0 + 1);
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const float cb = c * wz[b];
+                const float cb = cr * wz[b];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) atomicAdd(row + b * P + a, cb * wx[a]);
             }
         }
+        __syncwarp();
     }
     __syncthreads();
     // fold the padding onto the clamped edge nodes and write this CTA's partial grid
