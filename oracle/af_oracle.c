@@ -125,9 +125,10 @@ int or_exit_point(const or_geom *g, int e, double x, double z, double sbar,
             chord(rp, RL, f - thp, &b, &b1, &b2);
             double dT = a1 / g->c_lens + b1 * sbar;
             double d2T = a2 / g->c_lens + b2 * sbar;
+            if (dT == 0.0) break;                /* Fermat: stationary point reached */
             if (dT < 0.0) lo = f; else hi = f;
             double fn = (d2T > 0.0) ? f - dT / d2T : 0.5 * (lo + hi);
-            if (!(fn > lo && fn < hi)) fn = 0.5 * (lo + hi);
+            if (!(fn >= lo && fn <= hi)) fn = 0.5 * (lo + hi);
             double step = fabs(fn - f);
             f = fn;
             if (step <= 1e-15 || hi - lo <= 1e-15) break;

@@ -97,9 +97,10 @@ __device__ double exit_solve_fp64(double re, double rp, double RL, double dp, do
         ChordD a = chord_d(re, RL, x), b = chord_d(rp, RL, x - dp);
         double f = a.d1 * inv_cl + b.d1 * sbar;
         double fp = a.d2 * inv_cl + b.d2 * sbar;
+        if (f == 0.0) break;
         if (f < 0.0) lo = x; else hi = x;
         double xn = fp > 0.0 ? x - f / fp : 0.5 * (lo + hi);
-        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        if (!(xn >= lo && xn <= hi)) xn = 0.5 * (lo + hi);
         double step = fabs(xn - x);
         x = xn;
         if (step < 1e-13 || hi - lo < 1e-13) break;
@@ -161,9 +162,10 @@ __global__ void __launch_bounds__(256) delays_kernel(AfGeom g, const float *__re
                 Chord a = chord(ep.y, g.RL, x), b = chord(pp.y, g.RL, x - dp);
                 float f = fmaf(b.d1, sbar, a.d1 * g.inv_c_lens);
                 float fp = fmaf(b.d2, sbar, a.d2 * g.inv_c_lens);
+                if (f == 0.0f) { conv = true; break; }     // stationary point reached exactly
                 if (f < 0.0f) lo = x; else hi = x;
                 float xn = fp > 0.0f ? x - f / fp : 0.5f * (lo + hi);
-                if (!(xn > lo && xn < hi)) xn = 0.5f * (lo + hi);
+                if (!(xn >= lo && xn <= hi)) xn = 0.5f * (lo + hi);
                 conv = fabsf(xn - x) < 1e-6f || hi - lo < 1e-6f;
                 x = xn;
             }
