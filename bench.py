@@ -239,6 +239,7 @@ def run_ours(args, rank, world, local_rank):
     stages = plan.stage_times()
     plan.set_timing(False)
     counters = plan.counters()
+    counters["numeric_ok"] = plan.af_sync_status() == af.AF_OK
     clk = clocks.stop() if clocks else None
     t = torch.tensor([ms], device=dev)
     if world > 1:
