@@ -207,7 +207,7 @@ af_status af_destroy(af_plan_t pl)
     for (int k = 0; k < 2 * kTimingCap; ++k)
         if (pl->ev[k]) cudaEventDestroy(pl->ev[k]);
     void *ptrs[] = {pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->D, pl->B, pl->G, pl->z,
-                    pl->mask, pl->patch_sum, pl->patch_cnt, pl->gdel, pl->gpart, pl->scal};
+                    pl->mask, pl->patch_sum, pl->patch_cnt, pl->gdel, pl->gpart, pl->gpad, pl->scal};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete pl;
@@ -279,6 +279,17 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
         g.na_inv = na > 0 ? (float)(1.0 / na) : 0.0f;
         g.nb_inv = nbv > 0 ? (float)(1.0 / nbv) : 0.0f;
     }
+    {
+        // one ray adds at most |dL/dT| (5 cell diagonals + L / (N + 1)) to a node; a flush
+        // window holds 8 rounds of 256 rays; single contributions stay below 2^21
+        const double diag = sqrt(c->dx * c->dx + c->dz * c->dz);
+        const double lmax = sqrt(pow((c->nx - 1) * c->dx, 2) + pow((c->nz - 1) * c->dz, 2));
+        const double per_ray = 5.0 * diag + lmax / (c->nseg + 1);
+        const double window = 8.0 * 256.0 * per_ray;
+        const double s1 = ldexp(1.0, 30) / window;
+        const double s2 = ldexp(1.0, 21) * (c->nseg + 1) / lmax;
+        g.fix_scale = (float)fmin(s1, s2);
+    }
     g.c_ref = (float)c->c_ref;
     g.lr = (float)c->lr;
     g.beta1 = (float)c->beta1;
@@ -340,6 +351,7 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
     pl->delay_blocks = pl->sm_count * delays_blocks_per_sm(pl->smem_grid);
     pl->rayadj_blocks = pl->sm_count * rayadj_blocks_per_sm(pl->smem_grid);
     AF_ALLOC(pl->gpart, (size_t)pl->rayadj_blocks * g.ng * sizeof(float));
+    AF_ALLOC(pl->gpad, (size_t)pl->rayadj_blocks * pl->smem_grid);
 #undef AF_ALLOC
     e = cudaMemcpy(pl->elem, elem.data(), ne * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pl->elem_pol, elem_pol.data(), ne * sizeof(float2), cudaMemcpyHostToDevice);

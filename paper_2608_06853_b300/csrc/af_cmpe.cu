@@ -129,12 +129,13 @@ __device__ __forceinline__ float arg_sign(float2 z)
 __global__ void __launch_bounds__(256) cmpe_backward_kernel(AfGeom g, const float2 *__restrict__ B,
                                                             const float2 *__restrict__ z,
                                                             const uint8_t *__restrict__ mask,
-                                                            const AfScal *scal,
+                                                            AfScal *scal,
                                                             float2 *__restrict__ G)
 {
     const long total = (long)g.nb * g.npix;
     const float inv_m = scal->inv_m;
     const int n = g.nsub;
+    if (blockIdx.x == 0 && threadIdx.x == 0) scal->gmax_bits = 0;   // read by the ray adjoint
     for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (long)gridDim.x * blockDim.x) {
         const int b = (int)(idx / g.npix), p = (int)(idx - (long)b * g.npix);
@@ -198,7 +199,11 @@ cudaError_t launch_cmpe_backward(af_plan_t pl)
     if (total == 0) return cudaSuccess;
     long blocks = (total + 255) / 256;
     if (blocks > 65535L * 8) blocks = 65535L * 8;
-    if (pl->g.npair == 0) return cudaMemsetAsync(pl->G, 0, total * sizeof(float2), pl->stream);
+    if (pl->g.npair == 0) {
+        cudaError_t e = cudaMemsetAsync(pl->G, 0, total * sizeof(float2), pl->stream);
+        if (e != cudaSuccess) return e;
+        return cudaMemsetAsync(&pl->scal->gmax_bits, 0, sizeof(int), pl->stream);
+    }
     cmpe_backward_kernel<<<(int)blocks, 256, 0, pl->stream>>>(pl->g, pl->B, pl->z, pl->mask, pl->scal, pl->G);
     return cudaGetLastError();
 }

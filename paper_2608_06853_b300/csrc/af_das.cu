@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(256, 3) das_adjoint_kernel(AfGeom g, const voi
                                                              const float *__restrict__ scale,
                                                              const float4 *__restrict__ D,
                                                              const float2 *__restrict__ G,
-                                                             float *__restrict__ gdel)
+                                                             float *__restrict__ gdel,
+                                                             int *__restrict__ gmax_bits)
 {
     using S = Sample<DT>;
     extern __shared__ float gE[];                 // [ne][32]
@@ -160,8 +161,17 @@ __global__ void __launch_bounds__(256, 3) das_adjoint_kernel(AfGeom g, const voi
         }
     }
     __syncthreads();
+    float amax = 0.0f;
     if (valid)
-        for (int e = warp; e < g.ne; e += kWarps) gdel[(long)e * g.npix + p] = gE[e * 32 + lane];
+        for (int e = warp; e < g.ne; e += kWarps) {
+            const float v = gE[e * 32 + lane];
+            gdel[(long)e * g.npix + p] = v;
+            amax = fmaxf(amax, fabsf(v));
+        }
+    // max |dL/dT| for the fixed-point scale of the ray adjoint (non-negative
+    // floats order like their bit patterns)
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (lane == 0 && amax > 0.0f) atomicMax(gmax_bits, __float_as_int(amax));
 }
 
 template <int W, int DT>
@@ -184,7 +194,7 @@ cudaError_t launch_adj_t(af_plan_t pl)
         if (e != cudaSuccess) return e;
     }
     das_adjoint_kernel<W, DT><<<blocks, 32 * kWarps, smem, pl->stream>>>(
-        pl->g, pl->iq, pl->iq_scale, pl->D, pl->G, pl->gdel);
+        pl->g, pl->iq, pl->iq_scale, pl->D, pl->G, pl->gdel, &pl->scal->gmax_bits);
     return cudaGetLastError();
 }
 

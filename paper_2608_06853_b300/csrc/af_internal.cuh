@@ -30,6 +30,7 @@ struct AfGeom {
     // regularisation (Eq. 10-11), units of m/s per mm
     float w1, kx1, kz1, w2, kx2, kz2, hx_mm, hz_mm;
     float na_inv, nb_inv;                    // 1 / number of difference terms
+    float fix_scale;                         // ray-adjoint fixed-point scale times max |dL/dT|
     float c_ref, lr, beta1, beta2, omb1, omb2, eps;   // omb = 1 - beta, formed in double
 };
 
@@ -45,6 +46,7 @@ struct AfScal {
     int numeric_flag;    // set when a slowness is non-positive or non-finite
     int fp64_solves;     // exit solves that fell back to float64
     int n_apod;          // apodized (element, pixel) pairs
+    int gmax_bits;       // max |dL/dT| of the last adjoint (float bits, >= 0)
 };
 
 struct af_plan_s {
@@ -68,6 +70,7 @@ struct af_plan_s {
     int *patch_cnt;      // [n_patch] sum m
     float *gdel;         // [ne][npix] dL/dT
     float *gpart;        // [rayadj_blocks][ng] per-CTA partial gradients
+    float *gpad;         // [rayadj_blocks][padded grid] per-CTA float accumulators
     AfScal *scal;
     float *loss_out;     // last caller loss buffer
     const void *iq;      // last forward's inputs (kept for the adjoint)

@@ -20,30 +20,54 @@ namespace {
 // table, then walks their (N+1) points with lane = consecutive point index, so
 // the 16 taps of one atomic instruction land on 32 different stencils along a
 // ray (distinct addresses; the odd row pitch spreads them over the banks).
+//
+// Accumulation is int32 fixed point (shared-memory integer atomics are several
+// times faster than float ones and their sums do not depend on order): value
+// = round(c w S) with S = fix_scale / max|dL/dT|.  One ray adds at most
+// max|dL/dT| (5 cell diagonals + L/(N+1)) to a node, and fix_scale is set on
+// the host so that kRoundsPerFlush rounds of 256 rays stay below 2^30; after
+// that many rounds the integer grid is flushed into the CTA's float
+// accumulator in global memory and cleared.
 constexpr int kRayWarps = 8;
+constexpr int kRoundsPerFlush = 8;
+
+__device__ __forceinline__ int round_to_int(float v)     // |v| < 2^22
+{
+    return __float_as_int(v + 12582912.0f) - 0x4B400000;
+}
 
 __global__ void __launch_bounds__(256) ray_adjoint_kernel(AfGeom g, const float4 *__restrict__ elem,
                                                           const float2 *__restrict__ pix,
                                                           const float *__restrict__ phi,
                                                           const float *__restrict__ gdel,
+                                                          const AfScal *__restrict__ scal,
+                                                          float *__restrict__ gpad,
                                                           float *__restrict__ gpart)
 {
-    extern __shared__ float acc[];
+    extern __shared__ int acci[];
     __shared__ float4 rays[kRayWarps][32];      // (gx0, gz0, gdx, gdz)
-    __shared__ float rayc[kRayWarps][32];       // dL/dT |q - r| / (N + 1)
-    const int P = g.pitch, rows = g.nz + 4;
-    for (int k = threadIdx.x; k < P * rows; k += blockDim.x) acc[k] = 0.0f;
+    __shared__ float rayc[kRayWarps][32];       // dL/dT |q - r| / (N + 1), scaled
+    const int P = g.pitch, rows = g.nz + 4, npad = P * rows;
+    for (int k = threadIdx.x; k < npad; k += blockDim.x) acci[k] = 0;
+    float *mypad = gpad + (long)blockIdx.x * npad;
+    for (int k = threadIdx.x; k < npad; k += blockDim.x) mypad[k] = 0.0f;
+    const float gmax = __int_as_float(scal->gmax_bits);
+    const float S = gmax > 0.0f ? g.fix_scale / gmax : 0.0f;
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int npts = g.nseg + 1;
     const long total = (long)g.ne * g.npix;
     const long nchunks = (total + 31) / 32;
-    for (long chunk = (long)blockIdx.x * kRayWarps + warp; chunk < nchunks;
-         chunk += (long)gridDim.x * kRayWarps) {
+    // chunks of this CTA: blockIdx.x * 8 + warp + round * gridDim.x * 8
+    const long per_round = (long)gridDim.x * kRayWarps;
+    const long first = (long)blockIdx.x * kRayWarps;
+    const long nrounds = first < nchunks ? (nchunks - first + per_round - 1) / per_round : 0;
+    for (long round = 0; round < nrounds && S > 0.0f; ++round) {
+        const long chunk = first + round * per_round + warp;
         const long idx = chunk * 32 + lane;
         float c = 0.0f;
         float4 rp = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (idx < total) {
+        if (chunk < nchunks && idx < total) {
             const float gv = gdel[idx];
             if (gv != 0.0f) {
                 const int e = (int)(idx / g.npix), p = (int)(idx - (long)e * g.npix);
@@ -60,7 +84,7 @@ __global__ void __launch_bounds__(256) ray_adjoint_kernel(AfGeom g, const float4
                     qz = el.y;
                 }
                 const float lx = px.x - qx, lz = px.y - qz;
-                c = gv * sqrtf(lx * lx + lz * lz) * g.inv_nseg1;
+                c = gv * S * sqrtf(lx * lx + lz * lz) * g.inv_nseg1;
                 rp = make_float4((qx - g.x0) * g.inv_dx, (qz - g.z0) * g.inv_dz,
                                  lx * g.inv_dx * g.inv_nseg, lz * g.inv_dz * g.inv_nseg);
             }
@@ -84,15 +108,27 @@ __global__ void __launch_bounds__(256) ray_adjoint_kernel(AfGeom g, const float4
             float wx[4], wz[4];
             keys_weights(gx - fx, wx);
             keys_weights(gz - fz, wz);
-            float *row = acc + (j0 + 1) * P + (i0 + 1);
+            int *row = acci + (j0 + 1) * P + (i0 + 1);
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const float cb = cr * wz[b];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) atomicAdd(row + b * P + a, cb * wx[a]);
+                for (int a = 0; a < 4; ++a) atomicAdd(row + b * P + a, round_to_int(cb * wx[a]));
             }
         }
         __syncwarp();
+        if ((round + 1) % kRoundsPerFlush == 0 || round + 1 == nrounds) {
+            __syncthreads();
+            const float inv = 1.0f / S;
+            for (int k = threadIdx.x; k < npad; k += blockDim.x) {
+                const int v = acci[k];
+                if (v != 0) {
+                    mypad[k] += (float)v * inv;
+                    acci[k] = 0;
+                }
+            }
+            __syncthreads();
+        }
     }
     __syncthreads();
     // fold the padding onto the clamped edge nodes and write this CTA's partial grid
@@ -103,7 +139,7 @@ __global__ void __launch_bounds__(256) ray_adjoint_kernel(AfGeom g, const float4
         const int jlo = j == 0 ? 0 : j + 2, jhi = j == g.nz - 1 ? g.nz + 3 : j + 2;
         float v = 0.0f;
         for (int jj = jlo; jj <= jhi; ++jj)
-            for (int ii = ilo; ii <= ihi; ++ii) v += acc[jj * P + ii];
+            for (int ii = ilo; ii <= ihi; ++ii) v += mypad[jj * P + ii];
         out[k] = v;
     }
 }
@@ -181,7 +217,7 @@ cudaError_t launch_ray_adjoint(af_plan_t pl, const float *s, float *grad)
     int nparts = 0;
     if ((long)pl->g.ne * pl->g.npix > 0) {
         ray_adjoint_kernel<<<pl->rayadj_blocks, 256, pl->smem_grid, pl->stream>>>(
-            pl->g, pl->elem, pl->pix, pl->phi, pl->gdel, pl->gpart);
+            pl->g, pl->elem, pl->pix, pl->phi, pl->gdel, pl->scal, pl->gpad, pl->gpart);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         nparts = pl->rayadj_blocks;
