@@ -192,6 +192,28 @@ af_status af_get_counters(af_plan_t plan, long long *h_counters);
 af_status af_set_timing(af_plan_t plan, int enable);
 af_status af_get_stage_times(af_plan_t plan, float *h_ms, int *h_count);
 
+/* ---- allocation-free CMPE loss ----
+ *
+ * No counterpart in the paper: an extra entry point for callers that cannot
+ * allocate device memory while they run (a real-time pipeline that reserves
+ * all of its GPU memory at start-up, or a host framework that owns the device
+ * allocator).  It computes L_CMPE of caller-provided subaperture images with
+ * the same reading of the CMPE as af_forward, using no plan and no allocation:
+ * its scratch (per-patch partial sums) is a fixed array of
+ * AF_NOALLOC_MAX_PATCHES x 16 bytes inside the library's device memory, held
+ * by every GPU that loads the library until the process exits.
+ *  d_B        images, [nsub*nsub][n_patch*patch_npix][2] float (as af_get_images)
+ *  d_loss     [1] float, written with L_CMPE
+ *  d_n_active [1] int, number of active CMPE terms, or NULL
+ *  stream     cudaStream_t (NULL = legacy default stream)
+ * The first call on a device looks up the scratch array's device address;
+ * make it before any stream capture.  All calls share the scratch: calls that
+ * overlap on the GPU race, so order them on one stream.  n_patch above
+ * AF_NOALLOC_MAX_PATCHES returns AF_ERR_UNSUPPORTED.  No cudaMalloc/cudaFree. */
+#define AF_NOALLOC_MAX_PATCHES 16384
+af_status af_cmpe_loss_noalloc(const float *d_B, int nsub, int n_patch, int patch_npix,
+                               double rho_thresh, float *d_loss, int *d_n_active, void *stream);
+
 /* Message of the last failing call on this host thread ("" if none). */
 const char *af_last_error(void);
 

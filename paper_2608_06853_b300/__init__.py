@@ -83,6 +83,8 @@ _SIGNATURES = {
     "af_get_image_grad": (ctypes.c_int, [_VP, _VP]),
     "af_get_delay_grad": (ctypes.c_int, [_VP, _VP]),
     "af_get_counters": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
+    "af_cmpe_loss_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                             _VP, _VP, _VP]),
     "af_set_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "af_get_stage_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]),
     "af_last_error": (ctypes.c_char_p, []),
@@ -174,6 +176,22 @@ def iq_view(iq):
     if iq.dtype == torch.complex64:
         return torch.view_as_real(iq)
     return iq
+
+
+AF_NOALLOC_MAX_PATCHES = 16384
+
+
+def af_cmpe_loss_noalloc(B, nsub: int, n_patch: int, patch_npix: int, rho_thresh: float, loss,
+                         n_active=None, stream=None):
+    """L_CMPE of images B ([nsub*nsub][npix] complex64 or [..][2] float32, device) into
+    loss[0], without any device allocation by the library (see include/af.h)."""
+    import torch
+    Bv = torch.view_as_real(B) if B.dtype == torch.complex64 else B
+    h = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+    _check(load().af_cmpe_loss_noalloc(_ptr(Bv), int(nsub), int(n_patch), int(patch_npix),
+                                       float(rho_thresh), _ptr(loss), _ptr(n_active), h),
+           "af_cmpe_loss_noalloc")
+    return loss
 
 
 class Plan:

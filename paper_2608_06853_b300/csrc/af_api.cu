@@ -83,6 +83,15 @@ cudaError_t staged(af_plan_t pl, int stage, F &&launch)
 
 }  // namespace
 
+af_status af_set_error(af_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
 extern "C" {
 
 const char *af_last_error(void) { return g_err; }

@@ -150,6 +150,9 @@ __device__ __forceinline__ void keys_weights(float t, float w[4])
     w[3] = 0.5f * t3 - 0.5f * t2;
 }
 
+// records the message returned by af_last_error() and returns st
+af_status af_set_error(af_status st, const char *fmt, ...);
+
 // ---- launchers (each in its own .cu file) ----
 cudaError_t launch_grid_stats(af_plan_t pl, const float *s);
 cudaError_t launch_delays(af_plan_t pl, const float *s);
