@@ -185,6 +185,20 @@ def stage_roofline(stage, ms, launches, p, iq_bytes, pk):
             "algorithmic_ops": ops, "avg_launch_ms": ms / launches}
 
 
+# ---------------------------------------------------------------- ranks
+def combine_ranks(seconds: float, units_per_rank: float, world: int, device=None):
+    """Whole-job throughput: units of all ranks / max over ranks of the timed seconds.
+    Each rank runs an independent acquisition (no data-path collective); the only
+    collective is this max of the timings."""
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    return world * units_per_rank / t_max, t_max
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -241,11 +255,8 @@ def run_ours(args, rank, world, local_rank):
     counters = plan.counters()
     counters["numeric_ok"] = plan.af_sync_status() == af.AF_OK
     clk = clocks.stop() if clocks else None
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * args.steps / (ms_max * 1e-3)
+    value, t_max = combine_ranks(ms * 1e-3, args.steps, world, dev)
+    ms_max = t_max * 1e3
     final_loss = loss.cpu().numpy().tolist()
 
     # end to end: one autofocus job = upload of the acquisition and the initial map from
@@ -279,10 +290,7 @@ def run_ours(args, rank, world, local_rank):
             h_loss.copy_(loss, non_blocking=True)
         stream.synchronize()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.e2e_jobs * n_iter / float(te.item())
+    e2e_value, _ = combine_ranks(e2e_s, args.e2e_jobs * n_iter, world, dev) if args.e2e_jobs else (0.0, 0.0)
 
     if rank != 0:
         return

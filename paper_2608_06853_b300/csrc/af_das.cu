@@ -30,8 +30,35 @@ template <> struct Sample<AF_IQ_F16> {
 
 constexpr int kWarps = 8;   // warps per CTA; warp w takes receive blocks w, w + 8, ...
 
+// Gather of one transmit for the W receivers held by a lane: all 2W loads are
+// issued before any is used (indices clamped into the trace, out-of-range
+// samples get weight 0), so a warp keeps 2W loads in flight.
+template <int W, typename S>
+__device__ __forceinline__ void gather_w(const typename S::T *__restrict__ base, int ns, int nt,
+                                         float ft, const int (&nr)[W], const float (&fr)[W],
+                                         float2 (&a)[W], float2 (&b)[W], float (&f)[W], float (&on)[W])
+{
+    const int lim = ns - 1;
+    int idx[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        int n = nt + nr[k];
+        float fk = ft + fr[k];
+        if (fk >= 1.0f) { fk -= 1.0f; ++n; }
+        const bool valid = (unsigned)n < (unsigned)lim;
+        idx[k] = k * ns + (valid ? n : 0);
+        f[k] = fk;
+        on[k] = valid ? 1.0f : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        a[k] = S::load(base + idx[k]);
+        b[k] = S::load(base + idx[k] + 1);
+    }
+}
+
 template <int W, int DT>
-__global__ void __launch_bounds__(256, 4) das_forward_kernel(AfGeom g, const void *__restrict__ iq,
+__global__ void __launch_bounds__(256, 3) das_forward_kernel(AfGeom g, const void *__restrict__ iq,
                                                              const float *__restrict__ scale,
                                                              const float4 *__restrict__ D,
                                                              float2 *__restrict__ B)
@@ -41,7 +68,6 @@ __global__ void __launch_bounds__(256, 4) das_forward_kernel(AfGeom g, const voi
     const int p = blockIdx.x * 32 + lane;
     if (p >= g.npix) return;
     const typename S::T *psi = reinterpret_cast<const typename S::T *>(iq);
-    const int lim = g.ns - 1;
     for (int j = threadIdx.x >> 5; j < g.nsub; j += kWarps) {
         int nr[W];
         float fr[W];
@@ -53,27 +79,26 @@ __global__ void __launch_bounds__(256, 4) das_forward_kernel(AfGeom g, const voi
             fr[k] = d.y;
             pr[k] = make_float2(d.z, d.w);
         }
+        float4 dnext = D[p];
         for (int i = 0; i < g.nsub; ++i) {
             float ar = 0.0f, ai = 0.0f;
             for (int tt = 0; tt < W; ++tt) {
                 const int t = i * W + tt;
-                const float4 dt = D[(long)t * g.npix + p];
+                const float4 dt = dnext;
+                if (t + 1 < g.ne) dnext = D[(long)(t + 1) * g.npix + p];
                 const int nt = __float_as_int(dt.x);
                 if (nt == AF_APOD_OFF) continue;
                 const typename S::T *base = psi + ((long)t * g.ne + j * W) * g.ns;
+                float2 a[W], b[W];
+                float f[W], on[W];
+                gather_w<W, S>(base, g.ns, nt, dt.y, nr, fr, a, b, f, on);
                 float sr = 0.0f, si = 0.0f;
 #pragma unroll
                 for (int k = 0; k < W; ++k) {
-                    int n = nt + nr[k];
-                    float f = dt.y + fr[k];
-                    if (f >= 1.0f) { f -= 1.0f; ++n; }
-                    if ((unsigned)n < (unsigned)lim) {
-                        const float2 a = S::load(base + (long)k * g.ns + n);
-                        const float2 b = S::load(base + (long)k * g.ns + n + 1);
-                        const float vr = fmaf(f, b.x - a.x, a.x), vi = fmaf(f, b.y - a.y, a.y);
-                        sr = fmaf(pr[k].x, vr, fmaf(-pr[k].y, vi, sr));
-                        si = fmaf(pr[k].x, vi, fmaf(pr[k].y, vr, si));
-                    }
+                    const float vr = on[k] * fmaf(f[k], b[k].x - a[k].x, a[k].x);
+                    const float vi = on[k] * fmaf(f[k], b[k].y - a[k].y, a[k].y);
+                    sr = fmaf(pr[k].x, vr, fmaf(-pr[k].y, vi, sr));
+                    si = fmaf(pr[k].x, vi, fmaf(pr[k].y, vr, si));
                 }
                 float cr = dt.z, ci = dt.w;
                 if (DT != AF_IQ_C64) { const float sc = scale[t]; cr *= sc; ci *= sc; }
@@ -104,7 +129,6 @@ __global__ void __launch_bounds__(256, 3) das_adjoint_kernel(AfGeom g, const voi
     for (int k = threadIdx.x; k < g.ne * 32; k += blockDim.x) gE[k] = 0.0f;
     __syncthreads();
     const typename S::T *psi = reinterpret_cast<const typename S::T *>(iq);
-    const int lim = g.ns - 1;
     if (valid) {
         for (int j = warp; j < g.nsub; j += kWarps) {
             int nr[W];
@@ -119,11 +143,13 @@ __global__ void __launch_bounds__(256, 3) das_adjoint_kernel(AfGeom g, const voi
                 pr[k] = make_float2(d.z, d.w);
                 gr[k] = 0.0f;
             }
+            float4 dnext = D[p];
             for (int i = 0; i < g.nsub; ++i) {
                 const float2 Gv = G[(long)(i * g.nsub + j) * g.npix + p];
                 for (int tt = 0; tt < W; ++tt) {
                     const int t = i * W + tt;
-                    const float4 dt = D[(long)t * g.npix + p];
+                    const float4 dt = dnext;
+                    if (t + 1 < g.ne) dnext = D[(long)(t + 1) * g.npix + p];
                     const int nt = __float_as_int(dt.x);
                     if (nt == AF_APOD_OFF) continue;
                     float sc = 1.0f;
@@ -132,25 +158,21 @@ __global__ void __launch_bounds__(256, 3) das_adjoint_kernel(AfGeom g, const voi
                     const float xr = sc * fmaf(Gv.x, dt.z, Gv.y * dt.w);
                     const float xi = sc * fmaf(Gv.x, dt.w, -Gv.y * dt.z);
                     const typename S::T *base = psi + ((long)t * g.ne + j * W) * g.ns;
+                    float2 a[W], b[W];
+                    float f[W], on[W];
+                    gather_w<W, S>(base, g.ns, nt, dt.y, nr, fr, a, b, f, on);
                     float gt = 0.0f;
 #pragma unroll
                     for (int k = 0; k < W; ++k) {
-                        int n = nt + nr[k];
-                        float f = dt.y + fr[k];
-                        if (f >= 1.0f) { f -= 1.0f; ++n; }
-                        if ((unsigned)n < (unsigned)lim) {
-                            const float2 a = S::load(base + (long)k * g.ns + n);
-                            const float2 b = S::load(base + (long)k * g.ns + n + 1);
-                            const float sx = b.x - a.x, sy = b.y - a.y;
-                            const float vr = fmaf(f, sx, a.x), vi = fmaf(f, sy, a.y);
-                            const float yr = fmaf(xr, pr[k].x, -xi * pr[k].y);
-                            const float yi = fmaf(xr, pr[k].y, xi * pr[k].x);
-                            const float dr = fmaf(g.fs, sx, -g.wd * vi);
-                            const float di = fmaf(g.fs, sy, g.wd * vr);
-                            const float q = fmaf(yr, dr, -yi * di);
-                            gt += q;
-                            gr[k] += q;
-                        }
+                        const float sx = b[k].x - a[k].x, sy = b[k].y - a[k].y;
+                        const float vr = fmaf(f[k], sx, a[k].x), vi = fmaf(f[k], sy, a[k].y);
+                        const float yr = on[k] * fmaf(xr, pr[k].x, -xi * pr[k].y);
+                        const float yi = on[k] * fmaf(xr, pr[k].y, xi * pr[k].x);
+                        const float dr = fmaf(g.fs, sx, -g.wd * vi);
+                        const float di = fmaf(g.fs, sy, g.wd * vr);
+                        const float q = fmaf(yr, dr, -yi * di);
+                        gt += q;
+                        gr[k] += q;
                     }
                     if (gt != 0.0f) atomicAdd(&gE[t * 32 + lane], gt);
                 }
