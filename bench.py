@@ -157,32 +157,44 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- roofline
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
+# capture of the full workload, per kernel; None once the kernel changed after the
+# capture (see profiles/).
+NCU_TRAFFIC = {"das_forward": 436.6e6 + 60.7e6, "das_adjoint": 505.3e6 + 14.7e6,
+               "ray_adjoint": 30.9e6 + 8.1e6, "delays": None}
+
+# algorithmic FP32 lane-operations per ray point, from the arithmetic of the method:
+# position (2) + cell and fraction (4) + two Keys weight sets (2 x 10) + 16 taps and 4
+# row combinations (20), plus a 4-op compensated sum in the forward ray sum
+OPS_PER_POINT = {"delays": 50, "ray_adjoint": 46}
+
+
 def stage_roofline(stage, ms, launches, p, iq_bytes, pk):
     """Roofline entry of one stage: algorithmic bytes (or lane operations) per launch
     divided by its average launch time."""
     ne, npix = p.ne, p.npix
-    nsub = p.nsub
-    nb = nsub * nsub
+    nb = p.nsub * p.nsub
     avg_s = ms / launches * 1e-3
     hbm = pk.get("hbm_gbs", 6400.0)
     if stage in ("das_forward", "das_adjoint"):
-        # channel data once + one-way tables + images (+ dL/dB and dL/dT for the adjoint)
+        # channel data once + one-way tables + images (dL/dB and dL/dT for the adjoint)
         bytes_ = iq_bytes + ne * npix * 16 + nb * npix * 8
         if stage == "das_adjoint":
             bytes_ += ne * npix * 4
         achieved = bytes_ / avg_s / 1e9
         return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "kernel": stage,
-                "algorithmic_bytes": bytes_, "avg_launch_ms": ms / launches}
-    # FP32 lane-operation bound: SMs x 128 lanes x max SM clock
+                "frac": achieved / hbm, "traffic": NCU_TRAFFIC.get(stage), "kernel": stage,
+                "algorithmic_bytes": bytes_, "avg_launch_ms": ms / launches,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in pk else "fallback"}
+    # FP32 lane-operation bound: SMs x 128 lanes x max SM clock (derived, not measured)
     lanes = 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6
     pts = ne * npix * (p.nseg + 1)
-    ops_per_point = {"delays": 44, "ray_adjoint": 40}.get(stage, 0)
-    ops = pts * ops_per_point
+    ops = pts * OPS_PER_POINT.get(stage, 0)
     achieved = ops / avg_s / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": lanes / 1e12, "unit": "Tlane-op/s",
-            "frac": achieved / (lanes / 1e12), "traffic": None, "kernel": stage,
-            "algorithmic_ops": ops, "avg_launch_ms": ms / launches}
+            "frac": achieved / (lanes / 1e12), "traffic": NCU_TRAFFIC.get(stage), "kernel": stage,
+            "algorithmic_ops": ops, "avg_launch_ms": ms / launches,
+            "peak_source": "derived: 148 SMs x 128 FP32 lanes x max SM clock"}
 
 
 # ---------------------------------------------------------------- ranks
