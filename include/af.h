@@ -214,6 +214,17 @@ af_status af_get_stage_times(af_plan_t plan, float *h_ms, int *h_count);
 af_status af_cmpe_loss_noalloc(const float *d_B, int nsub, int n_patch, int patch_npix,
                                double rho_thresh, float *d_loss, int *d_n_active, void *stream);
 
+/* ---- BF16 tensor-core GEMM (building block of the lens-surrogate MLP) ----
+ * D[M][N] (float) = sum_k A(m,k) B(n,k) on the sm_103a tensor cores (tcgen05,
+ * f32 accumulation in tensor memory).  A is bf16 [M][K] (a_mn_major = 0) or
+ * [K][M] (1); B is bf16 [N][K] (b_mn_major = 0) or [K][N] (1); D is [M][N].
+ * M, N multiples of 128, K a multiple of 64, operands 16-byte aligned.
+ * *d_err (device int, caller-zeroed) is set to 1 if an MMA completion wait
+ * timed out.  No counterpart in the paper (the MLP surrogate is the north
+ * star's learned lens-time model). */
+af_status af_gemm_bf16(const void *d_A, const void *d_B, float *d_D, int M, int N, int K,
+                       int a_mn_major, int b_mn_major, int *d_err, void *stream);
+
 /* Message of the last failing call on this host thread ("" if none). */
 const char *af_last_error(void);
 

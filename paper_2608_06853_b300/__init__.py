@@ -85,6 +85,8 @@ _SIGNATURES = {
     "af_get_counters": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
     "af_cmpe_loss_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                              _VP, _VP, _VP]),
+    "af_gemm_bf16": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, _VP, _VP]),
     "af_set_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "af_get_stage_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]),
     "af_last_error": (ctypes.c_char_p, []),
@@ -192,6 +194,20 @@ def af_cmpe_loss_noalloc(B, nsub: int, n_patch: int, patch_npix: int, rho_thresh
                                        float(rho_thresh), _ptr(loss), _ptr(n_active), h),
            "af_cmpe_loss_noalloc")
     return loss
+
+
+def af_gemm_bf16(A, B, D, a_mn_major=False, b_mn_major=False, err=None, stream=None):
+    """D = A B^T on the tensor cores (see include/af.h).  A: bf16 [M][K] or [K][M];
+    B: bf16 [N][K] or [K][N]; D: float32 [M][N]."""
+    import torch
+    M, N = D.shape
+    K = A.shape[0] if a_mn_major else A.shape[1]
+    if err is None:
+        err = torch.zeros(1, dtype=torch.int32, device=D.device)
+    h = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+    _check(load().af_gemm_bf16(_ptr(A), _ptr(B), _ptr(D), M, N, K, int(bool(a_mn_major)),
+                               int(bool(b_mn_major)), _ptr(err), h), "af_gemm_bf16")
+    return err
 
 
 class Plan:
