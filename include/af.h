@@ -187,8 +187,9 @@ af_status af_get_counters(af_plan_t plan, long long *h_counters);
  *  0 grid statistics (c_med, Eq. 10-11)   1 delays (Eq. 1-4, 8)
  *  2 DAS forward (Eq. 5)                   3 CMPE forward + loss
  *  4 CMPE adjoint                          5 DAS adjoint
- *  6 ray adjoint + gradient reduction      7 Adam update (Eq. 9) */
-#define AF_NSTAGES 8
+ *  6 ray adjoint + gradient reduction      7 Adam update (Eq. 9)
+ *  8 lens-surrogate inference (when enabled) */
+#define AF_NSTAGES 9
 af_status af_set_timing(af_plan_t plan, int enable);
 af_status af_get_stage_times(af_plan_t plan, float *h_ms, int *h_count);
 
@@ -213,6 +214,43 @@ af_status af_get_stage_times(af_plan_t plan, float *h_ms, int *h_count);
 #define AF_NOALLOC_MAX_PATCHES 16384
 af_status af_cmpe_loss_noalloc(const float *d_B, int nsub, int n_patch, int patch_npix,
                                double rho_thresh, float *d_loss, int *d_n_active, void *stream);
+
+/* ---- learned lens surrogate (MLP on the tensor cores) ----
+ * A 4-layer MLP (4 -> 128 -> 128 -> 128 -> 2, tanh) standing in for the exit-
+ * point solve of Eq. 8: inputs element angle, pixel radius, pixel angle
+ * relative to the element (about the arc centre) and c_med; outputs the exit
+ * angle offset and the lens transit time.  The 128 x 128 layers run as bf16
+ * tcgen05 MMAs with f32 accumulation (forward and backward).  No counterpart in
+ * the paper, which solves Eq. 8 directly.
+ *
+ * af_surrogate_train: requires one earlier af_forward (its apodization defines
+ *   the validated pairs).  Draws n_samples configurations inside the f-number
+ *   cone with c in [1400, 1650] m/s, labels them with the float64 exact solver,
+ *   trains `epochs` passes of Adam (batch tiles_per_step x 128, cosine decay
+ *   from lr), then validates on every apodized pair at six speeds and marks
+ *   pairs whose delay error exceeds lambda/50 (1 / (50 fd)) for the exact
+ *   solver.  h_report[8] = {final training loss, rms exit-angle error (rad),
+ *   max delay error (s), max lens-time error (s), fallback fraction, samples,
+ *   tolerance (s), optimisation steps}.  Allocates and frees temporaries.
+ * af_surrogate_enable: 1 = af_forward uses the surrogate's exit angle (exact
+ *   solver on marked pairs; path lengths are always computed exactly), 0 = off.
+ * af_surrogate_eval: exit angle (rad) and lens time (s) of every (element,
+ *   pixel) pair at medium speed c, into [n_elem][npix] float arrays.
+ * af_surrogate_params: copy the AF_MLP_NPARAM float parameters out (set = 0)
+ *   or in (set = 1).  Layout: W1[128][4], b1[128], W2[128][128], b2[128],
+ *   W3[128][128], b3[128], W4[2][128], b4[2].
+ * af_surrogate_grad: gradient of the training loss (mean over the n samples of
+ *   the squared error of both normalised outputs) at the current parameters
+ *   for a caller batch d_X[n][4], d_Y[n][2] (normalised), n a multiple of 128;
+ *   *h_loss receives the loss.  Parameters are not changed. */
+#define AF_MLP_NPARAM 33922
+af_status af_surrogate_train(af_plan_t plan, long long n_samples, int epochs, int tiles_per_step, float lr,
+                             unsigned long long seed, double *h_report);
+af_status af_surrogate_enable(af_plan_t plan, int enable);
+af_status af_surrogate_eval(af_plan_t plan, float c, float *d_phi, float *d_tlens);
+af_status af_surrogate_params(af_plan_t plan, float *d_params, int set);
+af_status af_surrogate_grad(af_plan_t plan, const float *d_X, const float *d_Y, int n, float *d_grad,
+                            float *h_loss);
 
 /* ---- BF16 tensor-core GEMM (building block of the lens-surrogate MLP) ----
  * D[M][N] (float) = sum_k A(m,k) B(n,k) on the sm_103a tensor cores (tcgen05,

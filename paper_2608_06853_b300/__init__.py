@@ -85,6 +85,12 @@ _SIGNATURES = {
     "af_get_counters": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
     "af_cmpe_loss_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                              _VP, _VP, _VP]),
+    "af_surrogate_train": (ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                           ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_double)]),
+    "af_surrogate_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "af_surrogate_eval": (ctypes.c_int, [_VP, ctypes.c_float, _VP, _VP]),
+    "af_surrogate_params": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
+    "af_surrogate_grad": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_float)]),
     "af_gemm_bf16": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, _VP, _VP]),
     "af_set_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -312,17 +318,57 @@ class Plan:
         return g
 
     STAGES = ("grid_stats", "delays", "das_forward", "cmpe_forward", "cmpe_adjoint",
-              "das_adjoint", "ray_adjoint", "adam")
+              "das_adjoint", "ray_adjoint", "adam", "surrogate")
 
     def set_timing(self, enable: bool):
         _check(self.lib.af_set_timing(self.handle, 1 if enable else 0), "af_set_timing")
 
     def stage_times(self):
         """{stage: (total ms, launches)} recorded since set_timing(True)."""
-        ms = (ctypes.c_float * 8)()
-        n = (ctypes.c_int * 8)()
+        ms = (ctypes.c_float * 9)()
+        n = (ctypes.c_int * 9)()
         _check(self.lib.af_get_stage_times(self.handle, ms, n), "af_get_stage_times")
         return {name: (ms[k], n[k]) for k, name in enumerate(self.STAGES)}
+
+    # ---- learned lens surrogate ----
+    def surrogate_train(self, n_samples=10_000_000, epochs=4, tiles_per_step=32, lr=2e-3, seed=1):
+        """Train the lens-surrogate MLP on the tensor cores (see include/af.h)."""
+        rep = (ctypes.c_double * 8)()
+        _check(self.lib.af_surrogate_train(self.handle, int(n_samples), int(epochs), int(tiles_per_step),
+                                           float(lr), int(seed), rep), "af_surrogate_train")
+        keys = ("train_loss", "rms_angle_err", "max_delay_err", "max_lens_time_err", "fallback_fraction",
+                "samples", "tolerance", "steps")
+        return dict(zip(keys, list(rep)))
+
+    def surrogate_enable(self, enable=True):
+        _check(self.lib.af_surrogate_enable(self.handle, 1 if enable else 0), "af_surrogate_enable")
+
+    def surrogate_eval(self, c):
+        import torch
+        phi = torch.empty((self.ne, self.npix), dtype=torch.float32, device=self._dev())
+        tl = torch.empty_like(phi)
+        _check(self.lib.af_surrogate_eval(self.handle, float(c), _ptr(phi), _ptr(tl)), "af_surrogate_eval")
+        return phi, tl
+
+    NPARAM = 33922
+
+    def surrogate_params(self):
+        import torch
+        p = torch.empty(self.NPARAM, dtype=torch.float32, device=self._dev())
+        _check(self.lib.af_surrogate_params(self.handle, _ptr(p), 0), "af_surrogate_params")
+        return p
+
+    def set_surrogate_params(self, p):
+        _check(self.lib.af_surrogate_params(self.handle, _ptr(p.contiguous()), 1), "af_surrogate_params")
+
+    def surrogate_grad(self, X, Y):
+        """(gradient [NPARAM], loss) of the training loss on the batch X [n][4], Y [n][2]."""
+        import torch
+        g = torch.empty(self.NPARAM, dtype=torch.float32, device=self._dev())
+        loss = ctypes.c_float()
+        _check(self.lib.af_surrogate_grad(self.handle, _ptr(X.contiguous()), _ptr(Y.contiguous()), int(X.shape[0]),
+                                          _ptr(g), ctypes.byref(loss)), "af_surrogate_grad")
+        return g, loss.value
 
     def counters(self):
         """{apodized pairs, float64 exit solves, active CMPE terms, CMPE pairs per patch}."""

@@ -216,7 +216,8 @@ af_status af_destroy(af_plan_t pl)
     for (int k = 0; k < 2 * kTimingCap; ++k)
         if (pl->ev[k]) cudaEventDestroy(pl->ev[k]);
     void *ptrs[] = {pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->D, pl->B, pl->G, pl->z,
-                    pl->mask, pl->patch_sum, pl->patch_cnt, pl->gdel, pl->gpart, pl->gpad, pl->scal};
+                    pl->mask, pl->patch_sum, pl->patch_cnt, pl->gdel, pl->gpart, pl->gpad, pl->scal,
+                    pl->mlp_p, pl->mlp_m, pl->mlp_v, pl->mlp_g, pl->mlp_w2b, pl->mlp_w3b, pl->sur_fb};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete pl;
@@ -328,6 +329,41 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
         pix_pol[p] = make_float2((float)atan2(vx, vz), (float)hypot(vx, vz));
     }
 
+    {
+        // lens-surrogate sampling region and feature scales
+        double re = 0, thlo = 1e300, thhi = -1e300, zmax = 0;
+        for (int a = 0; a < ne; ++a) {
+            re += elem_pol[a].y / ne;
+            thlo = fmin(thlo, elem_pol[a].x);
+            thhi = fmax(thhi, elem_pol[a].x);
+        }
+        for (int p = 0; p < npix; ++p) zmax = fmax(zmax, pix_pol[p].y - re);
+        const double dl = fmax(c->lens_radius - re, 1e-5);
+        MlpGeom &G = pl->mlp_geom;
+        G.re = re;
+        G.RL = c->lens_radius;
+        G.inv_c_lens = c->lens_mode == AF_LENS_BENT_RAY ? 1.0 / c->c_lens : 0.0;
+        G.th_lo = thlo - 0.01;
+        G.th_hi = thhi + 0.01;
+        G.z_lo = dl + 1e-3;
+        G.z_hi = fmax(zmax, G.z_lo + 1e-3) + 10e-3;
+        G.cone = 1.05 * (c->apod_mode == AF_APOD_PRINTED ? 0.5 * c->fnum : 1.0 / (2.0 * c->fnum));
+        G.c_lo = 1400.0;
+        G.c_hi = 1650.0;
+        MlpNorm &n = pl->mlp_norm;
+        n.th_c = (float)(0.5 * (G.th_lo + G.th_hi));
+        n.th_s = (float)(2.0 / (G.th_hi - G.th_lo));
+        const double rlo = re + G.z_lo, rhi = re + G.z_hi * sqrt(1.0 + G.cone * G.cone);
+        n.r_c = (float)(0.5 * (rlo + rhi));
+        n.r_s = (float)(2.0 / (rhi - rlo));
+        n.dp_s = (float)(1.0 / 0.6);
+        n.c_c = 1525.0f;
+        n.c_s = 1.0f / 125.0f;
+        n.y0_s = (float)(2.0 * dl / c->lens_radius);
+        n.y1_c = (float)(dl * G.inv_c_lens);
+        n.y1_s = (float)(0.5 * dl * G.inv_c_lens);
+    }
+
     auto bail = [&](af_status s) { af_destroy(pl); return s; };
     cudaError_t e;
 #define AF_ALLOC(ptr, bytes)                                                     \
@@ -361,7 +397,16 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
     pl->rayadj_blocks = pl->sm_count * rayadj_blocks_per_sm(pl->smem_grid);
     AF_ALLOC(pl->gpart, (size_t)pl->rayadj_blocks * g.ng * sizeof(float));
     AF_ALLOC(pl->gpad, (size_t)pl->rayadj_blocks * pl->smem_grid);
+    AF_ALLOC(pl->mlp_p, AF_MLP_NPARAM * sizeof(float));
+    AF_ALLOC(pl->mlp_m, AF_MLP_NPARAM * sizeof(float));
+    AF_ALLOC(pl->mlp_v, AF_MLP_NPARAM * sizeof(float));
+    AF_ALLOC(pl->mlp_g, AF_MLP_NPARAM * sizeof(float));
+    AF_ALLOC(pl->mlp_w2b, 128 * 128 * 2);
+    AF_ALLOC(pl->mlp_w3b, 128 * 128 * 2);
+    AF_ALLOC(pl->sur_fb, nep);
 #undef AF_ALLOC
+    e = mlp_setup_attributes();
+    if (e != cudaSuccess) return bail(cuda_fail(e, "MLP kernel attributes"));
     e = cudaMemcpy(pl->elem, elem.data(), ne * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pl->elem_pol, elem_pol.data(), ne * sizeof(float2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && npix) e = cudaMemcpy(pl->pix, pix.data(), npix * sizeof(float2), cudaMemcpyHostToDevice);
@@ -384,6 +429,8 @@ af_status af_forward(af_plan_t pl, const void *iq, const float *scale, const flo
     pl->slowness = s;
     pl->loss_out = loss;
     AF_CUDA(staged(pl, 0, [&] { return launch_grid_stats(pl, s); }));
+    if (pl->use_surrogate)
+        AF_CUDA(staged(pl, 8, [&] { return mlp_infer(pl, 0.0f, pl->sur_fb, pl->phi, nullptr); }));
     AF_CUDA(staged(pl, 1, [&] { return launch_delays(pl, s); }));
     AF_CUDA(staged(pl, 2, [&] { return launch_das_forward(pl); }));
     AF_CUDA(staged(pl, 3, [&] { return launch_cmpe_forward(pl, loss); }));
@@ -526,6 +573,152 @@ af_status af_get_stage_times(af_plan_t pl, float *ms, int *count)
         ms[pl->rec_stage[r]] += t;
         count[pl->rec_stage[r]] += 1;
     }
+    return AF_OK;
+}
+
+af_status af_surrogate_train(af_plan_t pl, long long n_samples, int epochs, int tiles_per_step, float lr,
+                             unsigned long long seed, double *h_report)
+{
+    g_err[0] = 0;
+    if (!pl || !h_report) return fail(AF_ERR_ARG, "NULL argument");
+    if (pl->g.lens_mode != AF_LENS_BENT_RAY) return fail(AF_ERR_UNSUPPORTED, "the surrogate models the lens (bent-ray mode only)");
+    if (!pl->have_fwd) return fail(AF_ERR_STATE, "run af_forward once first (validation uses its apodization)");
+    if (tiles_per_step < 1 || tiles_per_step > 1024 || epochs < 1 || !(lr > 0))
+        return fail(AF_ERR_ARG, "bad epochs / tiles_per_step / lr");
+    const long long per_step = (long long)tiles_per_step * 128;
+    if (n_samples < per_step || n_samples > (1LL << 31)) return fail(AF_ERR_ARG, "n_samples out of range");
+    const long long steps_per_epoch = n_samples / per_step;
+    const long long n = steps_per_epoch * per_step;
+    float4 *X = nullptr;
+    float2 *Y = nullptr;
+    float *gpart = nullptr, *lpart = nullptr, *tphi = nullptr, *ttl = nullptr;
+    unsigned long long *stats = nullptr;
+    const size_t nep = (size_t)pl->g.ne * pl->g.npix;
+    auto cleanup = [&]() {
+        void *ptrs[] = {X, Y, gpart, lpart, tphi, ttl, stats};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+    };
+#define SU_CUDA(call)                                                         \
+    do {                                                                      \
+        cudaError_t _e = (call);                                              \
+        if (_e != cudaSuccess) { cleanup(); return cuda_fail(_e, #call); }    \
+    } while (0)
+    SU_CUDA(cudaMalloc(&X, n * sizeof(float4)));
+    SU_CUDA(cudaMalloc(&Y, n * sizeof(float2)));
+    SU_CUDA(cudaMalloc(&gpart, (size_t)tiles_per_step * AF_MLP_NPARAM * sizeof(float)));
+    SU_CUDA(cudaMalloc(&lpart, tiles_per_step * sizeof(float)));
+    SU_CUDA(cudaMalloc(&tphi, (nep ? nep : 1) * sizeof(float)));
+    SU_CUDA(cudaMalloc(&ttl, (nep ? nep : 1) * sizeof(float)));
+    SU_CUDA(cudaMalloc(&stats, 8 * sizeof(unsigned long long)));
+    SU_CUDA(cudaMemsetAsync(&pl->scal->mlp_err, 0, sizeof(int), pl->stream));
+    SU_CUDA(mlp_init_params(pl, seed));
+    SU_CUDA(mlp_generate(pl, n, seed * 2654435761ull + 1, X, Y));
+    const long long total_steps = steps_per_epoch * epochs;
+    std::vector<float> hl(tiles_per_step);
+    double last_loss = 0.0;
+    long long step = 0;
+    for (int ep = 0; ep < epochs; ++ep) {
+        for (long long st = 0; st < steps_per_epoch; ++st, ++step) {
+            // cosine decay to lr / 20
+            const double frac = (double)step / (double)total_steps;
+            const float lr_t = (float)(lr * (0.05 + 0.95 * 0.5 * (1.0 + cos(3.14159265358979323846 * frac))));
+            SU_CUDA(mlp_train_step(pl, X, Y, st * per_step, tiles_per_step, lr_t, (int)(step + 1), lpart, gpart));
+        }
+        SU_CUDA(cudaMemcpyAsync(hl.data(), lpart, tiles_per_step * sizeof(float), cudaMemcpyDeviceToHost, pl->stream));
+        SU_CUDA(cudaStreamSynchronize(pl->stream));
+        last_loss = 0.0;
+        for (float v : hl) last_loss += v;
+    }
+    // validation on this plan's apodized pairs at several medium speeds
+    const double tol = 1.0 / (50.0 * (double)pl->g.wd / (2.0 * 3.14159265358979323846));   // lambda / 50 in time
+    SU_CUDA(cudaMemsetAsync(pl->sur_fb, 0, nep ? nep : 1, pl->stream));
+    SU_CUDA(cudaMemsetAsync(stats, 0, 8 * sizeof(unsigned long long), pl->stream));
+    const double speeds[] = {1400.0, 1450.0, 1500.0, 1550.0, 1600.0, 1650.0};
+    for (double cv : speeds) {
+        SU_CUDA(mlp_infer(pl, (float)cv, nullptr, tphi, ttl));
+        SU_CUDA(mlp_validate(pl, cv, tphi, ttl, tol, pl->sur_fb, stats));
+    }
+    unsigned long long hs[8];
+    long long nfb = 0;
+    {
+        std::vector<uint8_t> hfb(nep);
+        SU_CUDA(cudaMemcpyAsync(hs, stats, sizeof hs, cudaMemcpyDeviceToHost, pl->stream));
+        if (nep) SU_CUDA(cudaMemcpyAsync(hfb.data(), pl->sur_fb, nep, cudaMemcpyDeviceToHost, pl->stream));
+        SU_CUDA(cudaStreamSynchronize(pl->stream));
+        for (uint8_t v : hfb) nfb += v;
+    }
+    int merr = 0;
+    SU_CUDA(cudaMemcpy(&merr, &pl->scal->mlp_err, sizeof(int), cudaMemcpyDeviceToHost));
+    cleanup();
+#undef SU_CUDA
+    if (merr) return fail(AF_ERR_TIMEOUT, "a tensor-core completion wait timed out");
+    const double count = hs[0] > 0 ? (double)hs[0] : 1.0;
+    h_report[0] = last_loss;
+    h_report[1] = sqrt((double)hs[4] * 1e-12 / count);      // rms exit-angle error (rad)
+    h_report[2] = (double)hs[2] * 1e-12;                    // max delay error (s)
+    h_report[3] = (double)hs[3] * 1e-12;                    // max lens-time error (s)
+    h_report[4] = (double)nfb / (double)(hs[0] / 6 > 0 ? hs[0] / 6 : 1);   // fallback fraction of apodized pairs
+    h_report[5] = (double)n;
+    h_report[6] = tol;
+    h_report[7] = (double)total_steps;
+    pl->sur_trained = true;
+    return AF_OK;
+}
+
+af_status af_surrogate_enable(af_plan_t pl, int enable)
+{
+    if (!pl) return fail(AF_ERR_ARG, "plan is NULL");
+    if (enable && !pl->sur_trained) return fail(AF_ERR_STATE, "surrogate not trained");
+    pl->use_surrogate = enable != 0;
+    return AF_OK;
+}
+
+af_status af_surrogate_eval(af_plan_t pl, float c, float *d_phi, float *d_tlens)
+{
+    if (!pl || !d_phi || !d_tlens) return fail(AF_ERR_ARG, "NULL argument");
+    if (!(c > 0)) return fail(AF_ERR_ARG, "c must be > 0");
+    AF_CUDA(mlp_infer(pl, c, nullptr, d_phi, d_tlens));
+    return AF_OK;
+}
+
+af_status af_surrogate_params(af_plan_t pl, float *d_params, int set)
+{
+    if (!pl || !d_params) return fail(AF_ERR_ARG, "NULL argument");
+    if (set) {
+        AF_CUDA(cudaMemcpyAsync(pl->mlp_p, d_params, AF_MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToDevice, pl->stream));
+        AF_CUDA(mlp_refresh_bf16(pl));
+    } else {
+        AF_CUDA(cudaMemcpyAsync(d_params, pl->mlp_p, AF_MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToDevice, pl->stream));
+    }
+    return AF_OK;
+}
+
+af_status af_surrogate_grad(af_plan_t pl, const float *d_X, const float *d_Y, int n, float *d_grad, float *h_loss)
+{
+    if (!pl || !d_X || !d_Y || !d_grad || !h_loss) return fail(AF_ERR_ARG, "NULL argument");
+    if (n <= 0 || n % 128 || n / 128 > 1024) return fail(AF_ERR_SHAPE, "n must be a positive multiple of 128 (<= 131072)");
+    const int tiles = n / 128;
+    float *gpart = nullptr, *lpart = nullptr;
+    AF_CUDA(cudaMalloc(&gpart, (size_t)tiles * AF_MLP_NPARAM * sizeof(float)));
+    cudaError_t e = cudaMalloc(&lpart, tiles * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemsetAsync(&pl->scal->mlp_err, 0, sizeof(int), pl->stream);
+    if (e == cudaSuccess)
+        e = mlp_train_step(pl, reinterpret_cast<const float4 *>(d_X), reinterpret_cast<const float2 *>(d_Y), 0, tiles,
+                           0.0f, 1, lpart, gpart);
+    std::vector<float> hl(tiles);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_grad, pl->mlp_g, AF_MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToDevice, pl->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hl.data(), lpart, tiles * sizeof(float), cudaMemcpyDeviceToHost, pl->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pl->stream);
+    int merr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&merr, &pl->scal->mlp_err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(gpart);
+    cudaFree(lpart);
+    if (e != cudaSuccess) return cuda_fail(e, "af_surrogate_grad");
+    if (merr) return fail(AF_ERR_TIMEOUT, "a tensor-core completion wait timed out");
+    double l = 0.0;
+    for (float v : hl) l += v;
+    *h_loss = (float)l;
     return AF_OK;
 }
 

@@ -4,6 +4,7 @@
 #include <math.h>
 
 #include "af_internal.cuh"
+#include "af_lens.cuh"
 
 namespace {
 
@@ -62,52 +63,6 @@ __global__ void __launch_bounds__(1024) grid_stats_kernel(AfGeom g, const float 
     }
 }
 
-// chord length between radius r1 at angle 0 and radius r2 at angle d, with
-// its first two derivatives in d; sh = sin(d/2), ch = cos(d/2)
-struct Chord { float len, d1, d2; };
-__device__ __forceinline__ Chord chord(float r1, float r2, float d)
-{
-    float sh, ch;
-    sincosf(0.5f * d, &sh, &ch);
-    float k = r1 * r2, dr = r1 - r2;
-    float len = sqrtf(fmaf(dr, dr, 4.0f * k * sh * sh));
-    float sd = 2.0f * sh * ch, cd = fmaf(-2.0f * sh, sh, 1.0f);
-    float inv = 1.0f / len;
-    float ks = k * sd * inv;
-    return {len, ks, (k * cd - ks * ks) * inv};
-}
-
-struct ChordD { double len, d1, d2; };
-__device__ ChordD chord_d(double r1, double r2, double d)
-{
-    double sh, ch;
-    sincos(0.5 * d, &sh, &ch);
-    double k = r1 * r2, dr = r1 - r2;
-    double len = sqrt(dr * dr + 4.0 * k * sh * sh);
-    double ks = k * 2.0 * sh * ch / len;
-    return {len, ks, (k * (1.0 - 2.0 * sh * sh) - ks * ks) / len};
-}
-
-// float64 safeguarded Newton / bisection on dT/dd = 0 over [lo, hi]
-__device__ double exit_solve_fp64(double re, double rp, double RL, double dp, double inv_cl,
-                                  double sbar)
-{
-    double lo = fmin(0.0, dp), hi = fmax(0.0, dp), x = 0.0;
-    for (int it = 0; it < 100; ++it) {
-        ChordD a = chord_d(re, RL, x), b = chord_d(rp, RL, x - dp);
-        double f = a.d1 * inv_cl + b.d1 * sbar;
-        double fp = a.d2 * inv_cl + b.d2 * sbar;
-        if (f == 0.0) break;
-        if (f < 0.0) lo = x; else hi = x;
-        double xn = fp > 0.0 ? x - f / fp : 0.5 * (lo + hi);
-        if (!(xn >= lo && xn <= hi)) xn = 0.5 * (lo + hi);
-        double step = fabs(xn - x);
-        x = xn;
-        if (step < 1e-13 || hi - lo < 1e-13) break;
-    }
-    return x;
-}
-
 // One thread per (element e, pixel p), grid-stride over e * npix + p, with the
 // slowness deviation s - sbar staged once per CTA in shared memory, padded by
 // two edge-replicated nodes on every side so that each of the 16 taps of a
@@ -118,6 +73,7 @@ __global__ void __launch_bounds__(256) delays_kernel(AfGeom g, const float *__re
                                                      const float2 *__restrict__ pix,
                                                      const float2 *__restrict__ pix_pol,
                                                      float *__restrict__ phi, int warm,
+                                                     const uint8_t *__restrict__ sur_fb,
                                                      float4 *__restrict__ D, AfScal *scal)
 {
     extern __shared__ float sm[];
@@ -158,6 +114,9 @@ __global__ void __launch_bounds__(256) delays_kernel(AfGeom g, const float *__re
             float lo = fminf(0.0f, dp), hi = fmaxf(0.0f, dp);
             float x = warm ? fminf(fmaxf(phi[idx] - ep.x, lo), hi) : 0.0f;
             bool conv = (lo == hi);
+            // lens surrogate: its exit angle (already in phi) replaces the solve
+            const bool use_sur = sur_fb && !sur_fb[idx];
+            if (use_sur) { x = phi[idx] - ep.x; conv = true; }
             for (int it = 0; it < 16 && !conv; ++it) {
                 Chord a = chord(ep.y, g.RL, x), b = chord(pp.y, g.RL, x - dp);
                 float f = fmaf(b.d1, sbar, a.d1 * g.inv_c_lens);
@@ -178,7 +137,7 @@ __global__ void __launch_bounds__(256) delays_kernel(AfGeom g, const float *__re
                 Chord b = chord(pp.y, g.RL, x - dp);
                 c_t = (pp.y * cd - g.RL) / b.len;
             }
-            if (!conv || c_t < 0.17f) {
+            if (!use_sur && (!conv || c_t < 0.17f)) {
                 x = (float)exit_solve_fp64(ep.y, pp.y, g.RL, (double)dp, (double)g.inv_c_lens,
                                            (double)sbar);
                 ++n_fp64;
@@ -289,7 +248,7 @@ cudaError_t launch_delays(af_plan_t pl, const float *s)
     if ((long)pl->g.ne * pl->g.npix == 0) return cudaSuccess;
     delays_kernel<<<pl->delay_blocks, 256, pl->smem_grid, pl->stream>>>(
         pl->g, s, pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->have_phi ? 1 : 0,
-        pl->D, pl->scal);
+        pl->use_surrogate ? pl->sur_fb : nullptr, pl->D, pl->scal);
     cudaError_t err = cudaGetLastError();
     if (err == cudaSuccess) pl->have_phi = true;
     return err;

@@ -58,8 +58,10 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const __nv_bfloat16 *__r
     const uint32_t tmem = tslot;
     const uint32_t idesc = tc::idesc_bf16_f32(kTile, kTile, a_mn, b_mn);
     // descriptor strides and the per-instruction advance along K (16 elements)
-    const uint32_t lbo_a = 128, sbo_a = a_mn ? kTile * 16 : kChunk * 16, step_a = a_mn ? 2 * kTile * 16 : 256;
-    const uint32_t lbo_b = 128, sbo_b = b_mn ? kTile * 16 : kChunk * 16, step_b = b_mn ? 2 * kTile * 16 : 256;
+    // K-major: LBO = 128 B (next 8 K), SBO = kChunk * 16 B (next 8 rows);
+    // MN-major: LBO = kTile * 16 B (next 8 K), SBO = 128 B (next 8 rows)
+    const uint32_t lbo_a = a_mn ? kTile * 16 : 128, sbo_a = a_mn ? 128 : kChunk * 16, step_a = 2 * lbo_a;
+    const uint32_t lbo_b = b_mn ? kTile * 16 : 128, sbo_b = b_mn ? 128 : kChunk * 16, step_b = 2 * lbo_b;
     bool ok = true;
     uint32_t phase = 0;
     for (int k0 = 0; k0 < K; k0 += kChunk) {
@@ -112,6 +114,8 @@ extern "C" af_status af_gemm_bf16(const void *d_A, const void *d_B, float *d_D, 
         return af_set_error(AF_ERR_SHAPE, "af_gemm_bf16: M, N must be multiples of 128 and K of 64");
     if (((uintptr_t)d_A | (uintptr_t)d_B) & 15) return af_set_error(AF_ERR_ARG, "af_gemm_bf16: operands not 16-byte aligned");
     dim3 grid(N / kTile, M / kTile);
+    cudaError_t a = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kGuardSmem);
+    if (a != cudaSuccess) return af_set_error(AF_ERR_CUDA, "af_gemm_bf16: %s", cudaGetErrorString(a));
     gemm_bf16_kernel<<<grid, 128, kGuardSmem, (cudaStream_t)stream>>>(
         reinterpret_cast<const __nv_bfloat16 *>(d_A), reinterpret_cast<const __nv_bfloat16 *>(d_B), d_D, M, N, K,
         a_mn_major ? 1 : 0, b_mn_major ? 1 : 0, d_err);

@@ -36,6 +36,21 @@ struct AfGeom {
 
 constexpr int kTimingCap = 4096;   // recorded stage launches per timing window
 
+// lens-surrogate MLP: parameter count (4->128->128->128->2) and normalisation
+#define AF_MLP_NPARAM 33922
+struct MlpNorm {
+    float th_c, th_s;      // element angle: (th_e - th_c) * th_s
+    float r_c, r_s;        // pixel radius
+    float dp_s;            // pixel angle relative to the element
+    float c_c, c_s;        // medium speed
+    float y0_s;            // exit-angle offset = y0 * y0_s (rad)
+    float y1_c, y1_s;      // lens time = y1_c + y1 * y1_s (s)
+};
+struct MlpGeom {           // sampling region and lens constants (float64)
+    double re, RL, inv_c_lens;
+    double th_lo, th_hi, z_lo, z_hi, cone, c_lo, c_hi;
+};
+
 // Plan-owned device scalars.
 struct AfScal {
     float sbar;          // 1 / c_med, c_med = mean(1/s)  (Sec. III-A)
@@ -47,6 +62,7 @@ struct AfScal {
     int fp64_solves;     // exit solves that fell back to float64
     int n_apod;          // apodized (element, pixel) pairs
     int gmax_bits;       // max |dL/dT| of the last adjoint (float bits, >= 0)
+    int mlp_err;         // a tensor-core completion wait of the MLP timed out
 };
 
 struct af_plan_s {
@@ -78,6 +94,13 @@ struct af_plan_s {
     const float *slowness;
     int iq_dtype;
     bool have_phi, have_fwd, have_adj;
+    // lens surrogate
+    float *mlp_p, *mlp_m, *mlp_v, *mlp_g;   // f32 parameters, Adam moments, last gradient
+    void *mlp_w2b, *mlp_w3b;                // bf16 copies of the two tensor-core layers
+    uint8_t *sur_fb;                        // [ne][npix] 1 = use the exact solver
+    MlpNorm mlp_norm;
+    MlpGeom mlp_geom;
+    bool use_surrogate, sur_trained;
     // stage timing: a ring of (start, stop) event pairs per recorded launch
     bool timing;
     int n_rec;
@@ -164,4 +187,13 @@ cudaError_t launch_ray_adjoint(af_plan_t pl, const float *s, float *grad);
 cudaError_t launch_adam(af_plan_t pl, const float *grad, float *s, float *m, float *v, int step);
 cudaError_t launch_export_delays(af_plan_t pl, double *T, uint8_t *apod);
 int delays_blocks_per_sm(size_t smem);
+cudaError_t mlp_setup_attributes();
+cudaError_t mlp_refresh_bf16(af_plan_t pl);
+cudaError_t mlp_init_params(af_plan_t pl, uint64_t seed);
+cudaError_t mlp_generate(af_plan_t pl, long count, uint64_t seed, float4 *X, float2 *Y);
+cudaError_t mlp_train_step(af_plan_t pl, const float4 *X, const float2 *Y, long first, int ntiles, float lr,
+                           int step, float *lpart, float *gpart);
+cudaError_t mlp_infer(af_plan_t pl, float c_fixed, const uint8_t *fb, float *phi_out, float *tl_out);
+cudaError_t mlp_validate(af_plan_t pl, double c, const float *phi_s, const float *tl_s, double tol, uint8_t *fb,
+                         unsigned long long *stats);
 int rayadj_blocks_per_sm(size_t smem);

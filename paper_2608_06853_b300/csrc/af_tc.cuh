@@ -5,11 +5,10 @@
 //
 // Operand layout used throughout (no swizzle): a 16-bit matrix is tiled into
 // "core matrices" of 8 rows x 16 bytes.  In the K-major layout a core matrix
-// holds 8 rows (M or N) x 8 consecutive K elements; LBO is the byte distance
-// between core matrices adjacent along K and SBO the distance between core
-// matrices adjacent along M/N.  In the MN-major layout a core matrix holds 8 K
-// rows x 8 consecutive M/N elements; LBO is the distance between core matrices
-// adjacent along M/N and SBO the distance along K.
+// holds 8 rows (M or N) x 8 consecutive K elements; in the MN-major layout it
+// holds 8 K rows x 8 consecutive M/N elements.  In both, LBO is the byte
+// distance between core matrices adjacent along K and SBO the distance between
+// core matrices adjacent along M/N.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -142,7 +141,7 @@ __host__ __device__ __forceinline__ uint32_t kmajor_offset(int row, int k, int k
     return (uint32_t)((row >> 3) * (kdim * 16) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 // byte offset of element (mn, k) of an MN-major operand with mndim x kdim elements
-// (core matrices: LBO = 128 B along MN, SBO = mndim * 16 B along K)
+// (core matrices: SBO = 128 B along MN, LBO = mndim * 16 B along K)
 __host__ __device__ __forceinline__ uint32_t mnmajor_offset(int mn, int k, int mndim)
 {
     return (uint32_t)((k >> 3) * (mndim * 16) + (mn >> 3) * 128 + (k & 7) * 16 + (mn & 7) * 2);

@@ -469,3 +469,36 @@ def test_adam_first_step_is_signed_learning_rate():
     # beta1 = beta2 = 0 keeps it a sign step at every iteration
     s2, _, _ = o.adam(s1, -g, m, v, 2, lr, beta1=0.0, beta2=0.0)
     np.testing.assert_allclose((s2 - s1) * 1540.0, lr * gu / (np.abs(gu) + 1e-8), rtol=1e-9, atol=1e-15)
+
+
+# ---------------------------------------------------------------- MLP reference
+def test_mlp_oracle_gradient_matches_finite_differences():
+    from oracle import mlp_oracle as mo
+    rng = np.random.default_rng(12)
+    p = mo.init(3) + 0.01 * rng.standard_normal(mo.NPARAM)
+    X = rng.uniform(-1, 1, (16, 4))
+    Y = rng.uniform(-1, 1, (16, 2))
+    L, g = mo.forward_backward(p, X, Y)
+    for k in rng.choice(mo.NPARAM, 25, replace=False):
+        h = 1e-6
+        pp, pm = p.copy(), p.copy()
+        pp[k] += h
+        pm[k] -= h
+        fd = (mo.forward_backward(pp, X, Y)[0] - mo.forward_backward(pm, X, Y)[0]) / (2 * h)
+        assert g[k] == pytest.approx(fd, rel=1e-6, abs=1e-10)
+
+
+def test_mlp_oracle_closed_forms():
+    """Zero weights: output = b4, loss = mean squared error, d loss / d b4 = 2 mean(err);
+    bf16 rounding keeps exactly representable values and rounds 1 + 2^-9 to 1."""
+    from oracle import mlp_oracle as mo
+    d = {n: np.zeros(s) for n, s in mo.SIZES}
+    d["b4"] = np.array([0.3, -0.2])
+    X = np.ones((8, 4))
+    Y = np.zeros((8, 2))
+    L, g = mo.forward_backward(mo.pack(d), X, Y)
+    assert L == pytest.approx(0.3 ** 2 + 0.2 ** 2)
+    gb4 = mo.unpack(g)["b4"]
+    np.testing.assert_allclose(gb4, [0.6, -0.4])
+    assert mo.bf16(np.array([1.0 + 2 ** -9]))[0] == 1.0
+    assert mo.bf16(np.array([0.75]))[0] == 0.75
