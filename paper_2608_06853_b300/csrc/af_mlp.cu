@@ -154,8 +154,9 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const float4 *__restr
     stage_weight(sW2, W2b);
     stage_weight(sW3, W3b);
     for (int k = b; k < 2 * HID; k += blockDim.x) sW4[k] = P[OFF_W4 + k];
-    const float4 xs = X[first + b];
-    const float2 ys = Y[first + b];
+    const long sample = first + (long)blockIdx.x * TILE + b;
+    const float4 xs = X[sample];
+    const float2 ys = Y[sample];
     sx[b][0] = xs.x; sx[b][1] = xs.y; sx[b][2] = xs.z; sx[b][3] = xs.w;
     // layer 1 on the FP32 pipes: H1 = tanh(W1 x + b1)
     for (int c = 0; c < HID; c += 32) {
