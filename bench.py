@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--scatterers", type=int, default=N_SCATTERERS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-jobs", type=int, default=2)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--surrogate-samples", type=int, default=10_000_000)
     return ap.parse_args()
 
 
@@ -211,6 +213,89 @@ def combine_ranks(seconds: float, units_per_rank: float, world: int, device=None
     return world * units_per_rank / t_max, t_max
 
 
+# ---------------------------------------------------------------- variants
+def _time_iterations(plan, iq, scale, p, stream, dev, steps, warmup):
+    import torch
+    s = torch.from_numpy(p.initial_slowness()).to(dev)
+    m, v, g = torch.zeros_like(s), torch.zeros_like(s), torch.zeros_like(s)
+    loss = torch.zeros(4, device=dev)
+    for it in range(1, warmup + 1):
+        plan.af_iterate(iq, s, g, m, v, it, loss, scale)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plan.set_timing(True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for it in range(warmup + 1, warmup + steps + 1):
+        plan.af_iterate(iq, s, g, m, v, it, loss, scale)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    stages = plan.stage_times()
+    plan.set_timing(False)
+    ms = e0.elapsed_time(e1) / steps
+    return ms, {k: v_[0] / max(v_[1], 1) for k, v_ in stages.items()}, loss.cpu().numpy().tolist()
+
+
+def run_variants(args, p, psi, plan32, iq32, stream, dev, ms32):
+    """16-bit channel-data storage (per-transmit scale) and the lens surrogate + bf16 form,
+    each timed on the same workload, with their error against the float32 GPU result."""
+    import torch
+
+    import paper_2608_06853_b300 as af
+    out = {"fp32": {"iterations_per_s": 1e3 / ms32}}
+    s0 = torch.from_numpy(p.initial_slowness()).to(dev)
+    with torch.cuda.stream(stream):
+        ref_loss = torch.zeros(4, device=dev)
+        plan32.af_forward(iq32, s0, ref_loss)
+        ref_B = plan32.images().clone()
+        g32 = torch.zeros_like(s0)
+        plan32.af_adjoint(g32)
+        T32, a32 = plan32.delays()
+    stream.synchronize()
+    r = torch.view_as_real(iq32)
+    scale = r.abs().amax(dim=(1, 2, 3)).clamp_min(1e-30).float().contiguous()
+    plans = {}
+    for name, dt, tdt in (("bf16", af.AF_IQ_BF16, torch.bfloat16), ("f16", af.AF_IQ_F16, torch.float16)):
+        with torch.cuda.stream(stream):
+            q = (r / scale[:, None, None, None]).to(tdt).contiguous()
+        pl = af.Plan(p, iq_dtype=dt, stream=stream)
+        ms, stages, _ = _time_iterations(pl, q, scale, p, stream, dev, args.steps, args.warmup)
+        with torch.cuda.stream(stream):
+            loss = torch.zeros(4, device=dev)
+            pl.af_forward(q, s0, loss)
+            B = pl.images()
+            g = torch.zeros_like(s0)
+            pl.af_adjoint(g)
+        stream.synchronize()
+        out[name] = {"iterations_per_s": 1e3 / ms, "ms_per_iteration": ms,
+                     "image_rel_l2_vs_fp32": float((B - ref_B).abs().norm() / ref_B.abs().norm()),
+                     "loss_rel_vs_fp32": float(abs(loss[0] - ref_loss[0]) / abs(ref_loss[0])),
+                     "grad_rel_l2_vs_fp32": float((g - g32).norm() / g32.norm()),
+                     "stage_ms": stages}
+        plans[name] = (pl, q)
+    # lens surrogate + bf16: train on the tensor cores, validate, enable
+    pl, q = plans["bf16"]
+    t0 = time.perf_counter()
+    rep = pl.surrogate_train(n_samples=args.surrogate_samples, epochs=4, tiles_per_step=32, lr=2e-3, seed=3)
+    t_train = time.perf_counter() - t0
+    pl.surrogate_enable(True)
+    ms, stages, _ = _time_iterations(pl, q, scale, p, stream, dev, args.steps, args.warmup)
+    with torch.cuda.stream(stream):
+        loss = torch.zeros(4, device=dev)
+        pl.af_forward(q, s0, loss)
+        Ts, _ = pl.delays()
+    stream.synchronize()
+    on = a32 == 1
+    derr = float((Ts - T32).abs()[on].max())
+    out["surrogate_bf16"] = {"iterations_per_s": 1e3 / ms, "ms_per_iteration": ms, "stage_ms": stages,
+                             "max_delay_err_s": derr, "tolerance_s": rep["tolerance"],
+                             "fallback_fraction": rep["fallback_fraction"],
+                             "rms_exit_angle_err_rad": rep["rms_angle_err"],
+                             "train_samples": int(rep["samples"]), "train_steps": int(rep["steps"]),
+                             "train_seconds": t_train, "train_loss": rep["train_loss"]}
+    pl.surrogate_enable(False)
+    return out
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -304,6 +389,10 @@ def run_ours(args, rank, world, local_rank):
     e2e_s = time.perf_counter() - t0
     e2e_value, _ = combine_ranks(e2e_s, args.e2e_jobs * n_iter, world, dev) if args.e2e_jobs else (0.0, 0.0)
 
+    variants = None
+    if not args.no_variants and dtype == af.AF_IQ_C64:
+        variants = run_variants(args, p, psi, plan, iq, stream, dev, ms_max / args.steps)
+
     if rank != 0:
         return
     pk = peaks()
@@ -329,6 +418,7 @@ def run_ours(args, rank, world, local_rank):
         "loss": final_loss,
         "counters": counters,
         "clocks": clk,
+        "variants": variants,
         "e2e": {"value": e2e_value, "unit": "iterations/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h),
                 "step": f"one autofocus job: upload + {n_iter} iterations + read back"},
