@@ -261,7 +261,7 @@ def run_variants(args, p, psi, plan32, iq32, stream, dev, ms32):
         ms, stages, _ = _time_iterations(pl, q, scale, p, stream, dev, args.steps, args.warmup)
         with torch.cuda.stream(stream):
             loss = torch.zeros(4, device=dev)
-            pl.af_forward(q, s0, loss)
+            pl.af_forward(q, s0, loss, scale)
             B = pl.images()
             g = torch.zeros_like(s0)
             pl.af_adjoint(g)
@@ -281,7 +281,7 @@ def run_variants(args, p, psi, plan32, iq32, stream, dev, ms32):
     ms, stages, _ = _time_iterations(pl, q, scale, p, stream, dev, args.steps, args.warmup)
     with torch.cuda.stream(stream):
         loss = torch.zeros(4, device=dev)
-        pl.af_forward(q, s0, loss)
+        pl.af_forward(q, s0, loss, scale)
         Ts, _ = pl.delays()
     stream.synchronize()
     on = a32 == 1
