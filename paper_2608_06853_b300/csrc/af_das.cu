@@ -2,10 +2,9 @@
 // one-way delays (Fig. 1g).  Delays are generated inside the gather from the
 // one-way tables (tau = T_t + T_r + t_ttp, never materialised per pair).
 //
-// CTA = 32 consecutive pixels x 8 warps.  Warp w takes receive blocks j = w,
-// w + 8, ...; a lane owns a pixel.  The receive-side delays and phasors of
-// block j live in registers, the transmit side is re-read per transmit
-// (shared by the warps of the CTA through L1).  Phase rotation is separable:
+// A lane owns a pixel and one receive block j; the receive-side delays and
+// phasors of block j live in registers, the transmit side is re-read per
+// transmit.  Phase rotation is separable:
 //   exp(j 2 pi fd tau) = P_t P_r,  P_e = exp(j 2 pi fd (T_e + t_ttp / 2)).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -57,6 +56,10 @@ __device__ __forceinline__ void gather_w(const typename S::T *__restrict__ base,
     }
 }
 
+// Forward: CTA = 8 warps on 8 neighbouring tiles of 32 pixels (256
+// consecutive pixels, about three laterally adjacent patches), all with the
+// same receive block j = blockIdx.y.  The warps walk the transmits in the same
+// order, so the trace windows one warp pulls into L1 serve the other seven.
 template <int W, int DT>
 __global__ void __launch_bounds__(256, 3) das_forward_kernel(AfGeom g, const void *__restrict__ iq,
                                                              const float *__restrict__ scale,
@@ -64,49 +67,48 @@ __global__ void __launch_bounds__(256, 3) das_forward_kernel(AfGeom g, const voi
                                                              float2 *__restrict__ B)
 {
     using S = Sample<DT>;
-    const int lane = threadIdx.x & 31;
-    const int p = blockIdx.x * 32 + lane;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p = (blockIdx.x * kWarps + warp) * 32 + lane;
+    const int j = blockIdx.y;
     if (p >= g.npix) return;
     const typename S::T *psi = reinterpret_cast<const typename S::T *>(iq);
-    for (int j = threadIdx.x >> 5; j < g.nsub; j += kWarps) {
-        int nr[W];
-        float fr[W];
-        float2 pr[W];
+    int nr[W];
+    float fr[W];
+    float2 pr[W];
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-            const float4 d = D[(long)(j * W + k) * g.npix + p];
-            nr[k] = __float_as_int(d.x);
-            fr[k] = d.y;
-            pr[k] = make_float2(d.z, d.w);
-        }
-        float4 dnext = D[p];
-        for (int i = 0; i < g.nsub; ++i) {
-            float ar = 0.0f, ai = 0.0f;
-            for (int tt = 0; tt < W; ++tt) {
-                const int t = i * W + tt;
-                const float4 dt = dnext;
-                if (t + 1 < g.ne) dnext = D[(long)(t + 1) * g.npix + p];
-                const int nt = __float_as_int(dt.x);
-                if (nt == AF_APOD_OFF) continue;
-                const typename S::T *base = psi + ((long)t * g.ne + j * W) * g.ns;
-                float2 a[W], b[W];
-                float f[W], on[W];
-                gather_w<W, S>(base, g.ns, nt, dt.y, nr, fr, a, b, f, on);
-                float sr = 0.0f, si = 0.0f;
+    for (int k = 0; k < W; ++k) {
+        const float4 d = D[(long)(j * W + k) * g.npix + p];
+        nr[k] = __float_as_int(d.x);
+        fr[k] = d.y;
+        pr[k] = make_float2(d.z, d.w);
+    }
+    float4 dnext = D[p];
+    for (int i = 0; i < g.nsub; ++i) {
+        float ar = 0.0f, ai = 0.0f;
+        for (int tt = 0; tt < W; ++tt) {
+            const int t = i * W + tt;
+            const float4 dt = dnext;
+            if (t + 1 < g.ne) dnext = D[(long)(t + 1) * g.npix + p];
+            const int nt = __float_as_int(dt.x);
+            if (nt == AF_APOD_OFF) continue;
+            const typename S::T *base = psi + ((long)t * g.ne + j * W) * g.ns;
+            float2 a[W], b[W];
+            float f[W], on[W];
+            gather_w<W, S>(base, g.ns, nt, dt.y, nr, fr, a, b, f, on);
+            float sr = 0.0f, si = 0.0f;
 #pragma unroll
-                for (int k = 0; k < W; ++k) {
-                    const float vr = on[k] * fmaf(f[k], b[k].x - a[k].x, a[k].x);
-                    const float vi = on[k] * fmaf(f[k], b[k].y - a[k].y, a[k].y);
-                    sr = fmaf(pr[k].x, vr, fmaf(-pr[k].y, vi, sr));
-                    si = fmaf(pr[k].x, vi, fmaf(pr[k].y, vr, si));
-                }
-                float cr = dt.z, ci = dt.w;
-                if (DT != AF_IQ_C64) { const float sc = scale[t]; cr *= sc; ci *= sc; }
-                ar = fmaf(cr, sr, fmaf(-ci, si, ar));
-                ai = fmaf(cr, si, fmaf(ci, sr, ai));
+            for (int k = 0; k < W; ++k) {
+                const float vr = on[k] * fmaf(f[k], b[k].x - a[k].x, a[k].x);
+                const float vi = on[k] * fmaf(f[k], b[k].y - a[k].y, a[k].y);
+                sr = fmaf(pr[k].x, vr, fmaf(-pr[k].y, vi, sr));
+                si = fmaf(pr[k].x, vi, fmaf(pr[k].y, vr, si));
             }
-            B[(long)(i * g.nsub + j) * g.npix + p] = make_float2(ar, ai);
+            float cr = dt.z, ci = dt.w;
+            if (DT != AF_IQ_C64) { const float sc = scale[t]; cr *= sc; ci *= sc; }
+            ar = fmaf(cr, sr, fmaf(-ci, si, ar));
+            ai = fmaf(cr, si, fmaf(ci, sr, ai));
         }
+        B[(long)(i * g.nsub + j) * g.npix + p] = make_float2(ar, ai);
     }
 }
 
@@ -199,7 +201,7 @@ __global__ void __launch_bounds__(256, 3) das_adjoint_kernel(AfGeom g, const voi
 template <int W, int DT>
 cudaError_t launch_fwd_t(af_plan_t pl)
 {
-    const int blocks = (pl->g.npix + 31) / 32;
+    const dim3 blocks((pl->g.npix + 32 * kWarps - 1) / (32 * kWarps), pl->g.nsub);
     das_forward_kernel<W, DT><<<blocks, 32 * kWarps, 0, pl->stream>>>(
         pl->g, pl->iq, pl->iq_scale, pl->D, pl->B);
     return cudaGetLastError();
