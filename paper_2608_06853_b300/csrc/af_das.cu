@@ -112,90 +112,86 @@ __global__ void __launch_bounds__(256, 3) das_forward_kernel(AfGeom g, const voi
     }
 }
 
-// dL/dtau for one gather: Re(conj(G) exp(j 2 pi fd tau) (fs dPsi/du + j 2 pi fd Psi(u)));
-// it is added to dL/dT_t and to dL/dT_r.  Both roles meet in a per-CTA table
-// gE[e][lane] in shared memory, so each dL/dT[e][p] is written exactly once.
+// Adjoint: same CTA shape as the forward (8 neighbouring pixel tiles, one
+// receive block j = blockIdx.y).  For one gather dL/dtau =
+// Re(conj(G) exp(j 2 pi fd tau) (fs dPsi/du + j 2 pi fd Psi(u))); it is added to
+// dL/dT_t and dL/dT_r.  A lane sums the transmit role over its block's W
+// receivers and the receive role over all transmits, then adds both into the
+// zeroed dL/dT table with coalesced atomic adds (one per transmit and one per
+// receiver of the block).
 template <int W, int DT>
 __global__ void __launch_bounds__(256, 3) das_adjoint_kernel(AfGeom g, const void *__restrict__ iq,
                                                              const float *__restrict__ scale,
                                                              const float4 *__restrict__ D,
                                                              const float2 *__restrict__ G,
-                                                             float *__restrict__ gdel,
-                                                             int *__restrict__ gmax_bits)
+                                                             float *__restrict__ gdel)
 {
     using S = Sample<DT>;
-    extern __shared__ float gE[];                 // [ne][32]
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int p = blockIdx.x * 32 + lane;
-    const bool valid = p < g.npix;
-    for (int k = threadIdx.x; k < g.ne * 32; k += blockDim.x) gE[k] = 0.0f;
-    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p = (blockIdx.x * kWarps + warp) * 32 + lane;
+    const int j = blockIdx.y;
+    if (p >= g.npix) return;
     const typename S::T *psi = reinterpret_cast<const typename S::T *>(iq);
-    if (valid) {
-        for (int j = warp; j < g.nsub; j += kWarps) {
-            int nr[W];
-            float fr[W];
-            float2 pr[W];
-            float gr[W];
+    int nr[W];
+    float fr[W];
+    float2 pr[W];
+    float gr[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        const float4 d = D[(long)(j * W + k) * g.npix + p];
+        nr[k] = __float_as_int(d.x);
+        fr[k] = d.y;
+        pr[k] = make_float2(d.z, d.w);
+        gr[k] = 0.0f;
+    }
+    float4 dnext = D[p];
+    for (int i = 0; i < g.nsub; ++i) {
+        const float2 Gv = G[(long)(i * g.nsub + j) * g.npix + p];
+        for (int tt = 0; tt < W; ++tt) {
+            const int t = i * W + tt;
+            const float4 dt = dnext;
+            if (t + 1 < g.ne) dnext = D[(long)(t + 1) * g.npix + p];
+            const int nt = __float_as_int(dt.x);
+            if (nt == AF_APOD_OFF) continue;
+            float sc = 1.0f;
+            if (DT != AF_IQ_C64) sc = scale[t];
+            // X = conj(G) P_t (scaled)
+            const float xr = sc * fmaf(Gv.x, dt.z, Gv.y * dt.w);
+            const float xi = sc * fmaf(Gv.x, dt.w, -Gv.y * dt.z);
+            const typename S::T *base = psi + ((long)t * g.ne + j * W) * g.ns;
+            float2 a[W], b[W];
+            float f[W], on[W];
+            gather_w<W, S>(base, g.ns, nt, dt.y, nr, fr, a, b, f, on);
+            float gt = 0.0f;
 #pragma unroll
             for (int k = 0; k < W; ++k) {
-                const float4 d = D[(long)(j * W + k) * g.npix + p];
-                nr[k] = __float_as_int(d.x);
-                fr[k] = d.y;
-                pr[k] = make_float2(d.z, d.w);
-                gr[k] = 0.0f;
+                const float sx = b[k].x - a[k].x, sy = b[k].y - a[k].y;
+                const float vr = fmaf(f[k], sx, a[k].x), vi = fmaf(f[k], sy, a[k].y);
+                const float yr = on[k] * fmaf(xr, pr[k].x, -xi * pr[k].y);
+                const float yi = on[k] * fmaf(xr, pr[k].y, xi * pr[k].x);
+                const float dr = fmaf(g.fs, sx, -g.wd * vi);
+                const float di = fmaf(g.fs, sy, g.wd * vr);
+                const float q = fmaf(yr, dr, -yi * di);
+                gt += q;
+                gr[k] += q;
             }
-            float4 dnext = D[p];
-            for (int i = 0; i < g.nsub; ++i) {
-                const float2 Gv = G[(long)(i * g.nsub + j) * g.npix + p];
-                for (int tt = 0; tt < W; ++tt) {
-                    const int t = i * W + tt;
-                    const float4 dt = dnext;
-                    if (t + 1 < g.ne) dnext = D[(long)(t + 1) * g.npix + p];
-                    const int nt = __float_as_int(dt.x);
-                    if (nt == AF_APOD_OFF) continue;
-                    float sc = 1.0f;
-                    if (DT != AF_IQ_C64) sc = scale[t];
-                    // X = conj(G) P_t (scaled)
-                    const float xr = sc * fmaf(Gv.x, dt.z, Gv.y * dt.w);
-                    const float xi = sc * fmaf(Gv.x, dt.w, -Gv.y * dt.z);
-                    const typename S::T *base = psi + ((long)t * g.ne + j * W) * g.ns;
-                    float2 a[W], b[W];
-                    float f[W], on[W];
-                    gather_w<W, S>(base, g.ns, nt, dt.y, nr, fr, a, b, f, on);
-                    float gt = 0.0f;
-#pragma unroll
-                    for (int k = 0; k < W; ++k) {
-                        const float sx = b[k].x - a[k].x, sy = b[k].y - a[k].y;
-                        const float vr = fmaf(f[k], sx, a[k].x), vi = fmaf(f[k], sy, a[k].y);
-                        const float yr = on[k] * fmaf(xr, pr[k].x, -xi * pr[k].y);
-                        const float yi = on[k] * fmaf(xr, pr[k].y, xi * pr[k].x);
-                        const float dr = fmaf(g.fs, sx, -g.wd * vi);
-                        const float di = fmaf(g.fs, sy, g.wd * vr);
-                        const float q = fmaf(yr, dr, -yi * di);
-                        gt += q;
-                        gr[k] += q;
-                    }
-                    if (gt != 0.0f) atomicAdd(&gE[t * 32 + lane], gt);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < W; ++k)
-                if (gr[k] != 0.0f) atomicAdd(&gE[(j * W + k) * 32 + lane], gr[k]);
+            atomicAdd(&gdel[(long)t * g.npix + p], gt);
         }
     }
-    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < W; ++k) atomicAdd(&gdel[(long)(j * W + k) * g.npix + p], gr[k]);
+}
+
+// max |dL/dT| for the fixed-point scale of the ray adjoint (non-negative floats
+// order like their bit patterns)
+__global__ void __launch_bounds__(256) gdel_max_kernel(const float *__restrict__ gdel, long n,
+                                                       int *__restrict__ gmax_bits)
+{
     float amax = 0.0f;
-    if (valid)
-        for (int e = warp; e < g.ne; e += kWarps) {
-            const float v = gE[e * 32 + lane];
-            gdel[(long)e * g.npix + p] = v;
-            amax = fmaxf(amax, fabsf(v));
-        }
-    // max |dL/dT| for the fixed-point scale of the ray adjoint (non-negative
-    // floats order like their bit patterns)
+    for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x)
+        amax = fmaxf(amax, fabsf(gdel[k]));
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    if (lane == 0 && amax > 0.0f) atomicMax(gmax_bits, __float_as_int(amax));
+    if ((threadIdx.x & 31) == 0 && amax > 0.0f) atomicMax(gmax_bits, __float_as_int(amax));
 }
 
 template <int W, int DT>
@@ -210,15 +206,15 @@ cudaError_t launch_fwd_t(af_plan_t pl)
 template <int W, int DT>
 cudaError_t launch_adj_t(af_plan_t pl)
 {
-    const int blocks = (pl->g.npix + 31) / 32;
-    const size_t smem = (size_t)pl->g.ne * 32 * sizeof(float);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(das_adjoint_kernel<W, DT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    das_adjoint_kernel<W, DT><<<blocks, 32 * kWarps, smem, pl->stream>>>(
-        pl->g, pl->iq, pl->iq_scale, pl->D, pl->G, pl->gdel, &pl->scal->gmax_bits);
+    const long n = (long)pl->g.ne * pl->g.npix;
+    cudaError_t e = cudaMemsetAsync(pl->gdel, 0, n * sizeof(float), pl->stream);
+    if (e != cudaSuccess) return e;
+    const dim3 blocks((pl->g.npix + 32 * kWarps - 1) / (32 * kWarps), pl->g.nsub);
+    das_adjoint_kernel<W, DT><<<blocks, 32 * kWarps, 0, pl->stream>>>(pl->g, pl->iq, pl->iq_scale, pl->D, pl->G,
+                                                                       pl->gdel);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    gdel_max_kernel<<<pl->sm_count * 4, 256, 0, pl->stream>>>(pl->gdel, n, &pl->scal->gmax_bits);
     return cudaGetLastError();
 }
 
