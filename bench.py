@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--e2e-jobs", type=int, default=2)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--surrogate-samples", type=int, default=10_000_000)
+    ap.add_argument("--batch-size", type=int, default=16)
     return ap.parse_args()
 
 
@@ -293,7 +294,56 @@ def run_variants(args, p, psi, plan32, iq32, stream, dev, ms32):
                              "train_samples": int(rep["samples"]), "train_steps": int(rep["steps"]),
                              "train_seconds": t_train, "train_loss": rep["train_loss"]}
     pl.surrogate_enable(False)
+    out["batch"] = run_batch(args, dev)
     return out
+
+
+def run_batch(args, dev, n_iter=100, n_scat=20_000):
+    """Batched workload: args.batch_size acquisitions of uneven size (96-192 elements,
+    2048-4096 samples, 80-160 mm, 64^2-128^2 grids), bf16 channel data, 100 iterations
+    each, captured as one CUDA graph and launched once; with and without the lens
+    surrogate (trained per acquisition on the tensor cores)."""
+    import torch
+
+    import paper_2608_06853_b300 as af
+    import synth
+    from paper_2608_06853_b300.batch import BatchRunner
+    probs, iqs, scales = [], [], []
+    t0 = time.perf_counter()
+    for k in range(args.batch_size):
+        p = synth.config_batch_member(k)
+        psi = synth.simulate(p, n_scat, seed=SEED + 1000 + k)
+        r = torch.view_as_real(torch.from_numpy(psi).to(dev))
+        sc = r.abs().amax(dim=(1, 2, 3)).clamp_min(1e-30).float().contiguous()
+        iqs.append((r / sc[:, None, None, None]).to(torch.bfloat16).contiguous())
+        scales.append(sc)
+        probs.append(p)
+    t_gen = time.perf_counter() - t0
+    res = {"acquisitions": len(probs), "iterations_each": n_iter, "scatterers_each": n_scat,
+           "sizes": [[p.ne, p.ns, p.nx] for p in probs], "generation_s": t_gen}
+    br = BatchRunner(probs, iqs, scales, iq_dtype=af.AF_IQ_BF16, device=dev)
+    for name, sur in (("bf16", False), ("surrogate_bf16", True)):
+        if sur:
+            t1 = time.perf_counter()
+            for plan in br.plans:
+                plan.surrogate_train(n_samples=2_000_000, epochs=2, tiles_per_step=32, lr=2e-3, seed=11)
+                plan.surrogate_enable(True)
+            torch.cuda.synchronize(dev)
+            res["surrogate_train_s"] = time.perf_counter() - t1
+        br.capture(n_iter)
+        br.reset()
+        br.replay()                                   # warm replay
+        torch.cuda.synchronize(dev)
+        br.reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        br.replay()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        res[name] = {"iterations_per_s": len(probs) * n_iter / (ms * 1e-3), "job_ms": ms,
+                     "numeric_ok": all(pl.af_sync_status() == af.AF_OK for pl in br.plans)}
+    return res
 
 
 # ---------------------------------------------------------------- our arm

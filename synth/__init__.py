@@ -367,3 +367,26 @@ def segment_time(medium: Medium, ax, az, bx, bz) -> float:
 
 def threads() -> int:
     return _load().sy_threads()
+
+
+def config_batch_member(k: int, seed: int = 20261206, **over) -> Problem:
+    """Member k of the batched workload: seeded uneven sizes (96-192 elements in
+    steps of 16, 2048-4096 samples, 80-160 mm deepest patch, 64^2-128^2 grid) with a
+    layered medium drawn like the full-size one."""
+    rng = np.random.default_rng(seed + 7919 * k)
+    ne = int(rng.choice(np.arange(96, 193, 16)))
+    ns = int(rng.integers(2048, 4097) // 64 * 64)
+    depth = float(rng.uniform(80e-3, 160e-3))
+    ng = int(rng.choice([64, 80, 96, 112, 128]))
+    fs = 14e6
+    # keep the deepest round trip inside the record
+    depth = min(depth, 0.9 * ns / fs * 1540.0 / 2.0 - 5e-3)
+    h_fat = rng.uniform(10e-3, 25e-3)
+    medium = Medium(speeds=[1600.0, 1440.0, 1560.0], base=[3e-3, 3e-3 + h_fat], amp=[0.0, 3e-3],
+                    period=[0.0, 20e-3], phase=[0.0, rng.uniform(0, 2 * np.pi)])
+    hyper = dict(TABLE2["invivo_c5"], lr=TABLE2["phantom_c5"]["lr"])
+    kw = dict(ne=ne, radius=60e-3, pitch=0.35e-3, fc=3.5e6, d_lens=1.2e-3, c_lens=1000.0, ns=ns, fs=fs,
+              nx=ng, nz=ng, n_ang=20, n_rad=20, patch_w=9, depth_min=10e-3, depth_max=depth,
+              sub_width=8, hyper=hyper, medium=medium)
+    kw.update(over)
+    return curvilinear_problem(f"batch{k}_ne{ne}_ns{ns}", **kw)
