@@ -60,7 +60,6 @@ size_t padded_grid_bytes(const af_config *c)
     return (size_t)padded_pitch(c->nx) * (size_t)(c->nz + 4) * sizeof(float);
 }
 
-constexpr size_t kMaxGridSmem = 200 * 1024;
 
 // Run one stage launcher, bracketed by events when timing is on.
 template <typename F>
@@ -127,7 +126,7 @@ af_status af_check_config(const af_config *c)
     if (c->n_patch < 0 || c->patch_npix < 1) return fail(AF_ERR_SHAPE, "n_patch %d / patch_npix %d", c->n_patch, c->patch_npix);
     if (c->n_patch > 0 && (!c->pix_x || !c->pix_z)) return fail(AF_ERR_ARG, "pix_x / pix_z is NULL");
     if (c->nx < 2 || c->nz < 2) return fail(AF_ERR_SHAPE, "grid %d x %d smaller than 2 x 2", c->nx, c->nz);
-    if (padded_grid_bytes(c) > kMaxGridSmem) return fail(AF_ERR_UNSUPPORTED, "grid %d x %d does not fit in shared memory", c->nx, c->nz);
+    if (padded_grid_bytes(c) > kMaxGridSmemBytes) return fail(AF_ERR_UNSUPPORTED, "grid %d x %d does not fit in shared memory", c->nx, c->nz);
     if (!(c->dx > 0) || !(c->dz > 0) || !is_fin(c->x0) || !is_fin(c->z0)) return fail(AF_ERR_ARG, "bad grid spacing / origin");
     if (c->nseg < 1) return fail(AF_ERR_ARG, "nseg = %d < 1", c->nseg);
     if (c->n_samp < 2) return fail(AF_ERR_SHAPE, "n_samp = %d < 2", c->n_samp);

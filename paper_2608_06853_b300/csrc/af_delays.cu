@@ -232,7 +232,9 @@ __global__ void export_delays_kernel(AfGeom g, const float4 *__restrict__ D, dou
 int delays_blocks_per_sm(size_t smem)
 {
     int n = 0;
-    cudaFuncSetAttribute(delays_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the attribute is per function, shared by every plan: set it to the largest
+    // grid any plan may use, the occupancy query uses this plan's size
+    cudaFuncSetAttribute(delays_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxGridSmemBytes);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, delays_kernel, 256, smem);
     return n > 0 ? n : 1;
 }

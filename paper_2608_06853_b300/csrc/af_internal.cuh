@@ -35,6 +35,7 @@ struct AfGeom {
 };
 
 constexpr int kTimingCap = 4096;   // recorded stage launches per timing window
+constexpr size_t kMaxGridSmemBytes = 200 * 1024;   // largest padded slowness grid held in shared memory
 
 // lens-surrogate MLP: parameter count (4->128->128->128->2) and normalisation
 #define AF_MLP_NPARAM 33922

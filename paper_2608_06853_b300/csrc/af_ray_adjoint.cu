@@ -207,7 +207,9 @@ __global__ void __launch_bounds__(256) adam_kernel(AfGeom g, const float *__rest
 int rayadj_blocks_per_sm(size_t smem)
 {
     int n = 0;
-    cudaFuncSetAttribute(ray_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the attribute is per function, shared by every plan: set it to the largest
+    // grid any plan may use, the occupancy query uses this plan's size
+    cudaFuncSetAttribute(ray_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxGridSmemBytes);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ray_adjoint_kernel, 256, smem);
     return n > 0 ? n : 1;
 }

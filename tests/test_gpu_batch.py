@@ -24,13 +24,19 @@ def test_graph_replay_matches_eager_for_uneven_batch():
     br.reset()
     br.run_eager(5)
     torch.cuda.synchronize()
-    eager = [x.cpu().numpy().copy() for x in br.s]
+    eager_s = [x.cpu().numpy().copy() for x in br.s]
+    eager_g = [x.cpu().numpy().copy() for x in br.g]
+    eager_l = [x.cpu().numpy().copy() for x in br.loss]
     br.capture(5)
     br.reset()
     br.replay()
     torch.cuda.synchronize()
-    graph = [x.cpu().numpy() for x in br.s]
-    for a, b in zip(eager, graph):
-        # float atomics in the adjoint may reorder: compare to float32 rounding scale
-        np.testing.assert_allclose(b, a, rtol=1e-4)
-        assert np.isfinite(b).all()
+    for k in range(len(problems)):
+        s, g, l = br.s[k].cpu().numpy(), br.g[k].cpu().numpy(), br.loss[k].cpu().numpy()
+        assert np.isfinite(s).all()
+        # float atomics in the adjoint may reorder the last bits; Adam's per-node
+        # normalisation can turn that into a fraction of one step on near-zero gradients
+        np.testing.assert_allclose(l, eager_l[k], rtol=1e-4)
+        assert np.linalg.norm(g - eager_g[k]) <= 1e-3 * np.linalg.norm(eager_g[k])
+        step = problems[k].lr / problems[k].c_ref
+        assert np.abs(s - eager_s[k]).max() <= 0.25 * step
