@@ -21,22 +21,33 @@ def test_graph_replay_matches_eager_for_uneven_batch():
     sizes = {(p.ne, p.ns, p.nx) for p in problems}
     assert len(sizes) == 3                                    # uneven
     br = BatchRunner(problems, iqs)
-    br.reset()
-    br.run_eager(5)
-    torch.cuda.synchronize()
-    eager_s = [x.cpu().numpy().copy() for x in br.s]
-    eager_g = [x.cpu().numpy().copy() for x in br.g]
-    eager_l = [x.cpu().numpy().copy() for x in br.loss]
-    br.capture(5)
-    br.reset()
-    br.replay()
-    torch.cuda.synchronize()
+
+    def run(n, graph):
+        br.reset()
+        if graph:
+            br.capture(n)
+            br.reset()
+            br.replay()
+        else:
+            br.run_eager(n)
+        torch.cuda.synchronize()
+        return ([x.cpu().numpy().copy() for x in br.s], [x.cpu().numpy().copy() for x in br.g],
+                [x.cpu().numpy().copy() for x in br.loss])
+
+    # one iteration: the forward is deterministic, the adjoint differs only by the
+    # order of float atomic additions
+    s1e, g1e, l1e = run(1, False)
+    s1g, g1g, l1g = run(1, True)
     for k in range(len(problems)):
-        s, g, l = br.s[k].cpu().numpy(), br.g[k].cpu().numpy(), br.loss[k].cpu().numpy()
-        assert np.isfinite(s).all()
-        # float atomics in the adjoint may reorder the last bits; Adam's per-node
-        # normalisation can turn that into a fraction of one step on near-zero gradients
-        np.testing.assert_allclose(l, eager_l[k], rtol=1e-4)
-        assert np.linalg.norm(g - eager_g[k]) <= 1e-3 * np.linalg.norm(eager_g[k])
+        np.testing.assert_allclose(l1g[k], l1e[k], rtol=1e-6)
+        assert np.linalg.norm(g1g[k] - g1e[k]) <= 1e-4 * np.linalg.norm(g1e[k])
+    # five iterations: Adam's per-node normalisation can turn rounding-level gradient
+    # differences on near-zero gradients into a fraction of a step; bound the divergence
+    s5e, _, l5e = run(5, False)
+    s5g, _, l5g = run(5, True)
+    for k in range(len(problems)):
         step = problems[k].lr / problems[k].c_ref
-        assert np.abs(s - eager_s[k]).max() <= 0.25 * step
+        d = np.abs(s5g[k] - s5e[k])
+        assert np.isfinite(s5g[k]).all()
+        assert d.max() <= 2.0 * step and np.median(d) <= 0.01 * step
+        np.testing.assert_allclose(l5g[k], l5e[k], rtol=1e-2)
