@@ -144,6 +144,13 @@ af_status af_iterate(af_plan_t plan, const void *d_iq, const float *d_iq_scale,
 /* Release the plan's device memory.  NULL is accepted. */
 af_status af_destroy(af_plan_t plan);
 
+/* Move the image points of a plan (same n_patch x patch_npix, host arrays, read
+ * during the call).  Used by the global-speed sweep of Sec. II-C / III-A, whose
+ * dynamic grid scales pixel and kernel positions with the active speed.  The
+ * same validation as af_plan applies (inside the grid box, outside the lens);
+ * synchronises the plan's stream. */
+af_status af_set_pixels(af_plan_t plan, const double *pix_x, const double *pix_z);
+
 /* Waits for the plan's stream and returns AF_ERR_NUMERIC if a kernel flagged
  * a non-positive or non-finite slowness since the last call, else AF_OK. */
 af_status af_sync_status(af_plan_t plan);

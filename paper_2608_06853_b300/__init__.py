@@ -76,6 +76,7 @@ _SIGNATURES = {
     "af_iterate": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
     "af_destroy": (ctypes.c_int, [_VP]),
     "af_sync_status": (ctypes.c_int, [_VP]),
+    "af_set_pixels": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "af_get_delays": (ctypes.c_int, [_VP, _VP, _VP]),
     "af_get_exit_angles": (ctypes.c_int, [_VP, _VP]),
     "af_get_images": (ctypes.c_int, [_VP, _VP]),
@@ -267,6 +268,11 @@ class Plan:
 
     def af_sync_status(self) -> int:
         return self.lib.af_sync_status(self.handle)
+
+    def af_set_pixels(self, pix_x, pix_z):
+        x = np.ascontiguousarray(pix_x, np.float64)
+        z = np.ascontiguousarray(pix_z, np.float64)
+        _check(self.lib.af_set_pixels(self.handle, x.ctypes.data_as(_dp), z.ctypes.data_as(_dp)), "af_set_pixels")
 
     # ---- introspection ----
     def _dev(self):

@@ -219,6 +219,8 @@ af_status af_destroy(af_plan_t pl)
                     pl->mlp_p, pl->mlp_m, pl->mlp_v, pl->mlp_g, pl->mlp_w2b, pl->mlp_w3b, pl->sur_fb};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    delete[] pl->host_ex;
+    delete[] pl->host_ez;
     delete pl;
     return AF_OK;
 }
@@ -233,6 +235,14 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
     af_plan_t pl = new af_plan_s();
     memset(pl, 0, sizeof(*pl));
     pl->stream = (cudaStream_t)stream;
+    pl->cfg = *c;
+    pl->host_ex = new double[c->n_elem];
+    pl->host_ez = new double[c->n_elem];
+    memcpy(pl->host_ex, c->elem_x, sizeof(double) * c->n_elem);
+    memcpy(pl->host_ez, c->elem_z, sizeof(double) * c->n_elem);
+    pl->cfg.elem_x = pl->host_ex;
+    pl->cfg.elem_z = pl->host_ez;
+    pl->cfg.pix_x = pl->cfg.pix_z = nullptr;
     pl->iq_dtype = c->iq_dtype;
     AfGeom &g = pl->g;
     const int ne = c->n_elem, npix = c->n_patch * c->patch_npix;
@@ -469,6 +479,32 @@ af_status af_iterate(af_plan_t pl, const void *iq, const float *scale, float *s,
     st = af_adjoint(pl, grad);
     if (st != AF_OK) return st;
     return af_step(pl, grad, s, m, v, step);
+}
+
+af_status af_set_pixels(af_plan_t pl, const double *px, const double *pz)
+{
+    g_err[0] = 0;
+    if (!pl) return fail(AF_ERR_ARG, "plan is NULL");
+    af_config c = pl->cfg;
+    c.pix_x = px;
+    c.pix_z = pz;
+    af_status st = af_check_config(&c);
+    if (st != AF_OK) return st;
+    const int npix = pl->g.npix;
+    std::vector<float2> pix((size_t)npix), pix_pol((size_t)npix);
+    for (int p = 0; p < npix; ++p) {
+        pix[p] = make_float2((float)px[p], (float)pz[p]);
+        const double vx = px[p] - c.arc_cx, vz = pz[p] - c.arc_cz;
+        pix_pol[p] = make_float2((float)atan2(vx, vz), (float)hypot(vx, vz));
+    }
+    AF_CUDA(cudaStreamSynchronize(pl->stream));
+    if (npix) {
+        AF_CUDA(cudaMemcpy(pl->pix, pix.data(), npix * sizeof(float2), cudaMemcpyHostToDevice));
+        AF_CUDA(cudaMemcpy(pl->pix_pol, pix_pol.data(), npix * sizeof(float2), cudaMemcpyHostToDevice));
+    }
+    pl->have_phi = false;        // exit angles of the old pixels are no warm start
+    pl->have_fwd = false;
+    return AF_OK;
 }
 
 af_status af_sync_status(af_plan_t pl)

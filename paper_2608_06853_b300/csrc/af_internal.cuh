@@ -68,6 +68,8 @@ struct AfScal {
 
 struct af_plan_s {
     AfGeom g;
+    af_config cfg;       // scalar copy of the configuration (host pointers cleared)
+    double *host_ex, *host_ez;   // element positions kept for re-validation
     cudaStream_t stream;
     int device, sm_count;
     size_t smem_grid;    // bytes of the padded slowness grid in shared memory
