@@ -174,6 +174,13 @@ af_status af_get_images(af_plan_t plan, float *d_B);
  * Any pointer may be NULL.  Synchronises the plan's stream. */
 af_status af_get_cmpe(af_plan_t plan, float *d_z, uint8_t *d_mask, int *h_n_active);
 
+/* Images of the last af_forward, [npix] float each (either may be NULL):
+ *  d_bmode       |sum_ij B_ij(p)|, the full-aperture DAS envelope (Figs. 2, 4);
+ *  d_cmpe_image  integrated CMPE (Sec. IV): sum over the common-midpoint pairs
+ *                of |arg(B_ij(p) conj(B_i+1,j-1(p)))|, per pixel.
+ * A plan over a dense pixel grid gives the full field of view. */
+af_status af_get_bmode(af_plan_t plan, float *d_bmode, float *d_cmpe_image);
+
 /* dL/dB[b][p] (= dL/dRe B + j dL/dIm B) of the last af_adjoint,
  * [nsub*nsub][npix][2] float. */
 af_status af_get_image_grad(af_plan_t plan, float *d_G);

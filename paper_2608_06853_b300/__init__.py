@@ -82,6 +82,7 @@ _SIGNATURES = {
     "af_get_images": (ctypes.c_int, [_VP, _VP]),
     "af_get_cmpe": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_int)]),
     "af_get_image_grad": (ctypes.c_int, [_VP, _VP]),
+    "af_get_bmode": (ctypes.c_int, [_VP, _VP, _VP]),
     "af_get_delay_grad": (ctypes.c_int, [_VP, _VP]),
     "af_get_counters": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
     "af_cmpe_loss_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -309,6 +310,14 @@ class Plan:
         n = ctypes.c_int()
         _check(self.lib.af_get_cmpe(self.handle, _ptr(z), _ptr(m), ctypes.byref(n)), "af_get_cmpe")
         return torch.view_as_complex(z)[:, : self.npair], m[:, : self.npair], n.value
+
+    def bmode(self):
+        """(|sum_ij B_ij| [npix], integrated CMPE image [npix]) of the last forward."""
+        import torch
+        b = torch.empty(self.npix, dtype=torch.float32, device=self._dev())
+        c = torch.empty_like(b)
+        _check(self.lib.af_get_bmode(self.handle, _ptr(b), _ptr(c)), "af_get_bmode")
+        return b, c
 
     def image_grad(self):
         """dL/dB [nsub*nsub][npix] complex64 of the last adjoint."""

@@ -575,6 +575,15 @@ af_status af_get_image_grad(af_plan_t pl, float *G)
     return AF_OK;
 }
 
+af_status af_get_bmode(af_plan_t pl, float *bmode, float *cmpe_image)
+{
+    if (!pl) return fail(AF_ERR_ARG, "plan is NULL");
+    if (!pl->have_fwd) return fail(AF_ERR_STATE, "no forward pass yet");
+    if (pl->g.npix && !bmode && !cmpe_image) return fail(AF_ERR_ARG, "both outputs are NULL");
+    AF_CUDA(launch_images(pl, bmode, cmpe_image));
+    return AF_OK;
+}
+
 af_status af_get_delay_grad(af_plan_t pl, float *gd)
 {
     if (!pl) return fail(AF_ERR_ARG, "plan is NULL");

@@ -177,7 +177,44 @@ __global__ void __launch_bounds__(256) cmpe_backward_kernel(AfGeom g, const floa
     }
 }
 
+// Full-aperture image |sum_ij B_ij(p)| (Figs. 2, 4) and the integrated CMPE
+// image: per pixel, the sum over the common-midpoint pairs of
+// |arg(B_ij(p) conj(B_i+1,j-1(p)))| (Sec. IV).
+__global__ void __launch_bounds__(256) image_kernel(AfGeom g, const float2 *__restrict__ B,
+                                                    float *__restrict__ bmode, float *__restrict__ cimg)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.npix) return;
+    if (bmode) {
+        float re = 0.f, im = 0.f;
+        for (int b = 0; b < g.nb; ++b) {
+            const float2 v = B[(long)b * g.npix + p];
+            re += v.x;
+            im += v.y;
+        }
+        bmode[p] = sqrtf(re * re + im * im);
+    }
+    if (cimg) {
+        float acc = 0.f;
+        for (int k = 0; k < g.npair; ++k) {
+            int i, j;
+            pair_ij(k, g.nsub, i, j);
+            const float2 a = B[(long)(i * g.nsub + j) * g.npix + p];
+            const float2 c = B[(long)((i + 1) * g.nsub + (j - 1)) * g.npix + p];
+            acc += fabsf(atan2f(fmaf(a.y, c.x, -a.x * c.y), fmaf(a.x, c.x, a.y * c.y)));
+        }
+        cimg[p] = acc;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_images(af_plan_t pl, float *bmode, float *cimg)
+{
+    if (pl->g.npix == 0) return cudaSuccess;
+    image_kernel<<<(pl->g.npix + 255) / 256, 256, 0, pl->stream>>>(pl->g, pl->B, bmode, cimg);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_cmpe_forward(af_plan_t pl, float *loss)
 {

@@ -189,6 +189,7 @@ cudaError_t launch_das_adjoint(af_plan_t pl);
 cudaError_t launch_ray_adjoint(af_plan_t pl, const float *s, float *grad);
 cudaError_t launch_adam(af_plan_t pl, const float *grad, float *s, float *m, float *v, int step);
 cudaError_t launch_export_delays(af_plan_t pl, double *T, uint8_t *apod);
+cudaError_t launch_images(af_plan_t pl, float *bmode, float *cimg);
 int delays_blocks_per_sm(size_t smem);
 cudaError_t mlp_setup_attributes();
 cudaError_t mlp_refresh_bf16(af_plan_t pl);

@@ -353,3 +353,36 @@ def test_full_size_sampled_parity(full_case):
     rtv, rsv = o_full.regularizers(sd)
     assert run.L[2] == pytest.approx(rtv, rel=1e-4)
     assert run.L[3] == pytest.approx(rsv, rel=1e-4, abs=1e-9)
+
+
+def test_bmode_and_integrated_cmpe_images(tiny_case):
+    """Full-aperture envelope |sum B| and integrated CMPE against the oracle's images; a
+    point scatterer at the true speed is the brightest pixel of its patch with zero
+    integrated phase error."""
+    p, psi = tiny_case
+    run = Run(p, psi, smooth_speed(p, 9))
+    b, c = run.plan.bmode()
+    b, c = b.cpu().numpy(), c.cpu().numpy()
+    o = oracle.Oracle(p)
+    T, _, _ = o.delays(smooth_speed(p, 9).astype(np.float64), apod_in=run.apod)
+    B = o.das(psi, T, run.apod)
+    np.testing.assert_allclose(b, np.abs(B.sum(0)), rtol=2e-4, atol=1e-4 * np.abs(B.sum(0)).max())
+    pr = o.pairs()
+    ref_c = np.abs(np.angle(B[pr[:, 0]] * np.conj(B[pr[:, 1]]))).sum(0)
+    # phases of near-zero cross products are ill-conditioned: compare where they are not
+    mag = np.abs(B[pr[:, 0]] * np.conj(B[pr[:, 1]])).min(0)
+    ok = mag > 1e-3 * mag.max()
+    np.testing.assert_allclose(c[ok], ref_c[ok], rtol=1e-3, atol=1e-3)
+    # point scatterer
+    q = synth.config_tiny(n_ang=3, n_rad=3, patch_w=3)
+    q.medium = synth.Medium(speeds=[1540.0])
+    P = 4
+    centre = P * q.patch_npix + q.patch_npix // 2
+    T1 = synth.oneway_times(q, np.array([q.pix_x[centre]]), np.array([q.pix_z[centre]]))
+    psi1 = synth.echoes(q, T1, np.array([1.0]))
+    run1 = Run(q, psi1, q.initial_slowness(1540.0))
+    b1, c1 = run1.plan.bmode()
+    b1, c1 = b1.cpu().numpy(), c1.cpu().numpy()
+    patch = slice(P * q.patch_npix, (P + 1) * q.patch_npix)
+    assert int(np.argmax(b1[patch])) == q.patch_npix // 2
+    assert c1[centre] < 1e-3
