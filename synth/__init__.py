@@ -200,7 +200,7 @@ def curvilinear_problem(name: str, *, ne: int, radius: float, pitch: float, fc: 
                         sub_width: int, hyper: dict, medium: Optional[Medium] = None,
                         t_ttp: float = 0.0, t0: float = 0.0, lens_mode: int = 0,
                         apod_mode: int = 0, sector_frac: float = 0.8,
-                        grid_margin: float = 2e-3) -> Problem:
+                        grid_margin: float = 2e-3, cover_speeds: Optional[tuple] = None) -> Problem:
     """Curvilinear array on an arc of `radius` about (0, -radius) (apex at the origin),
     a concentric lens shell of thickness d_lens, and a regular polar grid of square
     patches of patch_w x patch_w pixels at lambda/2 (lambda at 1540 m/s)."""
@@ -227,14 +227,28 @@ def curvilinear_problem(name: str, *, ne: int, radius: float, pitch: float, fc: 
                     pz.append(q[1])
     px = f32(np.array(px))
     pz = f32(np.array(pz))
+    # grid box also covering the patches as moved by a global-speed sweep over
+    # cover_speeds (depths below the lens and in-patch offsets scaled by c / C_REF)
+    bx, bz = [px], [pz]
+    if cover_speeds is not None:
+        qx = px.reshape(n_ang * n_rad, patch_w * patch_w)
+        qz = pz.reshape(n_ang * n_rad, patch_w * patch_w)
+        ccx, ccz = qx.mean(1, keepdims=True), qz.mean(1, keepdims=True)
+        rho = np.hypot(ccx - cx, ccz - cz)
+        for c in cover_speeds:
+            k = c / C_REF
+            r2 = RL + (rho - RL) * k
+            bx.append((cx + r2 * (ccx - cx) / rho + k * (qx - ccx)).ravel())
+            bz.append((cz + r2 * (ccz - cz) / rho + k * (qz - ccz)).ravel())
+    bx, bz = np.concatenate(bx), np.concatenate(bz)
     # grid: bounding box of the lens surface over the aperture and every pixel
     lens_th = np.linspace(th[0], th[-1], 64) if ne > 1 else np.zeros(1)
     lx = cx + RL * np.sin(lens_th)
     lz = cz + RL * np.cos(lens_th)
-    xmin = min(px.min(), lx.min(), ex.min()) - grid_margin
-    xmax = max(px.max(), lx.max(), ex.max()) + grid_margin
-    zmin = min(pz.min(), lz.min(), ez.min()) - grid_margin
-    zmax = max(pz.max(), lz.max()) + grid_margin
+    xmin = min(bx.min(), lx.min(), ex.min()) - grid_margin
+    xmax = max(bx.max(), lx.max(), ex.max()) + grid_margin
+    zmin = min(bz.min(), lz.min(), ez.min()) - grid_margin
+    zmax = max(bz.max(), lz.max()) + grid_margin
     dx = float(f32((xmax - xmin) / (nx - 1)))
     dz = float(f32((zmax - zmin) / (nz - 1)))
     return Problem(

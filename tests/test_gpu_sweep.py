@@ -23,7 +23,7 @@ def test_dynamic_pixels_scale_depth_and_spacing():
 
 
 def test_sweep_matches_oracle_and_picks_an_interior_speed():
-    p = synth.config_tiny()
+    p = synth.config_tiny(cover_speeds=(1400.0, 1660.0))
     psi = synth.simulate(p, 20000, seed=20261207)
     dev = torch.device("cuda")
     plan = af.Plan(p)
