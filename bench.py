@@ -163,8 +163,7 @@ def run_reference(args, rank, world):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
 # capture of the full workload, per kernel; None once the kernel changed after the
 # capture (see profiles/).
-NCU_TRAFFIC = {"das_forward": 436.6e6 + 60.7e6, "das_adjoint": 505.3e6 + 14.7e6,
-               "ray_adjoint": 30.9e6 + 8.1e6, "delays": None}
+NCU_TRAFFIC = {"das_forward": None, "das_adjoint": None, "ray_adjoint": None, "delays": None}
 
 # algorithmic FP32 lane-operations per ray point, from the arithmetic of the method:
 # position (2) + cell and fraction (4) + two Keys weight sets (2 x 10) + 16 taps and 4

@@ -76,7 +76,8 @@ enum { AF_APOD_FNUMBER = 0,  /* |x'| <= z' / (2F), z' > 0 (usual f-number readin
  *   (pixel p belongs to patch p / patch_npix), at (pix_x[p], pix_z[p]).
  * Slowness grid (Sec. III-A): node (i, j) at (x0 + i dx, z0 + j dz),
  *   stored row-major s[j * nx + i]; Keys bicubic interpolation; nseg ray
- *   segments (nseg + 1 endpoints) from the exit point to the pixel.
+ *   segments (nseg + 1 endpoints) from the exit point to the pixel,
+ *   1 <= nseg <= AF_MAX_NSEG (larger values: AF_ERR_UNSUPPORTED).
  *   Every pixel and the lens surface over the aperture must lie inside the
  *   grid box.
  * Channel data Psi[t][r][n] (Eq. 5): n_samp samples per (transmit, receive)
@@ -86,6 +87,8 @@ enum { AF_APOD_FNUMBER = 0,  /* |x'| <= z' / (2F), z' > 0 (usual f-number readin
  * Table II: rho_thresh, fnum, nseg, w1, kx1, kz1, w2, kx2, kz2, lr.
  * Adam (Eq. 9 as Adam): beta1, beta2, eps on u = s * c_ref.
  */
+#define AF_MAX_NSEG 65535
+
 typedef struct {
     int n_elem;
     const double *elem_x, *elem_z;

@@ -129,6 +129,7 @@ af_status af_check_config(const af_config *c)
     if (padded_grid_bytes(c) > kMaxGridSmemBytes) return fail(AF_ERR_UNSUPPORTED, "grid %d x %d does not fit in shared memory", c->nx, c->nz);
     if (!(c->dx > 0) || !(c->dz > 0) || !is_fin(c->x0) || !is_fin(c->z0)) return fail(AF_ERR_ARG, "bad grid spacing / origin");
     if (c->nseg < 1) return fail(AF_ERR_ARG, "nseg = %d < 1", c->nseg);
+    if (c->nseg > AF_MAX_NSEG) return fail(AF_ERR_UNSUPPORTED, "nseg = %d > %d", c->nseg, AF_MAX_NSEG);
     if (c->n_samp < 2) return fail(AF_ERR_SHAPE, "n_samp = %d < 2", c->n_samp);
     if (!(c->fs > 0) || !is_fin(c->fs) || !is_fin(c->fd) || !is_fin(c->t0) || !is_fin(c->t_ttp))
         return fail(AF_ERR_ARG, "bad fs / fd / t0 / t_ttp");
@@ -300,13 +301,14 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
     }
     {
         // one ray adds at most |dL/dT| (5 cell diagonals + L / (N + 1)) to a node; a flush
-        // window holds 8 rounds of 256 rays; single contributions stay below 2^21
+        // window holds kRayFlushRays rays; one point's contribution stays below 2^20, so
+        // the merged stencil of a work item (kRayGroup points) stays below 2^22
         const double diag = sqrt(c->dx * c->dx + c->dz * c->dz);
         const double lmax = sqrt(pow((c->nx - 1) * c->dx, 2) + pow((c->nz - 1) * c->dz, 2));
         const double per_ray = 5.0 * diag + lmax / (c->nseg + 1);
-        const double window = 8.0 * 256.0 * per_ray;
+        const double window = kRayFlushRays * per_ray;
         const double s1 = ldexp(1.0, 30) / window;
-        const double s2 = ldexp(1.0, 21) * (c->nseg + 1) / lmax;
+        const double s2 = ldexp(1.0, 20) * (c->nseg + 1) / lmax;
         g.fix_scale = (float)fmin(s1, s2);
     }
     g.c_ref = (float)c->c_ref;
@@ -403,9 +405,9 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
     AF_ALLOC(pl->scal, sizeof(AfScal));
     pl->smem_grid = padded_grid_bytes(c);
     pl->delay_blocks = pl->sm_count * delays_blocks_per_sm(pl->smem_grid);
-    pl->rayadj_blocks = pl->sm_count * rayadj_blocks_per_sm(pl->smem_grid);
-    AF_ALLOC(pl->gpart, (size_t)pl->rayadj_blocks * g.ng * sizeof(float));
-    AF_ALLOC(pl->gpad, (size_t)pl->rayadj_blocks * pl->smem_grid);
+    pl->rayadj = rayadj_shape(c->nx, c->nz, g.pitch, pl->sm_count);
+    AF_ALLOC(pl->gpart, (size_t)pl->rayadj.blocks * g.ng * sizeof(long long));
+    AF_ALLOC(pl->gpad, (size_t)pl->rayadj.blocks * (pl->smem_grid / sizeof(float)) * sizeof(long long));
     AF_ALLOC(pl->mlp_p, AF_MLP_NPARAM * sizeof(float));
     AF_ALLOC(pl->mlp_m, AF_MLP_NPARAM * sizeof(float));
     AF_ALLOC(pl->mlp_v, AF_MLP_NPARAM * sizeof(float));

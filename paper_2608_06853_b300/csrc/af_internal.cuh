@@ -37,6 +37,19 @@ struct AfGeom {
 constexpr int kTimingCap = 4096;   // recorded stage launches per timing window
 constexpr size_t kMaxGridSmemBytes = 200 * 1024;   // largest padded slowness grid held in shared memory
 
+// ray adjoint: pixels per work item, items between fixed-point flushes (the
+// window the fixed-point scale is sized for), and the largest pair of integer
+// grid copies it keeps in shared memory
+constexpr int kRayGroup = 3;
+constexpr int kRayItemsPerFlush = 1024;
+constexpr double kRayFlushRays = (double)kRayItemsPerFlush * kRayGroup;
+constexpr size_t kRayDualMaxBytes = 180 * 1024;
+struct RayAdjShape {
+    bool dual;           // two grid copies (row pitch 1 and 31 mod 32) or one
+    int threads, blocks;
+    size_t smem;         // dynamic shared memory per CTA
+};
+
 // lens-surrogate MLP: parameter count (4->128->128->128->2) and normalisation
 #define AF_MLP_NPARAM 33922
 struct MlpNorm {
@@ -64,6 +77,7 @@ struct AfScal {
     int n_apod;          // apodized (element, pixel) pairs
     int gmax_bits;       // max |dL/dT| of the last adjoint (float bits, >= 0)
     int mlp_err;         // a tensor-core completion wait of the MLP timed out
+    int ray_next;        // next item block of the ray adjoint (zero between launches)
 };
 
 struct af_plan_s {
@@ -73,7 +87,8 @@ struct af_plan_s {
     cudaStream_t stream;
     int device, sm_count;
     size_t smem_grid;    // bytes of the padded slowness grid in shared memory
-    int delay_blocks, rayadj_blocks;
+    int delay_blocks;
+    RayAdjShape rayadj;  // ray-adjoint launch shape (grid layout, threads, CTAs)
     // geometry
     float4 *elem;        // (x, z, cos theta_a, sin theta_a)  theta_a from Eq. 3
     float2 *elem_pol;    // (polar angle about the arc centre, radius)
@@ -88,8 +103,8 @@ struct af_plan_s {
     double *patch_sum;   // [n_patch] sum m |arg z|
     int *patch_cnt;      // [n_patch] sum m
     float *gdel;         // [ne][npix] dL/dT
-    float *gpart;        // [rayadj_blocks][ng] per-CTA partial gradients
-    float *gpad;         // [rayadj_blocks][padded grid] per-CTA float accumulators
+    long long *gpart;    // [rayadj.blocks][ng] per-CTA partial gradients (fixed point)
+    long long *gpad;     // [rayadj.blocks][padded grid] per-CTA fixed-point accumulators
     AfScal *scal;
     float *loss_out;     // last caller loss buffer
     const void *iq;      // last forward's inputs (kept for the adjoint)
@@ -200,4 +215,4 @@ cudaError_t mlp_train_step(af_plan_t pl, const float4 *X, const float2 *Y, long 
 cudaError_t mlp_infer(af_plan_t pl, float c_fixed, const uint8_t *fb, float *phi_out, float *tl_out);
 cudaError_t mlp_validate(af_plan_t pl, double c, const float *phi_s, const float *tl_s, double tol, uint8_t *fb,
                          unsigned long long *stats);
-int rayadj_blocks_per_sm(size_t smem);
+RayAdjShape rayadj_shape(int nx, int nz, int pitch, int sm_count);

@@ -15,62 +15,144 @@
 
 namespace {
 
-// Warp-cooperative scatter.  A warp takes 32 consecutive rays (element e,
-// pixels p..p+31), compacts the ones with a non-zero dL/dT into a per-warp
-// table, then walks their (N+1) points with lane = consecutive point index, so
-// the 16 taps of one atomic instruction land on 32 different stencils along a
-// ray (distinct addresses; the odd row pitch spreads them over the banks).
+// Scatter of the ray points.  A work item is one element and kRayGroup
+// consecutive pixels (for a 9 x 9 patch, a third of one patch row); their
+// rays run side by side, so at one step k their points usually fall in the
+// same grid cell.  A CTA takes blocks of one item per thread from a device
+// counter (blocks differ in work because of the apodization), compacts the
+// items with a non-zero dL/dT into a table, and spreads the flattened
+// (item, step) list over all its threads (lane = consecutive step along a
+// ray).  A thread sums, in registers, the 4 x 4 stencils of the item's points
+// that share the cell of its middle ray and adds them with one set of 16
+// shared-memory atomics.  A point in another cell goes to a per-warp queue,
+// which is processed 32 points at a time (one point per lane), so that these
+// points do not run as a divergent branch.
 //
-// Accumulation is int32 fixed point (shared-memory integer atomics are several
-// times faster than float ones and their sums do not depend on order): value
-// = round(c w S) with S = fix_scale / max|dL/dT|.  One ray adds at most
-// max|dL/dT| (5 cell diagonals + L/(N+1)) to a node, and fix_scale is set on
-// the host so that kRoundsPerFlush rounds of 256 rays stay below 2^30; after
-// that many rounds the integer grid is flushed into the CTA's float
-// accumulator in global memory and cleared.
-constexpr int kRayWarps = 8;
-constexpr int kRoundsPerFlush = 8;
+// Bank layout.  Along one ray the visited cells form a monotone path; with a
+// row pitch of 1 (mod 32) the bank of cell (i, j) is i + j (mod 32), so for a
+// ray going right-down (or left-up) the banks of 32 consecutive points differ
+// by their Manhattan distance and do not collide; rays going left-down use a
+// second copy of the grid with a row pitch of 31 (mod 32), bank i - j.  When
+// both copies do not fit in shared memory one copy with an odd pitch is used.
+//
+// Accumulation is fixed point: value = round(c w S), S = fix_scale /
+// max|dL/dT|.  Shared memory holds int32 (integer atomics are several times
+// faster than float ones); one ray adds at most max|dL/dT| (5 cell diagonals +
+// L/(N+1)) to a node and fix_scale is set on the host so that kRayFlushRays
+// rays stay below 2^30, so after kRayItemsPerFlush items the integer grids are
+// added into the CTA's int64 accumulator in global memory and cleared.  All
+// sums are integer sums up to the final conversion, so the result does not
+// depend on which CTA took which block.  Rounding adds 1.5 * 2^23 in the last
+// FMA of a value (|value| < 2^22), so each partial sum is rounded to an integer.
+struct RayGrid {
+    int width, rows;        // padded grid: nx + 4 columns, nz + 4 rows
+    int pa, pb, base_b;     // row pitch of copy A (and B), offset of copy B
+};
 
-__device__ __forceinline__ int round_to_int(float v)     // |v| < 2^22
+constexpr float kRound = 12582912.0f;   // 1.5 * 2^23
+constexpr int kRoundBits = 0x4B400000;
+constexpr int kLeadRay = kRayGroup / 2; // the middle ray of an item
+
+// padded cell of point k of a ray (gx0, gz0, gdx, gdz) and its Keys weights
+__device__ __forceinline__ void ray_stencil(const AfGeom &g, float k, float4 ry, int &ic, int &jc, float wx[4],
+                                            float wz[4])
 {
-    return __float_as_int(v + 12582912.0f) - 0x4B400000;
+    const float gx = fmaf(k, ry.z, ry.x), gz = fmaf(k, ry.w, ry.y);
+    const float fx = floorf(gx), fz = floorf(gz);
+    ic = min(max((int)fx, -1), g.nx - 1) + 1;
+    jc = min(max((int)fz, -1), g.nz - 1) + 1;
+    keys_weights(gx - fx, wx);
+    keys_weights(gz - fz, wz);
 }
 
-__global__ void __launch_bounds__(256) ray_adjoint_kernel(AfGeom g, const float4 *__restrict__ elem,
-                                                          const float2 *__restrict__ pix,
-                                                          const float *__restrict__ phi,
-                                                          const float *__restrict__ gdel,
-                                                          const AfScal *__restrict__ scal,
-                                                          float *__restrict__ gpad,
-                                                          float *__restrict__ gpart)
+// 16 atomics of one stencil whose values carry the rounding constant
+__device__ __forceinline__ void add_stencil(int *row, int pitch, const float (&W)[16])
 {
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) atomicAdd(row + b * pitch + a, __float_as_int(W[b * 4 + a]) - kRoundBits);
+}
+
+__device__ __forceinline__ float pick_c(const float4 &cc, int m)
+{
+    return m == 0 ? cc.x : (m == 1 ? cc.y : cc.z);
+}
+
+// one queued point: entry = (item << 18) | (step << 2) | ray
+__device__ __forceinline__ void run_queued(const AfGeom &g, int ent, int *acci, const float4 *rays, int T,
+                                           const float4 *rayc, const int2 *rayb)
+{
+    const int r = ent >> 18, k = (ent >> 2) & 0xFFFF, m = ent & 3;
+    const float4 cc = rayc[r];
+    const int2 gb = rayb[r];
+    const float cm = pick_c(cc, m);
+    float wx[4], wz[4], W[16];
+    int i1, j1;
+    ray_stencil(g, (float)k, rays[m * T + r], i1, j1, wx, wz);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const float cb = cm * wz[b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) W[b * 4 + a] = fmaf(cb, wx[a], kRound);
+    }
+    add_stencil(acci + gb.x + j1 * gb.y + i1, gb.y, W);
+}
+
+template <int WARPS, bool DUAL>
+__global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGrid rg,
+                                                                 const float4 *__restrict__ elem,
+                                                                 const float2 *__restrict__ pix,
+                                                                 const float *__restrict__ phi,
+                                                                 const float *__restrict__ gdel,
+                                                                 AfScal *__restrict__ scal,
+                                                                 long long *__restrict__ gpad,
+                                                                 long long *__restrict__ gpart)
+{
+    constexpr int T = WARPS * 32;                    // threads = items per block
+    constexpr int kQueue = 96;                       // < 32 carried + 2 x 32 new
     extern __shared__ int acci[];
-    __shared__ float4 rays[kRayWarps][32];      // (gx0, gz0, gdx, gdz)
-    __shared__ float rayc[kRayWarps][32];       // dL/dT |q - r| / (N + 1), scaled
-    const int P = g.pitch, rows = g.nz + 4, npad = P * rows;
-    for (int k = threadIdx.x; k < npad; k += blockDim.x) acci[k] = 0;
-    float *mypad = gpad + (long)blockIdx.x * npad;
-    for (int k = threadIdx.x; k < npad; k += blockDim.x) mypad[k] = 0.0f;
+    __shared__ float4 rays[kRayGroup * T];           // (gx0, gz0, gdx, gdz), ray m of item r at m * T + r
+    __shared__ float4 rayc[T];                       // dL/dT |q - r| / (N + 1), scaled; .w unused
+    __shared__ int2 rayb[T];                         // grid copy: (base, row pitch)
+    __shared__ int fq[WARPS][kQueue];                // queued points
+    __shared__ int wcount[WARPS];
+    __shared__ long s_blk;
+    const int P = g.pitch, npad = P * rg.rows;
+    const int nacc = DUAL ? rg.base_b + rg.pb * rg.rows : rg.pa * rg.rows;
+    for (int k = threadIdx.x; k < nacc; k += T) acci[k] = 0;
+    long long *mypad = gpad + (long)blockIdx.x * npad;
+    for (int k = threadIdx.x; k < npad; k += T) mypad[k] = 0;
     const float gmax = __int_as_float(scal->gmax_bits);
     const float S = gmax > 0.0f ? g.fix_scale / gmax : 0.0f;
-    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int npts = g.nseg + 1;
-    const long total = (long)g.ne * g.npix;
-    const long nchunks = (total + 31) / 32;
-    // chunks of this CTA: blockIdx.x * 8 + warp + round * gridDim.x * 8
-    const long per_round = (long)gridDim.x * kRayWarps;
-    const long first = (long)blockIdx.x * kRayWarps;
-    const long nrounds = first < nchunks ? (nchunks - first + per_round - 1) / per_round : 0;
-    for (long round = 0; round < nrounds && S > 0.0f; ++round) {
-        const long chunk = first + round * per_round + warp;
-        const long idx = chunk * 32 + lane;
-        float c = 0.0f;
-        float4 rp = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (chunk < nchunks && idx < total) {
-            const float gv = gdel[idx];
-            if (gv != 0.0f) {
-                const int e = (int)(idx / g.npix), p = (int)(idx - (long)e * g.npix);
+    const int ngroups = (g.npix + kRayGroup - 1) / kRayGroup;
+    const long nitems = (long)g.ne * ngroups;
+    const long nblk = S > 0.0f ? (nitems + T - 1) / T : 0;
+    constexpr int kBlocksPerFlush = kRayItemsPerFlush / T;
+    if (threadIdx.x == 0) s_blk = atomicAdd(&scal->ray_next, 1);
+    __syncthreads();
+    long blk = s_blk;
+    int since_flush = 0;
+    while (blk < nblk) {
+        const long item = blk * T + threadIdx.x;
+        float c[kRayGroup];
+        float4 rp[kRayGroup];
+        bool any = false;
+#pragma unroll
+        for (int m = 0; m < kRayGroup; ++m) {
+            c[m] = 0.0f;
+            rp[m] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (item < nitems) {
+            const int e = (int)(item / ngroups), grp = (int)(item - (long)e * ngroups);
+#pragma unroll
+            for (int m = 0; m < kRayGroup; ++m) {
+                const int p = grp * kRayGroup + m;
+                const long idx = (long)e * g.npix + p;
+                const float gv = p < g.npix ? gdel[idx] : 0.0f;
+                if (gv == 0.0f) continue;
                 const float2 px = pix[p];
                 float qx, qz;
                 if (g.lens_mode == AF_LENS_BENT_RAY) {
@@ -84,63 +166,134 @@ __global__ void __launch_bounds__(256) ray_adjoint_kernel(AfGeom g, const float4
                     qz = el.y;
                 }
                 const float lx = px.x - qx, lz = px.y - qz;
-                c = gv * S * sqrtf(lx * lx + lz * lz) * g.inv_nseg1;
-                rp = make_float4((qx - g.x0) * g.inv_dx, (qz - g.z0) * g.inv_dz,
-                                 lx * g.inv_dx * g.inv_nseg, lz * g.inv_dz * g.inv_nseg);
+                c[m] = gv * S * sqrtf(lx * lx + lz * lz) * g.inv_nseg1;
+                rp[m] = make_float4((qx - g.x0) * g.inv_dx, (qz - g.z0) * g.inv_dz,
+                                    lx * g.inv_dx * g.inv_nseg, lz * g.inv_dz * g.inv_nseg);
+                any = any || c[m] != 0.0f;
             }
         }
-        const unsigned live = __ballot_sync(0xffffffffu, c != 0.0f);
-        const int nlive = __popc(live);
-        if (c != 0.0f) {
-            const int slot = __popc(live & ((1u << lane) - 1u));
-            rays[warp][slot] = rp;
-            rayc[warp][slot] = c;
+        // CTA-wide compaction of the live items
+        const unsigned live = __ballot_sync(0xffffffffu, any);
+        if (lane == 0) wcount[warp] = __popc(live);
+        __syncthreads();
+        int base = 0, nlive = 0;
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) {
+            const int n = wcount[w];
+            base += w < warp ? n : 0;
+            nlive += n;
         }
-        __syncwarp();
+        if (any) {
+            const int slot = base + __popc(live & ((1u << lane) - 1u));
+            // path of the lead: the middle ray if live, else the first live one
+            float4 rl = rp[kLeadRay];
+            if (c[kLeadRay] == 0.0f) {
+#pragma unroll
+                for (int m = kRayGroup - 1; m >= 0; --m)
+                    if (c[m] != 0.0f) rl = rp[m];
+            }
+            // dead rays take the lead's path (weight 0), so they always merge
+#pragma unroll
+            for (int m = 0; m < kRayGroup; ++m) rays[m * T + slot] = c[m] != 0.0f ? rp[m] : rl;
+            rayc[slot] = make_float4(c[0], kRayGroup > 1 ? c[1] : 0.f, kRayGroup > 2 ? c[2] : 0.f, 0.f);
+            const bool right_down = rl.z * rl.w >= 0.0f;
+            rayb[slot] = DUAL && !right_down ? make_int2(rg.base_b, rg.pb) : make_int2(0, rg.pa);
+        }
+        if (threadIdx.x == 0) s_blk = atomicAdd(&scal->ray_next, 1);
+        __syncthreads();
         const int npt_total = nlive * npts;
-        for (int q = lane; q < npt_total; q += 32) {
-            const int r = q / npts, k = q - r * npts;
-            const float4 ry = rays[warp][r];
-            const float cr = rayc[warp][r];
-            const float gx = fmaf((float)k, ry.z, ry.x), gz = fmaf((float)k, ry.w, ry.y);
-            const float fx = floorf(gx), fz = floorf(gz);
-            const int i0 = min(max((int)fx, -1), g.nx - 1), j0 = min(max((int)fz, -1), g.nz - 1);
-            float wx[4], wz[4];
-            keys_weights(gx - fx, wx);
-            keys_weights(gz - fz, wz);
-            int *row = acci + (j0 + 1) * P + (i0 + 1);
+        int nq = 0;                                  // queued points of this warp (warp-uniform)
+        // flat index q = r * npts + k of this lane, advanced by T per pass without division
+        int r = (warp * 32 + lane) / npts, k = (warp * 32 + lane) - r * npts;
+        const int dr = T / npts, dk = T - dr * npts;
+        for (int q0 = warp * 32; q0 < npt_total; q0 += T) {
+            bool apart[kRayGroup];
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const float cb = cr * wz[b];
+            for (int m = 0; m < kRayGroup; ++m) apart[m] = false;
+            if (q0 + lane < npt_total) {
+                const float kf = (float)k;
+                const float4 cc = rayc[r];
+                const int2 gb = rayb[r];
+                float W[16];
+                int i0, j0;
+                {
+                    float wx[4], wz[4];
+                    ray_stencil(g, kf, rays[kLeadRay * T + r], i0, j0, wx, wz);
+                    const float cl = pick_c(cc, kLeadRay);
 #pragma unroll
-                for (int a = 0; a < 4; ++a) atomicAdd(row + b * P + a, round_to_int(cb * wx[a]));
-            }
-        }
-        __syncwarp();
-        if ((round + 1) % kRoundsPerFlush == 0 || round + 1 == nrounds) {
-            __syncthreads();
-            const float inv = 1.0f / S;
-            for (int k = threadIdx.x; k < npad; k += blockDim.x) {
-                const int v = acci[k];
-                if (v != 0) {
-                    mypad[k] += (float)v * inv;
-                    acci[k] = 0;
+                    for (int b = 0; b < 4; ++b) {
+                        const float cb = cl * wz[b];
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) W[b * 4 + a] = fmaf(cb, wx[a], kRound);
+                    }
                 }
+#pragma unroll
+                for (int m = 0; m < kRayGroup; ++m) {
+                    if (m == kLeadRay) continue;
+                    float wx[4], wz[4];
+                    int i1, j1;
+                    ray_stencil(g, kf, rays[m * T + r], i1, j1, wx, wz);
+                    const float cm = pick_c(cc, m);
+                    const bool away = i1 != i0 || j1 != j0;
+                    const float cmerge = away ? 0.0f : cm;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const float cb = cmerge * wz[b];
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) W[b * 4 + a] = fmaf(cb, wx[a], W[b * 4 + a]);
+                    }
+                    apart[m] = away && cm != 0.0f;
+                }
+                add_stencil(acci + gb.x + j0 * gb.y + i0, gb.y, W);
+            }
+            // queue the points that left the lead's cell; run full batches of 32
+#pragma unroll
+            for (int m = 0; m < kRayGroup; ++m) {
+                if (m == kLeadRay) continue;
+                const unsigned am = __ballot_sync(0xffffffffu, apart[m]);
+                if (apart[m]) fq[warp][nq + __popc(am & ((1u << lane) - 1u))] = (r << 18) | (k << 2) | m;
+                nq += __popc(am);
+            }
+            __syncwarp();
+            while (nq >= 32) {
+                nq -= 32;
+                const int ent = fq[warp][nq + lane];
+                __syncwarp();
+                run_queued(g, ent, acci, rays, T, rayc, rayb);
+            }
+            r += dr;
+            k += dk;
+            if (k >= npts) { k -= npts; ++r; }
+        }
+        if (lane < nq) run_queued(g, fq[warp][lane], acci, rays, T, rayc, rayb);   // last partial batch
+        blk = s_blk;
+        __syncthreads();                             // table and queue free for the next block
+        if (++since_flush == kBlocksPerFlush || blk >= nblk) {
+            since_flush = 0;
+            for (int q = threadIdx.x; q < rg.width * rg.rows; q += T) {
+                const int j = q / rg.width, i = q - j * rg.width;
+                int v = acci[j * rg.pa + i];
+                acci[j * rg.pa + i] = 0;
+                if (DUAL) {
+                    v += acci[rg.base_b + j * rg.pb + i];
+                    acci[rg.base_b + j * rg.pb + i] = 0;
+                }
+                if (v != 0) mypad[j * P + i] += v;
             }
             __syncthreads();
         }
     }
     __syncthreads();
     // fold the padding onto the clamped edge nodes and write this CTA's partial grid
-    float *out = gpart + (long)blockIdx.x * g.ng;
-    for (int k = threadIdx.x; k < g.ng; k += blockDim.x) {
-        const int j = k / g.nx, i = k - j * g.nx;
+    long long *out = gpart + (long)blockIdx.x * g.ng;
+    for (int q = threadIdx.x; q < g.ng; q += T) {
+        const int j = q / g.nx, i = q - j * g.nx;
         const int ilo = i == 0 ? 0 : i + 2, ihi = i == g.nx - 1 ? g.nx + 3 : i + 2;
         const int jlo = j == 0 ? 0 : j + 2, jhi = j == g.nz - 1 ? g.nz + 3 : j + 2;
-        float v = 0.0f;
+        long long v = 0;
         for (int jj = jlo; jj <= jhi; ++jj)
             for (int ii = ilo; ii <= ihi; ++ii) v += mypad[jj * P + ii];
-        out[k] = v;
+        out[q] = v;
     }
 }
 
@@ -149,15 +302,19 @@ __device__ __forceinline__ float dz_sign(float x, float k)      // D_k'(x)
     return fabsf(x) <= k ? 0.0f : (x > 0.0f ? 1.0f : -1.0f);
 }
 
-// grad[k] = sum_c gpart[c][k] + d(w1 R_TV + w2 R_SV)/ds_k  (gather form on c = 1/s)
+// grad[k] = sum_c gpart[c][k] / S + d(w1 R_TV + w2 R_SV)/ds_k  (gather form on c = 1/s);
+// also returns the ray adjoint's block counter to zero for its next launch
 __global__ void __launch_bounds__(256) reduce_grad_kernel(AfGeom g, const float *__restrict__ s,
-                                                          const float *__restrict__ gpart, int nparts,
-                                                          float *__restrict__ grad)
+                                                          const long long *__restrict__ gpart, int nparts,
+                                                          AfScal *scal, float *__restrict__ grad)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) scal->ray_next = 0;
     if (k >= g.ng) return;
-    float acc = 0.0f;
-    for (int c = 0; c < nparts; ++c) acc += gpart[(long)c * g.ng + k];
+    long long tot = 0;
+    for (int c = 0; c < nparts; ++c) tot += gpart[(long)c * g.ng + k];
+    const float gmax = __int_as_float(scal->gmax_bits);
+    const float acc = gmax > 0.0f ? (float)((double)tot * ((double)gmax / (double)g.fix_scale)) : 0.0f;
     const int j = k / g.nx, i = k - j * g.nx, nx = g.nx, nz = g.nz;
     auto C = [&](int ii, int jj) { return 1.0f / s[jj * nx + ii]; };
     const float hx = g.hx_mm, hz = g.hz_mm, hx2 = hx * hx, hz2 = hz * hz;
@@ -204,27 +361,72 @@ __global__ void __launch_bounds__(256) adam_kernel(AfGeom g, const float *__rest
 
 }  // namespace
 
-int rayadj_blocks_per_sm(size_t smem)
+// copy A pitch = 1 (mod 32), copy B pitch = 31 (mod 32), both >= nx + 4
+static RayGrid ray_grid_layout(int nx, int nz, bool dual, int pitch)
 {
+    RayGrid rg;
+    rg.width = nx + 4;
+    rg.rows = nz + 4;
+    if (dual) {
+        rg.pa = ((rg.width - 1 + 31) / 32) * 32 + 1;
+        rg.pb = ((rg.width + 1 + 31) / 32) * 32 - 1;
+        rg.base_b = rg.pa * rg.rows;
+    } else {
+        rg.pa = rg.pb = pitch;
+        rg.base_b = 0;
+    }
+    return rg;
+}
+
+static size_t ray_grid_bytes(const RayGrid &rg, bool dual)
+{
+    return (size_t)(dual ? rg.base_b + rg.pb * rg.rows : rg.pa * rg.rows) * sizeof(int);
+}
+
+// ray-adjoint launch shape of a plan: the two-copy layout when it fits in
+// shared memory (16 warps, one CTA per SM), else one odd-pitch copy (8 warps)
+RayAdjShape rayadj_shape(int nx, int nz, int pitch, int sm_count)
+{
+    RayAdjShape sh;
+    const RayGrid dual = ray_grid_layout(nx, nz, true, pitch);
+    sh.dual = ray_grid_bytes(dual, true) <= kRayDualMaxBytes;
+    const RayGrid rg = ray_grid_layout(nx, nz, sh.dual, pitch);
+    sh.smem = ray_grid_bytes(rg, sh.dual);
+    sh.threads = sh.dual ? 512 : 256;
     int n = 0;
-    // the attribute is per function, shared by every plan: set it to the largest
-    // grid any plan may use, the occupancy query uses this plan's size
-    cudaFuncSetAttribute(ray_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxGridSmemBytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ray_adjoint_kernel, 256, smem);
-    return n > 0 ? n : 1;
+    if (sh.dual) {
+        cudaFuncSetAttribute(ray_adjoint_kernel<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kRayDualMaxBytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ray_adjoint_kernel<16, true>, 512, sh.smem);
+    } else {
+        // the attribute is per function, shared by every plan: set it to the largest
+        // grid any plan may use, the occupancy query uses this plan's size
+        cudaFuncSetAttribute(ray_adjoint_kernel<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kMaxGridSmemBytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ray_adjoint_kernel<8, false>, 256, sh.smem);
+    }
+    sh.blocks = sm_count * (n > 0 ? n : 1);
+    return sh;
 }
 
 cudaError_t launch_ray_adjoint(af_plan_t pl, const float *s, float *grad)
 {
     int nparts = 0;
     if ((long)pl->g.ne * pl->g.npix > 0) {
-        ray_adjoint_kernel<<<pl->rayadj_blocks, 256, pl->smem_grid, pl->stream>>>(
-            pl->g, pl->elem, pl->pix, pl->phi, pl->gdel, pl->scal, pl->gpad, pl->gpart);
+        const RayAdjShape &sh = pl->rayadj;
+        const RayGrid rg = ray_grid_layout(pl->g.nx, pl->g.nz, sh.dual, pl->g.pitch);
+        if (sh.dual)
+            ray_adjoint_kernel<16, true><<<sh.blocks, 512, sh.smem, pl->stream>>>(
+                pl->g, rg, pl->elem, pl->pix, pl->phi, pl->gdel, pl->scal, pl->gpad, pl->gpart);
+        else
+            ray_adjoint_kernel<8, false><<<sh.blocks, 256, sh.smem, pl->stream>>>(
+                pl->g, rg, pl->elem, pl->pix, pl->phi, pl->gdel, pl->scal, pl->gpad, pl->gpart);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        nparts = pl->rayadj_blocks;
+        nparts = sh.blocks;
     }
-    reduce_grad_kernel<<<(pl->g.ng + 255) / 256, 256, 0, pl->stream>>>(pl->g, s, pl->gpart, nparts, grad);
+    reduce_grad_kernel<<<(pl->g.ng + 255) / 256, 256, 0, pl->stream>>>(pl->g, s, pl->gpart, nparts, pl->scal,
+                                                                      grad);
     return cudaGetLastError();
 }
 
