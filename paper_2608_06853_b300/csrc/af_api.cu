@@ -404,7 +404,7 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
     AF_ALLOC(pl->patch_cnt, g.n_patch * sizeof(int));
     AF_ALLOC(pl->scal, sizeof(AfScal));
     pl->smem_grid = padded_grid_bytes(c);
-    pl->delay_blocks = pl->sm_count * delays_blocks_per_sm(pl->smem_grid);
+    pl->delay = delays_shape(pl->smem_grid, pl->sm_count);
     pl->rayadj = rayadj_shape(c->nx, c->nz, g.pitch, pl->sm_count);
     AF_ALLOC(pl->gpart, (size_t)pl->rayadj.blocks * g.ng * sizeof(long long));
     AF_ALLOC(pl->gpad, (size_t)pl->rayadj.blocks * (pl->smem_grid / sizeof(float)) * sizeof(long long));

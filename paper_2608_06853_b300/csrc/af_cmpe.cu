@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(256) cmpe_forward_kernel(AfGeom g, const float
         const float2 *B1 = B + (long)(i * g.nsub + j) * g.npix + base;
         const float2 *B2 = B + (long)((i + 1) * g.nsub + (j - 1)) * g.npix + base;
         float zr = 0.f, zi = 0.f, e1 = 0.f, e2 = 0.f;
+#pragma unroll 4
         for (int q = lane; q < g.patch_npix; q += 32) {
             const float2 a = B1[q], c = B2[q];
             zr = fmaf(a.x, c.x, fmaf(a.y, c.y, zr));
@@ -61,14 +62,15 @@ __global__ void __launch_bounds__(256) cmpe_forward_kernel(AfGeom g, const float
         }
         zr = warp_sum(zr); zi = warp_sum(zi); e1 = warp_sum(e1); e2 = warp_sum(e2);
         if (lane == 0) {
-            const double den = sqrt((double)e1 * (double)e2);
-            const double rho = den > 0.0 ? hypot((double)zr, (double)zi) / den : 0.0;
-            const int m = rho >= (double)g.rho_thresh;
+            // float epilogue (the sums are float); sqrt of each energy avoids overflow
+            const float den = sqrtf(e1) * sqrtf(e2);
+            const float rho = den > 0.0f ? hypotf(zr, zi) / den : 0.0f;
+            const int m = rho >= g.rho_thresh;
             const long o = (long)P * g.npair + k;
             z[o] = make_float2(zr, zi);
             mask[o] = (uint8_t)m;
             if (m) {
-                lsum += fabs(atan2((double)zi, (double)zr));
+                lsum += (double)fabsf(atan2f(zi, zr));
                 ++cnt;
             }
         }

@@ -63,11 +63,42 @@ __global__ void __launch_bounds__(1024) grid_stats_kernel(AfGeom g, const float 
     }
 }
 
+// Padded grid in shared memory: scalar v[jj][ii], or (PAIRS) the node pairs
+// (v[jj][ii], v[jj][ii + 2]) as float2, so that the 4 taps of a row are two
+// aligned 64-bit loads (ii0, ii0 + 2) and (ii0 + 1, ii0 + 3).
+template <bool PAIRS> struct GridTaps;
+template <> struct GridTaps<false> {
+    static __device__ __forceinline__ void store(float *sm, int k, int P, float v, float) { sm[k] = v; }
+    static __device__ __forceinline__ float row(const float *sm, int o, const float (&wx)[4])
+    {
+        float h = wx[0] * sm[o];
+        h = fmaf(wx[1], sm[o + 1], h);
+        h = fmaf(wx[2], sm[o + 2], h);
+        return fmaf(wx[3], sm[o + 3], h);
+    }
+};
+template <> struct GridTaps<true> {
+    static __device__ __forceinline__ void store(float *sm, int k, int, float v, float v2)
+    {
+        reinterpret_cast<float2 *>(sm)[k] = make_float2(v, v2);
+    }
+    static __device__ __forceinline__ float row(const float *sm, int o, const float (&wx)[4])
+    {
+        const float2 *r = reinterpret_cast<const float2 *>(sm) + o;
+        const float2 a = r[0], b = r[1];      // (v0, v2), (v1, v3)
+        float h = wx[0] * a.x;
+        h = fmaf(wx[1], b.x, h);
+        h = fmaf(wx[2], a.y, h);
+        return fmaf(wx[3], b.y, h);
+    }
+};
+
 // One thread per (element e, pixel p), grid-stride over e * npix + p, with the
 // slowness deviation s - sbar staged once per CTA in shared memory, padded by
 // two edge-replicated nodes on every side so that each of the 16 taps of a
 // point inside the grid box reads the clamp-to-edge value without a branch.
-__global__ void __launch_bounds__(256) delays_kernel(AfGeom g, const float *__restrict__ s,
+template <bool PAIRS>
+__global__ void __launch_bounds__(PAIRS ? 768 : 256) delays_kernel(AfGeom g, const float *__restrict__ s,
                                                      const float4 *__restrict__ elem,
                                                      const float2 *__restrict__ elem_pol,
                                                      const float2 *__restrict__ pix,
@@ -82,7 +113,9 @@ __global__ void __launch_bounds__(256) delays_kernel(AfGeom g, const float *__re
     for (int k = threadIdx.x; k < P * rows; k += blockDim.x) {
         int jj = k / P, ii = k - jj * P;
         int i = min(max(ii - 2, 0), g.nx - 1), j = min(max(jj - 2, 0), g.nz - 1);
-        sm[k] = s[j * g.nx + i] - sbar;           // exact (Sterbenz) for s within 2x of sbar
+        const int i2 = min(max(ii, 0), g.nx - 1);          // node ii + 2 of the padded row
+        // exact (Sterbenz) for s within 2x of sbar
+        GridTaps<PAIRS>::store(sm, k, P, s[j * g.nx + i] - sbar, PAIRS ? s[j * g.nx + i2] - sbar : 0.0f);
     }
     __syncthreads();
 
@@ -163,17 +196,10 @@ __global__ void __launch_bounds__(256) delays_kernel(AfGeom g, const float *__re
             float wx[4], wz[4];
             keys_weights(gx - fx, wx);
             keys_weights(gz - fz, wz);
-            const float *row = sm + (j0 + 1) * P + (i0 + 1);   // padded node (i0-1, j0-1)
+            const int row = (j0 + 1) * P + (i0 + 1);           // padded node (i0-1, j0-1)
             float v = 0.0f;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const float *r = row + b * P;
-                float h = wx[0] * r[0];
-                h = fmaf(wx[1], r[1], h);
-                h = fmaf(wx[2], r[2], h);
-                h = fmaf(wx[3], r[3], h);
-                v = fmaf(wz[b], h, v);
-            }
+            for (int b = 0; b < 4; ++b) v = fmaf(wz[b], GridTaps<PAIRS>::row(sm, row + b * P, wx), v);
             // Kahan summation of the N+1 endpoint values
             const float y = v - comp;
             const float t = sum + y;
@@ -229,14 +255,28 @@ __global__ void export_delays_kernel(AfGeom g, const float4 *__restrict__ D, dou
 
 }  // namespace
 
-int delays_blocks_per_sm(size_t smem)
+// launch shape of the delay kernel: the paired grid (one 768-thread CTA per SM)
+// when it fits in shared memory, else the scalar grid (256-thread CTAs)
+DelayShape delays_shape(size_t smem_scalar, int sm_count)
 {
+    DelayShape sh;
+    sh.pairs = 2 * smem_scalar <= kMaxGridSmemBytes;
+    sh.smem = sh.pairs ? 2 * smem_scalar : smem_scalar;
+    sh.threads = sh.pairs ? 768 : 256;
     int n = 0;
     // the attribute is per function, shared by every plan: set it to the largest
     // grid any plan may use, the occupancy query uses this plan's size
-    cudaFuncSetAttribute(delays_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxGridSmemBytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, delays_kernel, 256, smem);
-    return n > 0 ? n : 1;
+    if (sh.pairs) {
+        cudaFuncSetAttribute(delays_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kMaxGridSmemBytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, delays_kernel<true>, 768, sh.smem);
+    } else {
+        cudaFuncSetAttribute(delays_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kMaxGridSmemBytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, delays_kernel<false>, 256, sh.smem);
+    }
+    sh.blocks = sm_count * (n > 0 ? n : 1);
+    return sh;
 }
 
 cudaError_t launch_grid_stats(af_plan_t pl, const float *s)
@@ -248,9 +288,15 @@ cudaError_t launch_grid_stats(af_plan_t pl, const float *s)
 cudaError_t launch_delays(af_plan_t pl, const float *s)
 {
     if ((long)pl->g.ne * pl->g.npix == 0) return cudaSuccess;
-    delays_kernel<<<pl->delay_blocks, 256, pl->smem_grid, pl->stream>>>(
-        pl->g, s, pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->have_phi ? 1 : 0,
-        pl->use_surrogate ? pl->sur_fb : nullptr, pl->D, pl->scal);
+    const DelayShape &sh = pl->delay;
+    if (sh.pairs)
+        delays_kernel<true><<<sh.blocks, sh.threads, sh.smem, pl->stream>>>(
+            pl->g, s, pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->have_phi ? 1 : 0,
+            pl->use_surrogate ? pl->sur_fb : nullptr, pl->D, pl->scal);
+    else
+        delays_kernel<false><<<sh.blocks, sh.threads, sh.smem, pl->stream>>>(
+            pl->g, s, pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->have_phi ? 1 : 0,
+            pl->use_surrogate ? pl->sur_fb : nullptr, pl->D, pl->scal);
     cudaError_t err = cudaGetLastError();
     if (err == cudaSuccess) pl->have_phi = true;
     return err;

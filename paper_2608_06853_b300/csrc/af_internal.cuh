@@ -44,6 +44,11 @@ constexpr int kRayGroup = 3;
 constexpr int kRayItemsPerFlush = 1024;
 constexpr double kRayFlushRays = (double)kRayItemsPerFlush * kRayGroup;
 constexpr size_t kRayDualMaxBytes = 180 * 1024;
+struct DelayShape {
+    bool pairs;          // grid as float2 node pairs (i, i + 2) or scalar
+    int threads, blocks;
+    size_t smem;
+};
 struct RayAdjShape {
     bool dual;           // two grid copies (row pitch 1 and 31 mod 32) or one
     int threads, blocks;
@@ -87,7 +92,7 @@ struct af_plan_s {
     cudaStream_t stream;
     int device, sm_count;
     size_t smem_grid;    // bytes of the padded slowness grid in shared memory
-    int delay_blocks;
+    DelayShape delay;    // delay-kernel launch shape (grid layout, threads, CTAs)
     RayAdjShape rayadj;  // ray-adjoint launch shape (grid layout, threads, CTAs)
     // geometry
     float4 *elem;        // (x, z, cos theta_a, sin theta_a)  theta_a from Eq. 3
@@ -205,7 +210,7 @@ cudaError_t launch_ray_adjoint(af_plan_t pl, const float *s, float *grad);
 cudaError_t launch_adam(af_plan_t pl, const float *grad, float *s, float *m, float *v, int step);
 cudaError_t launch_export_delays(af_plan_t pl, double *T, uint8_t *apod);
 cudaError_t launch_images(af_plan_t pl, float *bmode, float *cimg);
-int delays_blocks_per_sm(size_t smem);
+DelayShape delays_shape(size_t smem_scalar, int sm_count);
 cudaError_t mlp_setup_attributes();
 cudaError_t mlp_refresh_bf16(af_plan_t pl);
 cudaError_t mlp_init_params(af_plan_t pl, uint64_t seed);

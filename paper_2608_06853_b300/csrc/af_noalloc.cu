@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(256) noalloc_patch_kernel(const float2 *__rest
         const float2 *B1 = B + (long)(i * nsub + j) * npix + base;
         const float2 *B2 = B + (long)((i + 1) * nsub + (j - 1)) * npix + base;
         float zr = 0.f, zi = 0.f, e1 = 0.f, e2 = 0.f;
+#pragma unroll 4
         for (int q = lane; q < patch_npix; q += 32) {
             const float2 a = B1[q], c = B2[q];
             zr = fmaf(a.x, c.x, fmaf(a.y, c.y, zr));
@@ -74,10 +75,11 @@ __global__ void __launch_bounds__(256) noalloc_patch_kernel(const float2 *__rest
         }
         zr = warp_sum_na(zr); zi = warp_sum_na(zi); e1 = warp_sum_na(e1); e2 = warp_sum_na(e2);
         if (lane == 0) {
-            const double den = sqrt((double)e1 * (double)e2);
-            const double rho = den > 0.0 ? hypot((double)zr, (double)zi) / den : 0.0;
-            if (rho >= (double)rho_thresh) {
-                lsum += fabs(atan2((double)zi, (double)zr));
+            // float epilogue (the sums are float); sqrt of each energy avoids overflow
+            const float den = sqrtf(e1) * sqrtf(e2);
+            const float rho = den > 0.0f ? hypotf(zr, zi) / den : 0.0f;
+            if (rho >= rho_thresh) {
+                lsum += (double)fabsf(atan2f(zi, zr));
                 ++cnt;
             }
         }

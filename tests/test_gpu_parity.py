@@ -179,9 +179,12 @@ def test_adam_step_parity(tiny_case):
 
 
 def test_ragged_and_variant_shapes():
-    """Pixel count not a multiple of 32, no lens, sub_width 2 and 8, printed Eq. 4."""
+    """Pixel count not a multiple of 32, no lens, sub_width 2 and 8, printed Eq. 4; one
+    CTA's pixels spread over the whole depth range; an odd trace length."""
     cases = [
         dict(n_ang=3, n_rad=3, patch_w=3),                      # 81 pixels
+        dict(n_ang=1, n_rad=8, patch_w=5),                      # 200 pixels over 8-50 mm depth
+        dict(n_ang=3, n_rad=3, patch_w=3, ns=1023),             # 1023 samples per trace
         dict(n_ang=5, n_rad=2, patch_w=5, lens_mode=1),         # straight rays, 250 pixels
         dict(n_ang=2, n_rad=3, patch_w=3, sub_width=2),         # 16 subapertures
         dict(n_ang=2, n_rad=2, patch_w=4, sub_width=8),         # 4 subapertures
