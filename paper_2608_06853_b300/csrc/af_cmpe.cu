@@ -118,11 +118,14 @@ __global__ void __launch_bounds__(256) cmpe_finalize_kernel(AfGeom g, const doub
     }
 }
 
-// sign of arg z as atan2 defines it (arg in (-pi, pi])
+// sign of arg z as atan2 defines it: the sign of Im z, and on the real axis
+// +pi (or -pi for Im z = -0) left of the origin, 0 right of it
 __device__ __forceinline__ float arg_sign(float2 z)
 {
-    const float a = atan2f(z.y, z.x);
-    return a > 0.0f ? 1.0f : (a < 0.0f ? -1.0f : 0.0f);
+    if (z.y > 0.0f) return 1.0f;
+    if (z.y < 0.0f) return -1.0f;
+    if (z.x < 0.0f) return signbit(z.y) ? -1.0f : 1.0f;
+    return 0.0f;
 }
 
 // G[b][p] = dL_CMPE/dB_b(p): an image is the first member of at most one pair

@@ -17,21 +17,26 @@ __global__ void __launch_bounds__(1024) grid_stats_kernel(AfGeom g, const float 
                                                           AfScal *scal)
 {
     __shared__ double red[3][32];
-    double acc_c = 0.0, acc_a = 0.0, acc_b = 0.0;
+    // per-thread partial sums in float (float64 throughput is low on this GPU); the
+    // sum of 1/s, which sets c_med and with it every delay, is compensated (Kahan)
+    float pc = 0.0f, pc_comp = 0.0f, pa = 0.0f, pb = 0.0f;
     int bad = 0;
     for (int k = threadIdx.x; k < g.ng; k += blockDim.x) {
         int j = k / g.nx, i = k - j * g.nx;
         float sv = s[k];
         if (!(sv > 0.0f) || !isfinite(sv)) bad = 1;
         float c0 = 1.0f / sv;
-        acc_c += (double)c0;
-        if (i + 1 < g.nx) acc_a += deadzone((1.0f / s[k + 1] - c0) / g.hx_mm, g.kx1);
-        if (j + 1 < g.nz) acc_a += deadzone((1.0f / s[k + g.nx] - c0) / g.hz_mm, g.kz1);
+        const float y = c0 - pc_comp, t = pc + y;
+        pc_comp = (t - pc) - y;
+        pc = t;
+        if (i + 1 < g.nx) pa += deadzone((1.0f / s[k + 1] - c0) / g.hx_mm, g.kx1);
+        if (j + 1 < g.nz) pa += deadzone((1.0f / s[k + g.nx] - c0) / g.hz_mm, g.kz1);
         if (i >= 1 && i + 1 < g.nx)
-            acc_b += deadzone((1.0f / s[k + 1] - 2.0f * c0 + 1.0f / s[k - 1]) / (g.hx_mm * g.hx_mm), g.kx2);
+            pb += deadzone((1.0f / s[k + 1] - 2.0f * c0 + 1.0f / s[k - 1]) / (g.hx_mm * g.hx_mm), g.kx2);
         if (j >= 1 && j + 1 < g.nz)
-            acc_b += deadzone((1.0f / s[k + g.nx] - 2.0f * c0 + 1.0f / s[k - g.nx]) / (g.hz_mm * g.hz_mm), g.kz2);
+            pb += deadzone((1.0f / s[k + g.nx] - 2.0f * c0 + 1.0f / s[k - g.nx]) / (g.hz_mm * g.hz_mm), g.kz2);
     }
+    double acc_c = (double)pc - (double)pc_comp, acc_a = pa, acc_b = pb;
     for (int o = 16; o > 0; o >>= 1) {
         acc_c += __shfl_xor_sync(0xffffffffu, acc_c, o);
         acc_a += __shfl_xor_sync(0xffffffffu, acc_a, o);
