@@ -60,8 +60,10 @@ __device__ __forceinline__ void gather_w(const typename S::T *__restrict__ base,
 // consecutive pixels, about three laterally adjacent patches), all with the
 // same receive block j = blockIdx.y.  The warps walk the transmits in the same
 // order, so the trace windows one warp pulls into L1 serve the other seven.
+// The gathers are latency bound: the transmit loop is unrolled by two so that
+// a lane has the 4W loads of two transmits in flight (2 CTAs of 256 per SM).
 template <int W, int DT>
-__global__ void __launch_bounds__(256, 3) das_forward_kernel(AfGeom g, const void *__restrict__ iq,
+__global__ void __launch_bounds__(256, 2) das_forward_kernel(AfGeom g, const void *__restrict__ iq,
                                                              const float *__restrict__ scale,
                                                              const float4 *__restrict__ D,
                                                              float2 *__restrict__ B)
@@ -85,6 +87,7 @@ __global__ void __launch_bounds__(256, 3) das_forward_kernel(AfGeom g, const voi
     float4 dnext = D[p];
     for (int i = 0; i < g.nsub; ++i) {
         float ar = 0.0f, ai = 0.0f;
+#pragma unroll 2
         for (int tt = 0; tt < W; ++tt) {
             const int t = i * W + tt;
             const float4 dt = dnext;
@@ -120,7 +123,7 @@ __global__ void __launch_bounds__(256, 3) das_forward_kernel(AfGeom g, const voi
 // zeroed dL/dT table with coalesced atomic adds (one per transmit and one per
 // receiver of the block).
 template <int W, int DT>
-__global__ void __launch_bounds__(256, 3) das_adjoint_kernel(AfGeom g, const void *__restrict__ iq,
+__global__ void __launch_bounds__(256, 2) das_adjoint_kernel(AfGeom g, const void *__restrict__ iq,
                                                              const float *__restrict__ scale,
                                                              const float4 *__restrict__ D,
                                                              const float2 *__restrict__ G,
@@ -147,6 +150,7 @@ __global__ void __launch_bounds__(256, 3) das_adjoint_kernel(AfGeom g, const voi
     float4 dnext = D[p];
     for (int i = 0; i < g.nsub; ++i) {
         const float2 Gv = G[(long)(i * g.nsub + j) * g.npix + p];
+#pragma unroll 2
         for (int tt = 0; tt < W; ++tt) {
             const int t = i * W + tt;
             const float4 dt = dnext;
