@@ -165,38 +165,49 @@ def run_reference(args, rank, world):
 # capture (see profiles/).
 NCU_TRAFFIC = {"das_forward": None, "das_adjoint": None, "ray_adjoint": None, "delays": None}
 
-# algorithmic FP32 lane-operations per ray point, from the arithmetic of the method:
-# position (2) + cell and fraction (4) + two Keys weight sets (2 x 10) + 16 taps and 4
-# row combinations (20), plus a 4-op compensated sum in the forward ray sum
+# algorithmic FP32 lane-operations per unit, from the arithmetic of the method.
+# Ray point: position (2) + cell and fraction (4) + two Keys weight sets (2 x 10) + 16
+# taps and 4 row combinations (20), plus a 4-op compensated sum in the forward ray sum.
+# Gather (one live (transmit, receiver, pixel) triple): delay and fraction add with
+# carry (3) + 2 sample loads + complex lerp (4) + receive phasor and accumulate (4) = 13
+# forward; the adjoint adds the slope terms (2), the weight conj(G) P_t P_r (4), the
+# real part (2) and the two accumulations (2) = 23.
 OPS_PER_POINT = {"delays": 50, "ray_adjoint": 46}
+OPS_PER_GATHER = {"das_forward": 13, "das_adjoint": 23}
 
 
-def stage_roofline(stage, ms, launches, p, iq_bytes, pk):
-    """Roofline entry of one stage: algorithmic bytes (or lane operations) per launch
-    divided by its average launch time."""
+def stage_roofline(stage, ms, launches, p, iq_bytes, pk, gathers):
+    """Roofline entry of one stage: algorithmic lane operations per launch divided by
+    its average launch time, against the FP32 lane rate (the binding roofline of every
+    stage of this path: the channel data is read once per pass, 805 MB per iteration,
+    far below what HBM moves in the time the arithmetic takes).  The delay-and-sum
+    stages also carry their algorithmic HBM bytes against the measured copy peak."""
     ne, npix = p.ne, p.npix
     nb = p.nsub * p.nsub
     avg_s = ms / launches * 1e-3
     hbm = pk.get("hbm_gbs", 6400.0)
-    if stage in ("das_forward", "das_adjoint"):
+    # FP32 lane-operation bound: SMs x 128 lanes x max SM clock (derived, not measured)
+    lanes = 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6
+    if stage in OPS_PER_GATHER:
+        ops = gathers * OPS_PER_GATHER[stage]
+    else:
+        ops = ne * npix * (p.nseg + 1) * OPS_PER_POINT.get(stage, 0)
+    achieved = ops / avg_s / 1e12
+    out = {"bound": "alu", "achieved": achieved, "peak": lanes / 1e12, "unit": "Tlane-op/s",
+           "frac": achieved / (lanes / 1e12), "traffic": NCU_TRAFFIC.get(stage), "kernel": stage,
+           "algorithmic_ops": ops, "avg_launch_ms": ms / launches,
+           "peak_source": "derived: 148 SMs x 128 FP32 lanes x max SM clock"}
+    if stage in OPS_PER_GATHER:
         # channel data once + one-way tables + images (dL/dB and dL/dT for the adjoint)
         bytes_ = iq_bytes + ne * npix * 16 + nb * npix * 8
         if stage == "das_adjoint":
             bytes_ += ne * npix * 4
-        achieved = bytes_ / avg_s / 1e9
-        return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": NCU_TRAFFIC.get(stage), "kernel": stage,
-                "algorithmic_bytes": bytes_, "avg_launch_ms": ms / launches,
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in pk else "fallback"}
-    # FP32 lane-operation bound: SMs x 128 lanes x max SM clock (derived, not measured)
-    lanes = 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6
-    pts = ne * npix * (p.nseg + 1)
-    ops = pts * OPS_PER_POINT.get(stage, 0)
-    achieved = ops / avg_s / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": lanes / 1e12, "unit": "Tlane-op/s",
-            "frac": achieved / (lanes / 1e12), "traffic": NCU_TRAFFIC.get(stage), "kernel": stage,
-            "algorithmic_ops": ops, "avg_launch_ms": ms / launches,
-            "peak_source": "derived: 148 SMs x 128 FP32 lanes x max SM clock"}
+        gbs = bytes_ / avg_s / 1e9
+        out["hbm"] = {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                      "algorithmic_bytes": bytes_, "live_gathers": gathers,
+                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in pk
+                      else "fallback"}
+    return out
 
 
 # ---------------------------------------------------------------- ranks
@@ -400,6 +411,17 @@ def run_ours(args, rank, world, local_rank):
     plan.set_timing(False)
     counters = plan.counters()
     counters["numeric_ok"] = plan.af_sync_status() == af.AF_OK
+    # live gathers (last timed iteration) of the forward: sum over pixels of (elements
+    # that see the pixel)^2; of the adjoint: only those of images whose gradient is
+    # non-zero (it skips the rest, whose terms are exactly zero)
+    _, apod = plan.delays()
+    G = plan.image_grad()
+    stream.synchronize()
+    n_blk = apod.view(p.nsub, p.sub_width, p.npix).sum(dim=1, dtype=torch.int64).double()
+    nz = (G.view(p.nsub, p.nsub, p.npix) != 0).double()
+    gathers = {"das_forward": int((n_blk.sum(dim=0) ** 2).sum().item()),
+               "das_adjoint": int(torch.einsum("ijp,ip,jp->", nz, n_blk, n_blk).item())}
+    del apod, G, nz
     clk = clocks.stop() if clocks else None
     value, t_max = combine_ranks(ms * 1e-3, args.steps, world, dev)
     ms_max = t_max * 1e3
@@ -447,7 +469,10 @@ def run_ours(args, rank, world, local_rank):
     pk = peaks()
     ranked = sorted(((v_[0], k) for k, v_ in stages.items() if v_[1] > 0), reverse=True)
     dom = ranked[0][1]
-    roof = stage_roofline(dom, stages[dom][0], stages[dom][1], p, iq_bytes, pk)
+    roof = stage_roofline(dom, stages[dom][0], stages[dom][1], p, iq_bytes, pk, gathers.get(dom, 0))
+    stage_roof = {k: stage_roofline(k, v_[0], v_[1], p, iq_bytes, pk, gathers.get(k, 0))["frac"]
+                  for k, v_ in stages.items() if v_[1] > 0 and k in ("delays", "das_forward", "das_adjoint",
+                                                                   "ray_adjoint")}
     # achieved HBM GB/s of the whole iteration by algorithmic bytes (channel data read twice)
     it_bytes = 2 * iq_bytes
     line = {
@@ -464,6 +489,8 @@ def run_ours(args, rank, world, local_rank):
         "stage_ms": {k: v_[0] / max(v_[1], 1) for k, v_ in stages.items()},
         "hbm_gbs_algorithmic": it_bytes / (ms_max / args.steps * 1e-3) / 1e9,
         "roofline": roof,
+        "stage_alu_frac": stage_roof,
+        "live_gathers": gathers,
         "loss": final_loss,
         "counters": counters,
         "clocks": clk,

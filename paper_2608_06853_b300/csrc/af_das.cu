@@ -150,13 +150,21 @@ __global__ void __launch_bounds__(256, 2) das_adjoint_kernel(AfGeom g, const voi
     float4 dnext = D[p];
     for (int i = 0; i < g.nsub; ++i) {
         const float2 Gv = G[(long)(i * g.nsub + j) * g.npix + p];
+        // every term of transmit block i is weighted by conj(G_ij(p)): where the CMPE
+        // mask leaves G_ij(p) = 0 the block adds exactly nothing, so it is skipped
+        // (by the whole warp when no lane has a gradient, else lane by lane)
+        const bool gzero = Gv.x == 0.0f && Gv.y == 0.0f;
+        if (__all_sync(__activemask(), gzero)) {
+            if ((i + 1) * W < g.ne) dnext = D[(long)(i + 1) * W * g.npix + p];
+            continue;
+        }
 #pragma unroll 2
         for (int tt = 0; tt < W; ++tt) {
             const int t = i * W + tt;
             const float4 dt = dnext;
             if (t + 1 < g.ne) dnext = D[(long)(t + 1) * g.npix + p];
             const int nt = __float_as_int(dt.x);
-            if (nt == AF_APOD_OFF) continue;
+            if (nt == AF_APOD_OFF || gzero) continue;
             float sc = 1.0f;
             if (DT != AF_IQ_C64) sc = scale[t];
             // X = conj(G) P_t (scaled)

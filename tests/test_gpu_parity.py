@@ -180,11 +180,17 @@ def test_adam_step_parity(tiny_case):
 
 def test_ragged_and_variant_shapes():
     """Pixel count not a multiple of 32, no lens, sub_width 2 and 8, printed Eq. 4; one
-    CTA's pixels spread over the whole depth range; an odd trace length."""
+    CTA's pixels spread over the whole depth range; an odd trace length; the Eq. 6
+    conventional lens model and non-zero t_ttp / t0."""
     cases = [
         dict(n_ang=3, n_rad=3, patch_w=3),                      # 81 pixels
         dict(n_ang=1, n_rad=8, patch_w=5),                      # 200 pixels over 8-50 mm depth
         dict(n_ang=3, n_rad=3, patch_w=3, ns=1023),             # 1023 samples per trace
+        # Eq. 6 conventional model: straight rays from the elements plus one scalar
+        # offset (lens correction + envelope peak) on every round trip; and the
+        # bent-ray model with an envelope offset and a late first sample
+        dict(n_ang=3, n_rad=3, patch_w=3, lens_mode=1, t_ttp=1.1e-6),
+        dict(n_ang=3, n_rad=3, patch_w=3, t_ttp=3.5e-7, t0=2.0e-6),
         dict(n_ang=5, n_rad=2, patch_w=5, lens_mode=1),         # straight rays, 250 pixels
         dict(n_ang=2, n_rad=3, patch_w=3, sub_width=2),         # 16 subapertures
         dict(n_ang=2, n_rad=2, patch_w=4, sub_width=8),         # 4 subapertures
