@@ -161,9 +161,11 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------- roofline
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
-# capture of the full workload, per kernel; None once the kernel changed after the
-# capture (see profiles/).
-NCU_TRAFFIC = {"das_forward": None, "das_adjoint": None, "ray_adjoint": None, "delays": None}
+# capture of the full workload (second iteration), per kernel; None once the kernel
+# changed after the capture (see profiles/).  The adjoint stages' traffic follows
+# the CMPE mask of the captured iteration.
+NCU_TRAFFIC = {"das_forward": 743.3e6 + 65.6e6, "das_adjoint": 293.2e6 + 18.4e6,
+               "ray_adjoint": 26.2e6 + 1.9e6, "delays": 15.6e6 + 23.4e6}
 
 # algorithmic FP32 lane-operations per unit, from the arithmetic of the method.
 # Ray point: position (2) + cell and fraction (4) + two Keys weight sets (2 x 10) + 16
