@@ -307,7 +307,46 @@ def run_variants(args, p, psi, plan32, iq32, stream, dev, ms32):
                              "train_seconds": t_train, "train_loss": rep["train_loss"]}
     pl.surrogate_enable(False)
     out["batch"] = run_batch(args, dev)
+    out["sweep_and_images"] = run_sweep_images(p, iq32, plan32, stream, dev)
     return out
+
+
+def run_sweep_images(p, iq32, plan32, stream, dev):
+    """Global-speed sweep with the dynamic CMPE grid (41 speeds, 1340-1740 m/s, one
+    forward each) on the full workload's channel data, and the B-mode / integrated CMPE
+    images of one forward.  The sweep plan's grid box covers the patches as the sweep
+    moves them (same array, lens, medium and echoes; only the grid box differs)."""
+    import torch
+
+    import paper_2608_06853_b300 as af
+    import synth
+    from paper_2608_06853_b300.sweep import global_speed_sweep
+    p_sw = synth.config_full(cover_speeds=(1340.0, 1740.0))
+    pl = af.Plan(p_sw, stream=stream)
+    speeds = np.arange(1340.0, 1741.0, 10.0)
+    global_speed_sweep(pl, p_sw, iq32, speeds=speeds[:2], dynamic=True)      # warm
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    speeds, cmpe, active, best = global_speed_sweep(pl, p_sw, iq32, speeds=speeds, dynamic=True)
+    torch.cuda.synchronize(dev)
+    t_sweep = time.perf_counter() - t0
+    # images of one forward of the main plan
+    s0 = torch.from_numpy(p.initial_slowness()).to(dev)
+    with torch.cuda.stream(stream):
+        loss = torch.zeros(4, device=dev)
+        plan32.af_forward(iq32, s0, loss)
+    plan32.bmode()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(10):
+            plan32.bmode()
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return {"sweep_speeds": len(speeds), "sweep_ms": t_sweep * 1e3, "sweep_ms_per_speed": t_sweep * 1e3 / len(speeds),
+            "sweep_best_mps": best, "sweep_cmpe_min": float(cmpe.min()), "sweep_cmpe_max": float(cmpe.max()),
+            "images_ms": e0.elapsed_time(e1) / 10,
+            "note": "sweep: wall time incl. host pixel moves and per-speed readback; images: CUDA events"}
 
 
 def run_batch(args, dev, n_iter=100, n_scat=20_000):

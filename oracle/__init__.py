@@ -40,6 +40,7 @@ class Geom(ctypes.Structure):
         ("ne", ctypes.c_int), ("ex", _dp), ("ez", _dp),
         ("lens_mode", ctypes.c_int), ("arc_cx", ctypes.c_double), ("arc_cz", ctypes.c_double),
         ("lens_radius", ctypes.c_double), ("c_lens", ctypes.c_double), ("t_ttp", ctypes.c_double),
+        ("lens_z", ctypes.c_double),
         ("apod_mode", ctypes.c_int), ("fnum", ctypes.c_double),
         ("n_patch", ctypes.c_int), ("patch_npix", ctypes.c_int), ("px", _dp), ("pz", _dp),
         ("nx", ctypes.c_int), ("nz", ctypes.c_int), ("x0", ctypes.c_double), ("z0", ctypes.c_double),
@@ -115,6 +116,7 @@ class Oracle:
         g.arc_cx, g.arc_cz = p.arc_cx, p.arc_cz
         g.lens_radius = p.lens_radius
         g.c_lens, g.t_ttp = p.c_lens, p.t_ttp
+        g.lens_z = getattr(p, "lens_z", 0.0)
         g.apod_mode, g.fnum = int(p.apod_mode), p.fnum
         g.n_patch, g.patch_npix = int(p.n_patch), int(p.patch_npix)
         g.px, g.pz = _d(self._px), _d(self._pz)

@@ -95,6 +95,14 @@ static void chord(double r1, double r2, double delta, double *d, double *d1, dou
 void or_exit_from_angle(const or_geom *g, int e, double phi, double *t_lens,
                         double *qx, double *qz)
 {
+    if (g->lens_mode == 2) {
+        /* flat lens: the exit point is (phi, lens_z) */
+        *qx = phi;
+        *qz = g->lens_z;
+        *t_lens = sqrt((phi - g->ex[e]) * (phi - g->ex[e]) + (g->lens_z - g->ez[e]) * (g->lens_z - g->ez[e]))
+                  / g->c_lens;
+        return;
+    }
     double ux = g->ex[e] - g->arc_cx, uz = g->ez[e] - g->arc_cz;
     double re = sqrt(ux * ux + uz * uz), the = atan2(ux, uz);
     double d, d1, d2;
@@ -104,9 +112,45 @@ void or_exit_from_angle(const or_geom *g, int e, double phi, double *t_lens,
     *qz = g->arc_cz + g->lens_radius * cos(phi);
 }
 
+/* Flat lens (lens_mode 2, Eq. 7-8 with the lens surface the line z = lens_z):
+ *   T(u) = sqrt((u - x_e)^2 + h1^2) / c_lens + sqrt((x - u)^2 + h2^2) * sbar,
+ * h1 = lens_z - z_e > 0, h2 = z - lens_z > 0.  T'' > 0 and T' changes sign between
+ * x_e and x, so the exit point is the root of T' there: safeguarded Newton. */
+static int exit_point_flat(const or_geom *g, int e, double x, double z, double sbar, double *u_out)
+{
+    double xe = g->ex[e], h1 = g->lens_z - g->ez[e], h2 = z - g->lens_z;
+    if (!(h1 > 0.0) || !(h2 > 0.0)) return -1;
+    double lo = xe < x ? xe : x, hi = xe < x ? x : xe, u = xe;
+    int it = 0;
+    if (hi - lo > 0.0) {
+        for (it = 1; it <= 200; ++it) {
+            double d1 = sqrt((u - xe) * (u - xe) + h1 * h1), d2 = sqrt((x - u) * (x - u) + h2 * h2);
+            double dT = (u - xe) / (g->c_lens * d1) - (x - u) * sbar / d2;
+            double d2T = h1 * h1 / (g->c_lens * d1 * d1 * d1) + sbar * h2 * h2 / (d2 * d2 * d2);
+            if (dT == 0.0) break;                /* Fermat: stationary point reached */
+            if (dT < 0.0) lo = u; else hi = u;
+            double un = u - dT / d2T;
+            if (!(un >= lo && un <= hi)) un = 0.5 * (lo + hi);
+            double step = fabs(un - u);
+            u = un;
+            if (step <= 1e-15 || hi - lo <= 1e-15) break;
+        }
+    }
+    *u_out = u;
+    return it;
+}
+
 int or_exit_point(const or_geom *g, int e, double x, double z, double sbar,
                   double *phi, double *t_lens, double *qx, double *qz)
 {
+    if (g->lens_mode == 2) {
+        double u = g->ex[e];
+        int it = exit_point_flat(g, e, x, z, sbar, &u);
+        if (it < 0) return it;
+        *phi = u;
+        or_exit_from_angle(g, e, u, t_lens, qx, qz);
+        return it;
+    }
     double ux = g->ex[e] - g->arc_cx, uz = g->ez[e] - g->arc_cz;
     double re = sqrt(ux * ux + uz * uz), the = atan2(ux, uz);
     double vx = x - g->arc_cx, vz = z - g->arc_cz;
@@ -218,7 +262,7 @@ void or_delays(const or_geom *g, const double *s, const uint8_t *apod_in,
             int h = apod_in ? apod_in[k] : or_apod(g, theta, e, x, z);
             if (apod) apod[k] = (uint8_t)h;
             double tl = 0.0, qx = g->ex[e], qz = g->ez[e], f = 0.0;
-            if (g->lens_mode == 0) {
+            if (g->lens_mode == 0 || g->lens_mode == 2) {
                 if (phi_in) {
                     f = phi_in[k];
                     or_exit_from_angle(g, e, f, &tl, &qx, &qz);
@@ -420,7 +464,7 @@ void or_ray_adjoint(const or_geom *g, const double *s, const double *phi,
             if (gv == 0.0) continue;
             double x = g->px[p], z = g->pz[p];
             double qx = g->ex[e], qz = g->ez[e], tl;
-            if (g->lens_mode == 0) or_exit_from_angle(g, e, phi[k], &tl, &qx, &qz);
+            if (g->lens_mode == 0 || g->lens_mode == 2) or_exit_from_angle(g, e, phi[k], &tl, &qx, &qz);
             double len = sqrt((x - qx) * (x - qx) + (z - qz) * (z - qz));
             double c = gv * len / (n + 1);
             for (int kk = 0; kk <= n; ++kk) {

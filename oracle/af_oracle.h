@@ -24,13 +24,15 @@ typedef struct {
     /* transducer array, Sec. II-A: element positions r_a */
     int ne;
     const double *ex, *ez;
-    /* lens, Sec. II-B Eq. 7-8 and Sec. III-B: outer surface is an arc of
-     * radius lens_radius about (arc_cx, arc_cz), concentric with the
-     * element arc; lens_mode 0 = bent-ray (Fermat) model, 1 = no lens
-     * (rays start at the element, Eq. 1). */
+    /* lens, Sec. II-B Eq. 7-8 and Sec. III-B: lens_mode 0 = bent-ray (Fermat)
+     * model with a curved lens whose outer surface is an arc of radius
+     * lens_radius about (arc_cx, arc_cz), concentric with the element arc;
+     * 1 = no lens (rays start at the element, Eq. 1; with t_ttp this is the
+     * conventional model of Eq. 6); 2 = bent-ray model with a flat lens whose
+     * outer surface is the line z = lens_z (linear array). */
     int lens_mode;
     double arc_cx, arc_cz, lens_radius;
-    double c_lens, t_ttp;
+    double c_lens, t_ttp, lens_z;
     /* apodization, Eq. 2-4: apod_mode 0 = |x'| <= z'/(2F), 1 = |x'| <= (F/2) z' */
     int apod_mode;
     double fnum;
@@ -57,10 +59,12 @@ int or_apod(const or_geom *g, const double *theta, int e, double x, double z);
 /* Sec. III-A: mean sound speed of the grid, c_med = mean(1/s) */
 double or_mean_speed(const or_geom *g, const double *s);
 /* Eq. 8 + Sec. III-A: lens exit point by Fermat's principle at slowness sbar.
- * Returns the number of iterations (negative if the pixel lies inside the lens). */
+ * Returns the number of iterations (negative if the pixel lies inside the lens).
+ * phi is the exit angle about the arc centre (lens_mode 0) or the exit x on
+ * the line z = lens_z (lens_mode 2). */
 int or_exit_point(const or_geom *g, int e, double x, double z, double sbar,
                   double *phi, double *t_lens, double *qx, double *qz);
-/* lens time and exit point for a given (frozen) exit angle phi */
+/* lens time and exit point for a given (frozen) exit angle / exit x phi */
 void or_exit_from_angle(const or_geom *g, int e, double phi, double *t_lens,
                         double *qx, double *qz);
 /* Keys cubic-convolution weights (a = -1/2) for taps -1, 0, 1, 2 at fraction t */

@@ -37,16 +37,18 @@ def global_speed_sweep(plan, problem, iq, speeds=None, dynamic=True, iq_scale=No
     dev = torch.device("cuda", torch.cuda.current_device())
     speeds = np.arange(1340.0, 1741.0, 10.0) if speeds is None else np.asarray(speeds, np.float64)
     cmpe, active = [], []
-    loss = torch.zeros(4, device=dev)
     try:
-        for c0 in speeds:
-            if dynamic:
-                plan.af_set_pixels(*dynamic_pixels(problem, c0))
-            s = torch.full((problem.nz, problem.nx), 1.0 / c0, dtype=torch.float32, device=dev)
-            plan.af_forward(iq, s, loss, iq_scale)
-            _, _, m = plan.cmpe()
-            cmpe.append(float(loss[1]))
-            active.append(m)
+        # tensors made and read on the plan's stream, which its kernels run on
+        with torch.cuda.stream(plan.stream):
+            loss = torch.zeros(4, device=dev)
+            for c0 in speeds:
+                if dynamic:
+                    plan.af_set_pixels(*dynamic_pixels(problem, c0))
+                s = torch.full((problem.nz, problem.nx), 1.0 / c0, dtype=torch.float32, device=dev)
+                plan.af_forward(iq, s, loss, iq_scale)
+                _, _, m = plan.cmpe()
+                cmpe.append(float(loss[1]))
+                active.append(m)
     finally:
         if dynamic:
             plan.af_set_pixels(problem.pix_x, problem.pix_z)

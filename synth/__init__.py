@@ -50,7 +50,7 @@ def _load():
         lib = ctypes.CDLL(_LIB_PATH)
         dp = ctypes.POINTER(ctypes.c_double)
         lib.sy_oneway_times.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double,
-                                        ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                         ctypes.POINTER(_Medium), ctypes.c_int, dp, dp, dp]
         lib.sy_echoes.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_double,
                                   ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -117,7 +117,7 @@ class Problem:
     d_lens: float
     c_lens: float
     t_ttp: float
-    lens_mode: int            # 0 bent-ray, 1 no lens
+    lens_mode: int            # 0 bent-ray (curved lens), 1 no lens, 2 bent-ray (flat lens)
     # apodization (Eq. 4)
     fnum: float
     apod_mode: int            # 0 |x'| <= z'/(2F), 1 printed (F/2) z'
@@ -155,8 +155,9 @@ class Problem:
     eps: float = 1e-8
     c_ref: float = C_REF
     medium: Optional[Medium] = None
-    sector_half_angle: float = 0.0
+    sector_half_angle: float = 0.0    # curved array: sector half angle; linear: half width (m)
     depth_range: tuple = (0.0, 0.0)
+    lens_z: float = 0.0       # flat lens (lens_mode 2): outer surface z = lens_z
 
     @property
     def ne(self) -> int:
@@ -185,8 +186,10 @@ class Problem:
         return self.medium.speed_at(X, Z)
 
 
-# Table II (phantom C5-2v and in vivo C5-2v columns)
+# Table II (phantom L12-3v, phantom C5-2v and in vivo C5-2v columns)
 TABLE2 = {
+    "phantom_l12": dict(lr=0.0030, w1=7.0, kx1=0.0010, kz1=0.0200, w2=0.0, kx2=0.0,
+                        kz2=0.0, rho_thresh=0.9, fnum=0.75, nseg=32),
     "phantom_c5": dict(lr=0.0030, w1=10.0, kx1=0.0100, kz1=0.0100, w2=100.0, kx2=0.0010,
                        kz2=0.0010, rho_thresh=0.9, fnum=0.5, nseg=32),
     "invivo_c5": dict(lr=0.0500, w1=100.0, kx1=0.0100, kz1=0.0100, w2=100.0, kx2=0.0020,
@@ -264,6 +267,67 @@ def curvilinear_problem(name: str, *, ne: int, radius: float, pitch: float, fc: 
         sector_half_angle=float(half), depth_range=(depth_min, depth_max))
 
 
+def linear_problem(name: str, *, ne: int, pitch: float, fc: float, d_lens: float, c_lens: float,
+                   ns: int, fs: float, nx: int, nz: int, n_lat: int, n_ax: int, patch_w: int,
+                   depth_min: float, depth_max: float, sub_width: int, hyper: dict,
+                   medium: Optional[Medium] = None, t_ttp: float = 0.0, t0: float = 0.0,
+                   lens_mode: int = 2, apod_mode: int = 0, lat_frac: float = 0.8,
+                   grid_margin: float = 1e-3) -> Problem:
+    """Linear array on z = 0 (elements along x), a flat lens whose outer surface is the
+    line z = d_lens, and a rectangular grid of square patches of patch_w x patch_w
+    pixels at lambda/2 (lambda at 1540 m/s) below the lens."""
+    ex = f32((np.arange(ne) - (ne - 1) / 2.0) * pitch)
+    ez = f32(np.zeros(ne))
+    lz = float(f32(d_lens))
+    half = lat_frac * abs(float(ex[-1])) if ne > 1 else 1e-3
+    lat = np.linspace(-half, half, n_lat) if n_lat > 1 else np.zeros(1)
+    ax = lz + (np.linspace(depth_min, depth_max, n_ax) if n_ax > 1 else np.array([depth_min]))
+    step = C_REF / fc / 2.0
+    h = (patch_w - 1) / 2.0
+    px, pz = [], []
+    for zc in ax:
+        for xc in lat:
+            for b in range(patch_w):
+                for k in range(patch_w):
+                    px.append(xc + (k - h) * step)
+                    pz.append(zc + (b - h) * step)
+    px = f32(np.array(px))
+    pz = f32(np.array(pz))
+    # grid: bounding box of the lens line over the aperture and every pixel
+    xmin = min(px.min(), ex.min()) - grid_margin
+    xmax = max(px.max(), ex.max()) + grid_margin
+    zmin = min(ez.min(), lz) - grid_margin
+    zmax = pz.max() + grid_margin
+    dx = float(f32((xmax - xmin) / (nx - 1)))
+    dz = float(f32((zmax - zmin) / (nz - 1)))
+    return Problem(
+        name=name, elem_x=ex, elem_z=ez, arc_cx=0.0, arc_cz=0.0, arc_radius=0.0,
+        d_lens=float(f32(d_lens)), c_lens=float(f32(c_lens)), t_ttp=float(f32(t_ttp)),
+        lens_mode=lens_mode, fnum=float(f32(hyper["fnum"])), apod_mode=apod_mode,
+        n_patch=n_lat * n_ax, patch_npix=patch_w * patch_w, pix_x=px, pix_z=pz,
+        nx=nx, nz=nz, x0=float(f32(xmin)), z0=float(f32(zmin)), dx=dx, dz=dz,
+        nseg=int(hyper["nseg"]), ns=ns, fs=float(f32(fs)), fd=float(f32(fc)), fc=fc,
+        t0=float(f32(t0)), sub_width=sub_width, rho_thresh=float(f32(hyper["rho_thresh"])),
+        w1=hyper["w1"], kx1=hyper["kx1"], kz1=hyper["kz1"], w2=hyper["w2"],
+        kx2=hyper["kx2"], kz2=hyper["kz2"], lr=hyper["lr"], medium=medium,
+        sector_half_angle=float(half), depth_range=(depth_min, depth_max), lens_z=lz)
+
+
+def config_linear_tiny(**over) -> Problem:
+    """32-element, 0.2 mm-pitch linear array at 6 MHz with the L12-3v lens of Table I
+    (0.67 mm at 1049.4 m/s, t_ttp 578.3 ns); 32 x 32 x 1024 samples at 24 MHz; 16 x 16
+    grid; 16 patches of 5 x 5 pixels from 4 to 20 mm below the lens; Table II L12-3v
+    column; two-layer medium (6 mm at 1575 m/s over 1516 m/s, a tissue layer on a
+    phantom)."""
+    kw = dict(ne=32, pitch=0.2e-3, fc=6e6, d_lens=0.67e-3, c_lens=1049.4, t_ttp=578.3e-9,
+              ns=1024, fs=24e6, nx=16, nz=16, n_lat=4, n_ax=4, patch_w=5,
+              depth_min=4e-3, depth_max=20e-3, sub_width=4, hyper=TABLE2["phantom_l12"],
+              medium=Medium(speeds=[1575.0, 1516.0], base=[6.67e-3], amp=[0.0], period=[0.0],
+                            phase=[0.0]))
+    kw.update(over)
+    return linear_problem("l32_fsa1024", **kw)
+
+
 def config_tiny(**over) -> Problem:
     """32-element, 40 mm-radius, 0.4 mm-pitch, 3 MHz array; 1.0 mm lens at 1000 m/s;
     32 x 32 x 1024 samples at 12 MHz; 16 x 16 grid; 64 patches of 5 x 5 pixels;
@@ -319,14 +383,20 @@ def sector_scatterers(problem: Problem, n: int, seed: int, depth=(2e-3, None),
     """n scatterers uniform in area over the imaging sector, N(0,1) amplitudes,
     none inside the medium's cysts."""
     rng = np.random.default_rng(seed)
-    RL = problem.lens_radius
     d0 = depth[0]
     d1 = depth[1] if depth[1] is not None else problem.depth_range[1] + 10e-3
-    half = half_angle if half_angle is not None else 1.15 * problem.sector_half_angle
-    r = np.sqrt(rng.uniform((RL + d0) ** 2, (RL + d1) ** 2, n))
-    a = rng.uniform(-half, half, n)
-    x = problem.arc_cx + r * np.sin(a)
-    z = problem.arc_cz + r * np.cos(a)
+    if problem.arc_radius == 0.0:
+        # linear array: a rectangle below the lens, 15 % wider than the patches
+        half = 1.15 * problem.sector_half_angle + 2e-3
+        x = rng.uniform(-half, half, n)
+        z = rng.uniform(problem.lens_z + d0, problem.lens_z + d1, n)
+    else:
+        RL = problem.lens_radius
+        half = half_angle if half_angle is not None else 1.15 * problem.sector_half_angle
+        r = np.sqrt(rng.uniform((RL + d0) ** 2, (RL + d1) ** 2, n))
+        a = rng.uniform(-half, half, n)
+        x = problem.arc_cx + r * np.sin(a)
+        z = problem.arc_cz + r * np.cos(a)
     amp = rng.standard_normal(n)
     keep = np.ones(n, bool)
     if problem.medium is not None:
@@ -345,9 +415,9 @@ def oneway_times(problem: Problem, kx: np.ndarray, kz: np.ndarray,
     ex = np.ascontiguousarray(problem.elem_x, np.float64)
     ez = np.ascontiguousarray(problem.elem_z, np.float64)
     T = np.empty((problem.ne, kx.shape[0]), np.float64)
+    kind = {0: 1, 1: 0, 2: 2}[int(problem.lens_mode)]     # curved lens / none / flat lens
     lib.sy_oneway_times(problem.ne, _dp(ex), _dp(ez), problem.arc_cx, problem.arc_cz,
-                        problem.lens_radius, problem.c_lens,
-                        1 if problem.lens_mode == 0 else 0, ctypes.byref(med),
+                        problem.lens_radius, problem.lens_z, problem.c_lens, kind, ctypes.byref(med),
                         kx.shape[0], _dp(kx), _dp(kz), _dp(T))
     return T
 

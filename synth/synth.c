@@ -106,14 +106,44 @@ double sy_segment_time(const sy_medium *m, double ax, double az, double bx, doub
     return acc * len;
 }
 
-/* one-way time element -> scatterer: lens leg (c_lens) + tissue leg through the layers.
- * The exit point minimises lens time + straight distance in the top layer (Snell at
- * the lens surface), found by golden-section search between the element and the
- * scatterer angles. */
-static double oneway(const sy_medium *m, double ex, double ez, double cx, double cz,
-                     double RL, double c_lens, int lens_on, double kx, double kz)
+/* one-way time element -> scatterer through a flat lens whose outer surface is the
+ * line z = lz: the exit point minimises lens time + straight distance in the top layer
+ * (Snell at the lens surface).  The lens-side angle is below asin(c_lens / c_tissue),
+ * so the exit point lies within a few lens thicknesses of the element foot;
+ * golden-section search there. */
+static double oneway_flat(const sy_medium *m, double ex, double ez, double lz, double c_lens,
+                          double kx, double kz)
 {
-    if (!lens_on) return sy_segment_time(m, ex, ez, kx, kz);
+    double h1 = lz - ez, h2 = kz - lz;
+    double s_top = m->slow[layer_of(m, ex, ez)];
+    double a = ex < kx ? ex : kx, b = ex < kx ? kx : ex;
+    double w = 4.0 * h1 + 1e-4;
+    if (a < ex - w) a = ex - w;
+    if (b > ex + w) b = ex + w;
+    const double gr = 0.6180339887498949;
+    double c1 = b - gr * (b - a), c2 = a + gr * (b - a);
+#define SY_TF(x) (hypot((x) - ex, h1) / c_lens + hypot(kx - (x), h2) * s_top)
+    double f1 = SY_TF(c1), f2 = SY_TF(c2);
+    /* an exit-point error d only changes the time by O(d^2): 1e-12 m is ample */
+    for (int it = 0; it < 80 && b - a > 1e-12; ++it) {
+        if (f1 < f2) { b = c2; c2 = c1; f2 = f1; c1 = b - gr * (b - a); f1 = SY_TF(c1); }
+        else { a = c1; c1 = c2; f1 = f2; c2 = a + gr * (b - a); f2 = SY_TF(c2); }
+    }
+#undef SY_TF
+    double qx = 0.5 * (a + b);
+    return hypot(qx - ex, h1) / c_lens + sy_segment_time(m, qx, lz, kx, kz);
+}
+
+/* one-way time element -> scatterer: lens leg (c_lens) + tissue leg through the layers.
+ * lens_kind 0: no lens; 1: curved lens (arc of radius RL about (cx, cz)); 2: flat lens
+ * (line z = lz).  For the curved lens the exit point minimises lens time + straight
+ * distance in the top layer (Snell at the lens surface), found by golden-section
+ * search between the element and the scatterer angles. */
+static double oneway(const sy_medium *m, double ex, double ez, double cx, double cz,
+                     double RL, double lz, double c_lens, int lens_kind, double kx, double kz)
+{
+    if (lens_kind == 0) return sy_segment_time(m, ex, ez, kx, kz);
+    if (lens_kind == 2) return oneway_flat(m, ex, ez, lz, c_lens, kx, kz);
     double the = atan2(ex - cx, ez - cz), thk = atan2(kx - cx, kz - cz);
     double s_top = m->slow[layer_of(m, ex, ez)];
     double a = the < thk ? the : thk, b = the < thk ? thk : the;
@@ -139,14 +169,14 @@ static double oneway(const sy_medium *m, double ex, double ez, double cx, double
 
 /* T[e][k] one-way times for every element and scatterer */
 void sy_oneway_times(int ne, const double *ex, const double *ez, double cx, double cz,
-                     double RL, double c_lens, int lens_on, const sy_medium *m,
+                     double RL, double lz, double c_lens, int lens_kind, const sy_medium *m,
                      int nk, const double *kx, const double *kz, double *T)
 {
     long total = (long)ne * nk;
 #pragma omp parallel for schedule(dynamic, 4096)
     for (long idx = 0; idx < total; ++idx) {
         int e = (int)(idx / nk), k = (int)(idx % nk);
-        T[idx] = oneway(m, ex[e], ez[e], cx, cz, RL, c_lens, lens_on, kx[k], kz[k]);
+        T[idx] = oneway(m, ex[e], ez[e], cx, cz, RL, lz, c_lens, lens_kind, kx[k], kz[k]);
     }
 }
 

@@ -30,11 +30,16 @@ def small(**over):
 def test_table_values_match_paper():
     """Table I/II values as printed in the paper drive the configs."""
     t2 = json.load(open(os.path.join(GOLDEN, "table2_hyperparameters.json")))
-    for col in ("phantom_c5", "invivo_c5"):
+    for col in ("phantom_l12", "phantom_c5", "invivo_c5"):
         for k, v in t2[col].items():
             assert synth.TABLE2[col][k] == pytest.approx(v, rel=0, abs=0), (col, k)
     t1 = json.load(open(os.path.join(GOLDEN, "table1_lens_calibration.json")))
     assert t1["C5-2v (Phantoms)"]["c_lens"] == 999.4
+    # the linear-array configuration uses the L12-3v lens of Table I
+    pl = synth.config_linear_tiny()
+    assert pl.c_lens == pytest.approx(t1["L12-3v"]["c_lens"], rel=1e-7)
+    assert pl.d_lens == pytest.approx(t1["L12-3v"]["d_lens_mm"] * 1e-3, rel=1e-7)
+    assert pl.t_ttp == pytest.approx(t1["L12-3v"]["t_ttp_ns"] * 1e-9, rel=1e-7)
 
 
 def test_eq3_orientation_exact_on_uniform_arc(tiny):
@@ -134,6 +139,75 @@ def test_exit_straight_line_when_lens_matches_medium():
             phi, tl, qx, qz, _ = o.exit_point(e, x, z, 1.0 / c)
             T = tl + math.hypot(x - qx, z - qz) / c
             assert T == pytest.approx(math.hypot(x - p.elem_x[e], z - p.elem_z[e]) / c, rel=1e-14)
+
+
+# ---------------------------------------------------------------- flat lens (linear array)
+def _brute_exit_flat(p, e, x, z, sbar, n=1_000_001):
+    """Dense search along the lens line z = lens_z."""
+    xe, ze = p.elem_x[e], p.elem_z[e]
+    lo, hi = min(xe, x) - 1e-3, max(xe, x) + 1e-3
+    u = np.linspace(lo, hi, n)
+    T = np.hypot(u - xe, p.lens_z - ze) / p.c_lens + np.hypot(x - u, z - p.lens_z) * sbar
+    k = int(np.argmin(T))
+    u2 = np.linspace(u[max(k - 1, 0)], u[min(k + 1, n - 1)], 200_001)
+    T2 = np.hypot(u2 - xe, p.lens_z - ze) / p.c_lens + np.hypot(x - u2, z - p.lens_z) * sbar
+    k2 = int(np.argmin(T2))
+    return u2[k2], T2[k2]
+
+
+def test_flat_lens_exit_matches_brute_force_and_snell():
+    """Eq. 8 with a flat lens: the exit point minimises the two-leg time (dense search)
+    and satisfies Snell's law about the lens normal (the z axis)."""
+    p = synth.config_linear_tiny()
+    o = oracle.Oracle(p)
+    rng = np.random.default_rng(5)
+    sbar = 1.0 / 1530.0
+    for _ in range(12):
+        e = int(rng.integers(p.ne))
+        k = int(rng.integers(p.npix))
+        x, z = p.pix_x[k], p.pix_z[k]
+        u, tl, qx, qz, it = o.exit_point(e, x, z, sbar)
+        assert it > 0 and qz == p.lens_z and qx == u
+        T = tl + math.hypot(x - qx, z - qz) * sbar
+        bu, bT = _brute_exit_flat(p, e, x, z, sbar)
+        assert T <= bT * (1 + 1e-14)
+        assert abs(T - bT) <= 1e-12 * bT
+        assert abs(u - bu) < 1e-8
+        sl = (qx - p.elem_x[e]) / math.hypot(qx - p.elem_x[e], qz - p.elem_z[e])
+        st = (x - qx) / math.hypot(x - qx, z - qz)
+        assert abs(sl / p.c_lens - st * sbar) < 1e-12 * sbar
+
+
+def test_flat_lens_closed_forms():
+    """A pixel straight below the element exits at the element's foot with
+    T_lens = h1 / c_lens; with c_lens = c_med the path is the straight line."""
+    p = synth.config_linear_tiny()
+    o = oracle.Oracle(p)
+    h1 = p.lens_z - p.elem_z[3]
+    u, tl, qx, qz, _ = o.exit_point(3, p.elem_x[3], p.lens_z + 7e-3, 1.0 / 1540.0)
+    assert u == p.elem_x[3] and tl == pytest.approx(h1 / p.c_lens, rel=1e-15)
+    c = 1500.0
+    pc = synth.config_linear_tiny(c_lens=c)
+    oc = oracle.Oracle(pc)
+    for e in (0, 9, 31):
+        for k in (0, 150, 399):
+            x, z = pc.pix_x[k], pc.pix_z[k]
+            _, tl, qx, qz, _ = oc.exit_point(e, x, z, 1.0 / c)
+            T = tl + math.hypot(x - qx, z - qz) / c
+            assert T == pytest.approx(math.hypot(x - pc.elem_x[e], z - pc.elem_z[e]) / c, rel=1e-14)
+
+
+@pytest.mark.parametrize("linear", [False, True])
+def test_homogeneous_delays_match_independent_simulator(linear):
+    """Uniform medium: the oracle's one-way delays (Newton exit point, Eq. 1 ray sum on a
+    uniform grid) equal the simulator's (golden-section exit point, exact segment
+    time), for the curved and the flat lens."""
+    c = 1530.0
+    p = synth.config_linear_tiny() if linear else small()
+    s = np.full((p.nz, p.nx), 1.0 / c)
+    T, _, _ = oracle.Oracle(p).delays(s)
+    Ts = synth.oneway_times(p, p.pix_x, p.pix_z, synth.Medium(speeds=[c]))
+    np.testing.assert_allclose(T, Ts, rtol=1e-11, atol=0)
 
 
 def test_zero_thickness_lens_reduces_to_straight_ray():
