@@ -57,8 +57,10 @@ enum { AF_IQ_C64 = 0,        /* interleaved float32 (re, im) */
        AF_IQ_F16 = 2 };      /* interleaved float16 (re, im), times a per-transmit float scale */
 
 /* lens model */
-enum { AF_LENS_BENT_RAY = 0, /* Eq. 7-8: Fermat exit point on the lens surface */
-       AF_LENS_NONE = 1 };   /* Eq. 1 straight rays from the element */
+enum { AF_LENS_BENT_RAY = 0, /* Eq. 7-8: Fermat exit point on a curved lens surface */
+       AF_LENS_NONE = 1,     /* Eq. 1 straight rays from the element (with t_ttp: the
+                                conventional model of Eq. 6) */
+       AF_LENS_PLANAR = 2 }; /* Eq. 7-8 with a flat lens (linear array) */
 
 /* apodization */
 enum { AF_APOD_FNUMBER = 0,  /* |x'| <= z' / (2F), z' > 0 (usual f-number reading of Eq. 4) */
@@ -69,9 +71,12 @@ enum { AF_APOD_FNUMBER = 0,  /* |x'| <= z' / (2F), z' > 0 (usual f-number readin
  *
  * Array (Sec. II-A): element a at (elem_x[a], elem_z[a]); its orientation is
  *   Eq. 3 from its neighbours (end elements: linear extrapolation).
- * Lens (Sec. II-B, III-B, Table I): outer surface = arc of radius lens_radius
- *   about (arc_cx, arc_cz), concentric with the elements; sound speed c_lens;
- *   t_ttp is added to every round-trip delay (Eq. 6-7).
+ * Lens (Sec. II-B, III-B, Table I): AF_LENS_BENT_RAY: outer surface = arc of
+ *   radius lens_radius about (arc_cx, arc_cz), concentric with the elements;
+ *   AF_LENS_PLANAR: outer surface = the line z = lens_z, every element above it
+ *   (elem_z < lens_z) and every pixel below it (arc_cx, arc_cz, lens_radius
+ *   unused); sound speed c_lens; t_ttp is added to every round-trip delay
+ *   (Eq. 6-7).
  * Image points r_Omega: n_patch patches of patch_npix pixels, patch-major
  *   (pixel p belongs to patch p / patch_npix), at (pix_x[p], pix_z[p]).
  * Slowness grid (Sec. III-A): node (i, j) at (x0 + i dx, z0 + j dz),
@@ -93,7 +98,7 @@ typedef struct {
     int n_elem;
     const double *elem_x, *elem_z;
     int lens_mode;
-    double arc_cx, arc_cz, lens_radius, c_lens, t_ttp;
+    double arc_cx, arc_cz, lens_radius, c_lens, t_ttp, lens_z;
     int apod_mode;
     double fnum;
     int n_patch, patch_npix;
@@ -165,7 +170,9 @@ af_status af_sync_status(af_plan_t plan);
  * Either pointer may be NULL. */
 af_status af_get_delays(af_plan_t plan, double *d_T, uint8_t *d_apod);
 
-/* Lens exit angles phi[e][p] (rad, about the arc centre), [n_elem][npix]. */
+/* Lens exit points, [n_elem][npix] float: the exit angle (rad, about the arc
+ * centre) for AF_LENS_BENT_RAY, the exit x (m, on the line z = lens_z) for
+ * AF_LENS_PLANAR, 0 for AF_LENS_NONE. */
 af_status af_get_exit_angles(af_plan_t plan, float *d_phi);
 
 /* Subaperture images B[b][p] as interleaved float (re, im), b = i*nsub + j,

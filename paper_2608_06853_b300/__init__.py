@@ -30,7 +30,7 @@ LIB_PATH = os.path.join(_HERE, "libaf.so")
 AF_OK, AF_ERR_ARG, AF_ERR_SHAPE, AF_ERR_DTYPE, AF_ERR_CUDA = 0, 1, 2, 3, 4
 AF_ERR_NUMERIC, AF_ERR_TIMEOUT, AF_ERR_UNSUPPORTED, AF_ERR_STATE = 5, 6, 7, 8
 AF_IQ_C64, AF_IQ_BF16, AF_IQ_F16 = 0, 1, 2
-AF_LENS_BENT_RAY, AF_LENS_NONE = 0, 1
+AF_LENS_BENT_RAY, AF_LENS_NONE, AF_LENS_PLANAR = 0, 1, 2
 AF_APOD_FNUMBER, AF_APOD_PRINTED = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -42,6 +42,7 @@ class AfConfig(ctypes.Structure):
         ("n_elem", ctypes.c_int), ("elem_x", _dp), ("elem_z", _dp),
         ("lens_mode", ctypes.c_int), ("arc_cx", ctypes.c_double), ("arc_cz", ctypes.c_double),
         ("lens_radius", ctypes.c_double), ("c_lens", ctypes.c_double), ("t_ttp", ctypes.c_double),
+        ("lens_z", ctypes.c_double),
         ("apod_mode", ctypes.c_int), ("fnum", ctypes.c_double),
         ("n_patch", ctypes.c_int), ("patch_npix", ctypes.c_int), ("pix_x", _dp), ("pix_z", _dp),
         ("nx", ctypes.c_int), ("nz", ctypes.c_int), ("x0", ctypes.c_double), ("z0", ctypes.c_double),
@@ -146,6 +147,7 @@ def make_config(problem, iq_dtype: int = AF_IQ_C64):
     c.lens_mode = int(problem.lens_mode)
     c.arc_cx, c.arc_cz = float(problem.arc_cx), float(problem.arc_cz)
     c.lens_radius, c.c_lens, c.t_ttp = float(problem.lens_radius), float(problem.c_lens), float(problem.t_ttp)
+    c.lens_z = float(getattr(problem, "lens_z", 0.0))
     c.apod_mode, c.fnum = int(problem.apod_mode), float(problem.fnum)
     c.n_patch, c.patch_npix = int(problem.n_patch), int(problem.patch_npix)
     c.pix_x, c.pix_z = arr(problem.pix_x), arr(problem.pix_z)

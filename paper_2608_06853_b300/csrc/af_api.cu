@@ -135,7 +135,8 @@ af_status af_check_config(const af_config *c)
         return fail(AF_ERR_ARG, "bad fs / fd / t0 / t_ttp");
     if (c->iq_dtype != AF_IQ_C64 && c->iq_dtype != AF_IQ_BF16 && c->iq_dtype != AF_IQ_F16)
         return fail(AF_ERR_DTYPE, "unknown iq_dtype %d", c->iq_dtype);
-    if (c->lens_mode != AF_LENS_BENT_RAY && c->lens_mode != AF_LENS_NONE) return fail(AF_ERR_ARG, "unknown lens_mode %d", c->lens_mode);
+    if (c->lens_mode != AF_LENS_BENT_RAY && c->lens_mode != AF_LENS_NONE && c->lens_mode != AF_LENS_PLANAR)
+        return fail(AF_ERR_ARG, "unknown lens_mode %d", c->lens_mode);
     if (c->apod_mode != AF_APOD_FNUMBER && c->apod_mode != AF_APOD_PRINTED) return fail(AF_ERR_ARG, "unknown apod_mode %d", c->apod_mode);
     if (!(c->fnum > 0) || !is_fin(c->fnum)) return fail(AF_ERR_ARG, "fnum must be > 0");
     if (!is_fin(c->rho_thresh)) return fail(AF_ERR_ARG, "rho_thresh not finite");
@@ -159,7 +160,11 @@ af_status af_check_config(const af_config *c)
         remax = fmax(remax, hypot(c->elem_x[a] - c->arc_cx, c->elem_z[a] - c->arc_cz));
         if (c->lens_mode == AF_LENS_NONE && !inside(c->elem_x[a], c->elem_z[a]))
             return fail(AF_ERR_ARG, "element %d outside the slowness grid", a);
+        if (c->lens_mode == AF_LENS_PLANAR && !(c->elem_z[a] < c->lens_z))
+            return fail(AF_ERR_ARG, "element %d not above the lens line z = %.9g", a, c->lens_z);
     }
+    if (c->lens_mode == AF_LENS_PLANAR && (!(c->c_lens > 0) || !is_fin(c->c_lens) || !is_fin(c->lens_z)))
+        return fail(AF_ERR_ARG, "bad lens parameters");
     if (c->lens_mode == AF_LENS_BENT_RAY) {
         if (!(c->c_lens > 0) || !is_fin(c->c_lens) || !is_fin(c->arc_cx) || !is_fin(c->arc_cz))
             return fail(AF_ERR_ARG, "bad lens parameters");
@@ -167,10 +172,20 @@ af_status af_check_config(const af_config *c)
             return fail(AF_ERR_ARG, "lens_radius %.9g below the element radius %.9g", c->lens_radius, remax);
     }
     double pmin = emin, pmax = emax;
+    double xlo = 1e300, xhi = -1e300;            // flat lens: extent of the exit points
+    for (int a = 0; a < c->n_elem; ++a) {
+        xlo = fmin(xlo, c->elem_x[a]);
+        xhi = fmax(xhi, c->elem_x[a]);
+    }
     for (long long p = 0; p < npix; ++p) {
         const double x = c->pix_x[p], z = c->pix_z[p];
         if (!is_fin(x) || !is_fin(z)) return fail(AF_ERR_ARG, "pixel %lld not finite", p);
         if (!inside(x, z)) return fail(AF_ERR_ARG, "pixel %lld outside the slowness grid", p);
+        if (c->lens_mode == AF_LENS_PLANAR) {
+            if (!(z > c->lens_z)) return fail(AF_ERR_ARG, "pixel %lld not below the lens line", p);
+            xlo = fmin(xlo, x);
+            xhi = fmax(xhi, x);
+        }
         if (c->lens_mode == AF_LENS_BENT_RAY) {
             if (!(hypot(x - c->arc_cx, z - c->arc_cz) > c->lens_radius))
                 return fail(AF_ERR_ARG, "pixel %lld inside the lens", p);
@@ -178,6 +193,11 @@ af_status af_check_config(const af_config *c)
             pmin = fmin(pmin, th);
             pmax = fmax(pmax, th);
         }
+    }
+    if (c->lens_mode == AF_LENS_PLANAR && npix > 0) {
+        // every exit point lies on the lens line between its element and its pixel
+        if (!inside(xlo, c->lens_z) || !inside(xhi, c->lens_z))
+            return fail(AF_ERR_ARG, "lens line over [%.6g, %.6g] outside the slowness grid", xlo, xhi);
     }
     if (c->lens_mode == AF_LENS_BENT_RAY) {
         // every possible exit point lies on the lens arc between the extreme angles
@@ -266,16 +286,18 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
     g.arc_cx = (float)c->arc_cx;
     g.arc_cz = (float)c->arc_cz;
     g.RL = (float)c->lens_radius;
+    g.lens_z = (float)c->lens_z;
     g.fnum_inv2 = (float)(1.0 / (2.0 * c->fnum));
     g.fnum_half = (float)(0.5 * c->fnum);
     g.x0 = (float)c->x0;
     g.z0 = (float)c->z0;
     g.inv_dx = (float)(1.0 / c->dx);
     g.inv_dz = (float)(1.0 / c->dz);
-    g.inv_c_lens = c->lens_mode == AF_LENS_BENT_RAY ? (float)(1.0 / c->c_lens) : 0.0f;
+    const bool has_lens = c->lens_mode == AF_LENS_BENT_RAY || c->lens_mode == AF_LENS_PLANAR;
+    g.inv_c_lens = has_lens ? (float)(1.0 / c->c_lens) : 0.0f;
     g.fs = (float)c->fs;
     g.wd = (float)(2.0 * 3.14159265358979323846 * c->fd);
-    if (c->lens_mode == AF_LENS_BENT_RAY) split_ff(c->fs / c->c_lens, &g.fs_clens_hi, &g.fs_clens_lo);
+    if (has_lens) split_ff(c->fs / c->c_lens, &g.fs_clens_hi, &g.fs_clens_lo);
     split_ff(0.5 * (c->t_ttp - c->t0) * c->fs, &g.off_hi, &g.off_lo);
     split_ff(c->fd / c->fs, &g.rfd_hi, &g.rfd_lo);
     {

@@ -187,6 +187,40 @@ __global__ void __launch_bounds__(PAIRS ? 768 : 256) delays_kernel(AfGeom g, con
             qx = fmaf(g.RL, sn, g.arc_cx);
             qz = fmaf(g.RL, cs, g.arc_cz);
             tl = ff_mul(ff_dist(qx, qz, el.x, el.y), fscl);      // lens leg in samples
+        } else if (g.lens_mode == AF_LENS_PLANAR) {
+            // Eq. 8 with a flat lens: exit x u on z = lens_z, root of
+            // dT/du = (u - xe) / (c_lens d1) - (xp - u) sbar / d2 (convex T)
+            const float h1 = g.lens_z - el.y, h2 = px.y - g.lens_z;
+            float lo = fminf(el.x, px.x), hi = fmaxf(el.x, px.x);
+            float u = warm ? fminf(fmaxf(phi[idx], lo), hi) : el.x;
+            bool conv = (lo == hi);
+            for (int it = 0; it < 16 && !conv; ++it) {
+                const float a = u - el.x, b = px.x - u;
+                const float d1 = sqrtf(fmaf(a, a, h1 * h1)), d2 = sqrtf(fmaf(b, b, h2 * h2));
+                const float r1 = 1.0f / d1, r2 = 1.0f / d2;
+                const float f = fmaf(a * g.inv_c_lens, r1, -b * sbar * r2);
+                const float fp = fmaf(h1 * h1 * g.inv_c_lens, r1 * r1 * r1, h2 * h2 * sbar * r2 * r2 * r2);
+                if (f == 0.0f) { conv = true; break; }     // stationary point reached exactly
+                if (f < 0.0f) lo = u; else hi = u;
+                float un = u - f / fp;
+                if (!(un >= lo && un <= hi)) un = 0.5f * (lo + hi);
+                // the delay error is second order in the exit-point error: 1e-8 m is ample
+                conv = fabsf(un - u) < 1e-8f || hi - lo < 1e-8f;
+                u = un;
+            }
+            // grazing exit (tissue ray beyond ~80 deg from the lens normal) or no
+            // convergence: solve again in float64
+            const float bx = px.x - u;
+            if (!conv || h2 < 0.17f * sqrtf(fmaf(bx, bx, h2 * h2))) {
+                u = (float)exit_solve_flat_fp64((double)el.x, (double)h1, (double)px.x, (double)h2,
+                                                (double)g.inv_c_lens, (double)sbar);
+                ++n_fp64;
+            }
+            ph = u;
+            phi[idx] = u;
+            qx = u;
+            qz = g.lens_z;
+            tl = ff_mul(ff_dist(qx, qz, el.x, el.y), fscl);      // lens leg in samples
         }
         // Eq. 1 discretised: L * (sbar + mean_k interp(s - sbar)) over N+1 endpoints
         const ff L = ff_dist(px.x, px.y, qx, qz);

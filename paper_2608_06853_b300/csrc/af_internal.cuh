@@ -18,6 +18,7 @@ struct AfGeom {
     int ns, nx, nz, ng, nseg, pitch;         // pitch = padded grid row length (>= nx + 4, odd)
     int lens_mode, apod_mode;
     float arc_cx, arc_cz, RL, fnum_inv2, fnum_half;
+    float lens_z;                            // flat lens: outer surface z = lens_z
     float x0, z0, inv_dx, inv_dz;
     float inv_c_lens;                        // for the FP64 fallback solve
     float fs, wd;                            // sample rate, 2 pi fd

@@ -54,4 +54,27 @@ __device__ double exit_solve_fp64(double re, double rp, double RL, double dp, do
     return x;
 }
 
+// Flat lens (outer surface the line z = zl): exit x u minimising
+//   T(u) = sqrt((u - xe)^2 + h1^2) / c_lens + sqrt((xp - u)^2 + h2^2) sbar,
+// h1 = zl - ze, h2 = zp - zl.  T'' > 0 and T' changes sign between xe and xp:
+// float64 safeguarded Newton / bisection on T' = 0 over that bracket.
+__device__ double exit_solve_flat_fp64(double xe, double h1, double xp, double h2, double inv_cl,
+                                       double sbar)
+{
+    double lo = fmin(xe, xp), hi = fmax(xe, xp), u = xe;
+    for (int it = 0; it < 100 && hi > lo; ++it) {
+        const double d1 = sqrt((u - xe) * (u - xe) + h1 * h1), d2 = sqrt((xp - u) * (xp - u) + h2 * h2);
+        const double f = (u - xe) * inv_cl / d1 - (xp - u) * sbar / d2;
+        const double fp = h1 * h1 * inv_cl / (d1 * d1 * d1) + h2 * h2 * sbar / (d2 * d2 * d2);
+        if (f == 0.0) break;
+        if (f < 0.0) lo = u; else hi = u;
+        double un = u - f / fp;
+        if (!(un >= lo && un <= hi)) un = 0.5 * (lo + hi);
+        const double step = fabs(un - u);
+        u = un;
+        if (step < 1e-15 || hi - lo < 1e-15) break;
+    }
+    return u;
+}
+
 }  // namespace

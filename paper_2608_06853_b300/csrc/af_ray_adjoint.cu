@@ -160,6 +160,9 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
                     sincosf(phi[idx], &sn, &cs);
                     qx = fmaf(g.RL, sn, g.arc_cx);
                     qz = fmaf(g.RL, cs, g.arc_cz);
+                } else if (g.lens_mode == AF_LENS_PLANAR) {
+                    qx = phi[idx];          // exit x on the lens line
+                    qz = g.lens_z;
                 } else {
                     const float4 el = elem[e];
                     qx = el.x;

@@ -91,6 +91,26 @@ def test_degenerate_but_valid_shapes():
     assert af.check_config(R(p, lens_mode=af.AF_LENS_NONE)) == af.AF_OK
 
 
+def test_flat_lens_configs():
+    """Linear array with a flat lens: valid as built; an element not above the lens
+    line, a pixel not below it, or a lens line leaving the grid box is rejected."""
+    p = synth.config_linear_tiny()
+    R = dataclasses.replace
+    lib = af.load()
+    assert p.lens_mode == af.AF_LENS_PLANAR
+    assert af.check_config(p) == af.AF_OK
+    assert af.check_config(R(p, lens_mode=af.AF_LENS_NONE)) == af.AF_OK
+    ez = p.elem_z.copy()
+    ez[5] = p.lens_z + 1e-4
+    assert af.check_config(R(p, elem_z=ez)) == af.AF_ERR_ARG
+    assert b"above the lens" in lib.af_last_error()
+    pz = p.pix_z.copy()
+    pz[7] = p.lens_z - 1e-4
+    assert af.check_config(R(p, pix_z=pz)) == af.AF_ERR_ARG
+    assert af.check_config(R(p, lens_z=p.z0 - 1e-3)) == af.AF_ERR_ARG
+    assert af.check_config(R(p, c_lens=0.0)) == af.AF_ERR_ARG
+
+
 def test_plan_without_gpu_fails_cleanly():
     """Without a CUDA device af_plan reports AF_ERR_CUDA instead of crashing."""
     import torch

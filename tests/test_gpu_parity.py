@@ -208,6 +208,25 @@ def test_ragged_and_variant_shapes():
         assert rel_l2(run.dLds, ref["grad"]) <= GRAD_TOL, kw
 
 
+@pytest.mark.parametrize("lens_mode", [af.AF_LENS_PLANAR, af.AF_LENS_NONE])
+def test_linear_array_parity(lens_mode):
+    """Linear array (L12-3v lens of Table I): the bent-ray model with a flat lens, and
+    the Eq. 6 conventional model (straight rays + the scalar t_ttp), every stage
+    against the oracle."""
+    p = synth.config_linear_tiny(lens_mode=lens_mode)
+    psi = synth.simulate(p, 800, seed=17)
+    run, o, ref = full_parity(p, psi, smooth_speed(p, 6))
+    on = run.apod == 1
+    assert on.any()
+    assert np.abs(run.T - ref["T"])[on].max() <= DELAY_TOL
+    if lens_mode == af.AF_LENS_PLANAR:
+        np.testing.assert_allclose(run.phi[on], ref["phi"][on], rtol=0, atol=5e-8)   # exit x (m)
+    assert rel_l2(run.B, ref["B"]) <= IMG_TOL
+    assert abs(run.L[0] - ref["parts"][0]) <= LOSS_TOL * max(abs(ref["parts"][0]), 1e-12)
+    assert rel_l2(run.dLds, ref["grad"]) <= GRAD_TOL
+    assert run.plan.counters()["fp64_solves"] == 0
+
+
 def test_degenerate_cases():
     """No patches: loss and gradient are the regulariser's; < 3 subapertures: no CMPE terms."""
     base = synth.config_tiny(n_ang=2, n_rad=2, patch_w=3)
