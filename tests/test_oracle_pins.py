@@ -576,3 +576,50 @@ def test_mlp_oracle_closed_forms():
     np.testing.assert_allclose(gb4, [0.6, -0.4])
     assert mo.bf16(np.array([1.0 + 2 ** -9]))[0] == 1.0
     assert mo.bf16(np.array([0.75]))[0] == 0.75
+
+
+# ---------------------------------------------------------------- image metrics (Sec. III-F)
+def test_metrics_closed_forms():
+    """Coherence factor, lag-one coherence, contrast, CNR and gCNR on inputs whose
+    values are known in closed form."""
+    from oracle import metrics as M
+    n, P = 8, 5
+    same = np.ones((n, P), complex) * (0.3 + 0.4j)
+    assert np.allclose(M.coherence_factor(same), 1.0)                 # coherent channels
+    spread = np.exp(2j * np.pi * np.arange(n) / n)[:, None] * np.ones(P)
+    assert np.allclose(M.coherence_factor(spread), 0.0, atol=1e-15)   # phases cancel
+    one = np.zeros((n, P), complex)
+    one[3] = 2.0
+    assert np.allclose(M.coherence_factor(one), 1.0 / n)              # a single channel
+    sel = np.ones(P, bool)
+    assert M.lag_one_coherence(same, sel) == pytest.approx(1.0)
+    alt = ((-1.0) ** np.arange(n))[:, None] * np.ones(P)
+    assert M.lag_one_coherence(alt.astype(complex), sel) == pytest.approx(-1.0)
+    env = np.array([1.0, 3.0, 9.0, 11.0, 5.0])
+    roi = np.array([1, 1, 2, 2, 0])
+    c, cnr, g, mi, mo = M.contrast_cnr_gcnr(env, roi)
+    assert c == pytest.approx(20 * math.log10(2.0 / 10.0), rel=1e-14)
+    assert cnr == pytest.approx(8.0 / math.sqrt(2.0), rel=1e-14)
+    assert g == pytest.approx(1.0) and (mi, mo) == (2.0, 10.0)        # disjoint histograms
+    env2 = np.array([1.0, 2.0, 1.0, 2.0])
+    assert M.contrast_cnr_gcnr(env2, np.array([1, 1, 2, 2]))[2] == pytest.approx(0.0)   # identical
+    assert M.speed_mae([1500.0, 1520.0], [1510.0, 1510.0]) == pytest.approx(10.0)
+
+
+def test_cmcc_matches_cmpe_correlations():
+    """The mean common-midpoint correlation equals the mean of the C oracle's CMPE
+    correlation coefficients (an independent implementation of the same sums); images
+    identical along each common-midpoint pair give 1."""
+    from oracle import metrics as M
+    p = small()
+    o = oracle.Oracle(p)
+    rng = np.random.default_rng(4)
+    B = rng.standard_normal((p.nsub ** 2, p.npix)) + 1j * rng.standard_normal((p.nsub ** 2, p.npix))
+    _, _, rho, _, _ = o.cmpe(B)
+    assert M.cmcc(B, p.nsub, p.n_patch, p.patch_npix) == pytest.approx(rho.mean(), rel=1e-12)
+    # images that depend only on i + j (the common midpoint) are identical in each pair
+    C = np.empty_like(B)
+    for i in range(p.nsub):
+        for j in range(p.nsub):
+            C[i * p.nsub + j] = B[(i + j) % B.shape[0]]
+    assert M.cmcc(C, p.nsub, p.n_patch, p.patch_npix) == pytest.approx(1.0, rel=1e-12)
