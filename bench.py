@@ -343,9 +343,20 @@ def run_sweep_images(p, iq32, plan32, stream, dev):
             plan32.bmode()
         e1.record(stream)
     torch.cuda.synchronize(dev)
+    # image metrics of that forward: target = pixels inside the medium's cysts, background
+    # = every other pixel (host wall time: scratch allocation, kernels and read back)
+    inside = np.zeros(p.npix, bool)
+    for (cxs, czs, rad) in (p.medium.cysts if p.medium is not None else []):
+        inside |= np.hypot(p.pix_x - cxs, p.pix_z - czs) < rad
+    roi = torch.from_numpy(np.where(inside, 1, 2).astype(np.uint8)).to(dev)
+    plan32.image_metrics(roi)
+    t1 = time.perf_counter()
+    met = plan32.image_metrics(roi)
+    t_met = time.perf_counter() - t1
     return {"sweep_speeds": len(speeds), "sweep_ms": t_sweep * 1e3, "sweep_ms_per_speed": t_sweep * 1e3 / len(speeds),
             "sweep_best_mps": best, "sweep_cmpe_min": float(cmpe.min()), "sweep_cmpe_max": float(cmpe.max()),
-            "images_ms": e0.elapsed_time(e1) / 10,
+            "images_ms": e0.elapsed_time(e1) / 10, "metrics_ms": t_met * 1e3,
+            "metrics": {k: met[k] for k in ("cf_mean", "loc", "cmcc", "contrast_db", "gcnr", "n_in")},
             "note": "sweep: wall time incl. host pixel moves and per-speed readback; images: CUDA events"}
 
 

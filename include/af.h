@@ -191,6 +191,40 @@ af_status af_get_cmpe(af_plan_t plan, float *d_z, uint8_t *d_mask, int *h_n_acti
  * A plan over a dense pixel grid gives the full field of view. */
 af_status af_get_bmode(af_plan_t plan, float *d_bmode, float *d_cmpe_image);
 
+/* Image-quality metrics of the last af_forward (Sec. III-F, Model Evaluation;
+ * the paper defines MAE and cites the other metrics, read here as follows).
+ * S_j(p) = sum_i B_ij(p) is the image of receive subaperture j.
+ *  cf_mean      mean over the background of |sum_j S_j|^2 / (n_sub sum_j |S_j|^2)
+ *               (coherence factor over receive subapertures);
+ *  loc          mean over j of Re sum_p S_j conj(S_j+1) /
+ *               sqrt(sum_p |S_j|^2 sum_p |S_j+1|^2), p over the background
+ *               (lag-one coherence over receive subapertures);
+ *  cmcc         mean over patches and common-midpoint pairs of the CMPE
+ *               correlation coefficient rho;
+ *  contrast_db  20 log10(mean_in / mean_out) of the envelope |sum_ij B_ij|;
+ *  cnr          |mean_in - mean_out| / sqrt(var_in + var_out) (population
+ *               variances);
+ *  gcnr         1 - sum_b min(h_in(b), h_out(b)), h the normalised histograms of
+ *               the envelope over nbins equal bins spanning its range over both
+ *               regions (generalized CNR).
+ * d_roi [npix] uint8 (device): 1 target region, 2 background, 0 unused.
+ * Quantities of an empty region are NaN.  Allocates and frees its own device
+ * scratch (about (2 n_sub + 8) x npix floats); synchronises the plan's stream.
+ * Errors: AF_ERR_ARG (NULL, nbins outside [2, 65536]), AF_ERR_STATE (no forward
+ * pass yet), AF_ERR_CUDA. */
+typedef struct {
+    double cf_mean, loc, cmcc, contrast_db, cnr, gcnr, mean_in, mean_out;
+    long long n_in, n_out;
+} af_metrics;
+af_status af_image_metrics(af_plan_t plan, const uint8_t *d_roi, int nbins, af_metrics *h_out);
+
+/* Sound-speed MAE (Sec. III-F): mean over the plan's pixels of
+ * |1 / bicubic(s, r_p) - c_true[p]| (Keys a = -1/2, clamp to edge, the
+ * interpolation of Sec. III-A).  d_s [nz][nx] and d_c_true [npix] float on the
+ * device; the result is written to *h_mae (host).  Synchronises the plan's
+ * stream; allocates npix floats of scratch. */
+af_status af_speed_mae(af_plan_t plan, const float *d_s, const float *d_c_true, double *h_mae);
+
 /* dL/dB[b][p] (= dL/dRe B + j dL/dIm B) of the last af_adjoint,
  * [nsub*nsub][npix][2] float. */
 af_status af_get_image_grad(af_plan_t plan, float *d_G);

@@ -67,6 +67,12 @@ _lib = None
 
 # name -> (restype, argtypes) of every exported entry point of include/af.h
 _VP = ctypes.c_void_p
+class AfMetrics(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("cf_mean", "loc", "cmcc", "contrast_db", "cnr", "gcnr",
+                                                "mean_in", "mean_out")] + \
+               [("n_in", ctypes.c_longlong), ("n_out", ctypes.c_longlong)]
+
+
 _SIGNATURES = {
     "af_check_config": (ctypes.c_int, [ctypes.POINTER(AfConfig)]),
     "af_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(AfConfig), ctypes.POINTER(ctypes.c_size_t)]),
@@ -84,6 +90,8 @@ _SIGNATURES = {
     "af_get_cmpe": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_int)]),
     "af_get_image_grad": (ctypes.c_int, [_VP, _VP]),
     "af_get_bmode": (ctypes.c_int, [_VP, _VP, _VP]),
+    "af_image_metrics": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(AfMetrics)]),
+    "af_speed_mae": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_double)]),
     "af_get_delay_grad": (ctypes.c_int, [_VP, _VP]),
     "af_get_counters": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
     "af_cmpe_loss_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -320,6 +328,20 @@ class Plan:
         c = torch.empty_like(b)
         _check(self.lib.af_get_bmode(self.handle, _ptr(b), _ptr(c)), "af_get_bmode")
         return b, c
+
+    def image_metrics(self, roi, nbins: int = 256):
+        """Metrics of the last forward (af_image_metrics): roi [npix] uint8 tensor on the
+        device, 1 target, 2 background.  Returns a dict."""
+        m = AfMetrics()
+        _check(self.lib.af_image_metrics(self.handle, _ptr(roi), int(nbins), ctypes.byref(m)),
+               "af_image_metrics")
+        return {name: getattr(m, name) for name, _ in AfMetrics._fields_}
+
+    def speed_mae(self, s, c_true):
+        """Mean |1 / bicubic(s) - c_true| over the plan's pixels (af_speed_mae)."""
+        out = ctypes.c_double()
+        _check(self.lib.af_speed_mae(self.handle, _ptr(s), _ptr(c_true), ctypes.byref(out)), "af_speed_mae")
+        return out.value
 
     def image_grad(self):
         """dL/dB [nsub*nsub][npix] complex64 of the last adjoint."""

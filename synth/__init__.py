@@ -328,6 +328,22 @@ def config_linear_tiny(**over) -> Problem:
     return linear_problem("l32_fsa1024", **kw)
 
 
+def image_grid_problem(problem: Problem, n_lat: int, n_ax: int, depth: tuple,
+                       half: Optional[float] = None) -> Problem:
+    """The same curvilinear acquisition imaged on a dense polar grid: n_ax depths
+    below the lens (depth[0]..depth[1]) by n_lat angles (+-half, default 0.9 of the
+    sector), one patch per depth row (patch-major pixels).  The slowness grid is
+    unchanged, so the pixels must lie inside its box."""
+    RL = problem.lens_radius
+    half = 0.9 * problem.sector_half_angle if half is None else half
+    ang = np.linspace(-half, half, n_lat)
+    rad = RL + np.linspace(depth[0], depth[1], n_ax)
+    px = problem.arc_cx + rad[:, None] * np.sin(ang)[None, :]
+    pz = problem.arc_cz + rad[:, None] * np.cos(ang)[None, :]
+    return dataclasses.replace(problem, n_patch=n_ax, patch_npix=n_lat, pix_x=f32(px.ravel()),
+                               pix_z=f32(pz.ravel()))
+
+
 def config_tiny(**over) -> Problem:
     """32-element, 40 mm-radius, 0.4 mm-pitch, 3 MHz array; 1.0 mm lens at 1000 m/s;
     32 x 32 x 1024 samples at 12 MHz; 16 x 16 grid; 64 patches of 5 x 5 pixels;
