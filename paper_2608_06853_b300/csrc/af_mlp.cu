@@ -44,6 +44,15 @@ __device__ __forceinline__ float tanh_fast(float x)
     return y;
 }
 
+// x rounded to the nearest bfloat16 (ties to even), on the integer pipes instead
+// of a conversion instruction (finite x: the activations are tanh outputs)
+__device__ __forceinline__ float round_bf16(float x)
+{
+    uint32_t u = __float_as_uint(x);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return __uint_as_float(u & 0xFFFF0000u);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -385,87 +394,112 @@ __global__ void mlp_gen_kernel(MlpGeom G, MlpNorm n, long count, uint64_t seed, 
 }
 
 // ---------------------------------------------------------------- inference
-// Persistent: each CTA keeps W2, W3 in shared memory and runs tiles of 128
-// (element, pixel) pairs.  Writes the exit angle (phi) and the predicted lens
-// time for every pair whose fallback bit is clear (all pairs if fb is NULL).
-__global__ void __launch_bounds__(128) mlp_infer_kernel(AfGeom g, MlpNorm n, const float *__restrict__ P,
-                                                        const __nv_bfloat16 *__restrict__ W2b,
-                                                        const __nv_bfloat16 *__restrict__ W3b,
-                                                        const float2 *__restrict__ elem_pol,
-                                                        const float2 *__restrict__ pix_pol,
-                                                        const AfScal *__restrict__ scal, float c_fixed,
-                                                        const uint8_t *__restrict__ fb,
-                                                        float *__restrict__ phi_out, float *__restrict__ tl_out,
-                                                        int *__restrict__ err)
+// Persistent: each CTA keeps W2, W3 in shared memory (and the small parameters
+// W1, b1..b4, W4) and runs tiles of 128 (element, pixel) pairs.  256 threads:
+// warp w reads tensor-memory lanes 32 (w mod 4).. (its rows) and handles hidden
+// columns 64 (w / 4)..+63 of them, so two warps share a row's epilogue; two CTAs
+// per SM let one CTA's epilogue overlap the other's MMA.  Writes the exit angle
+// (phi) and the predicted lens time for every pair whose fallback bit is clear
+// (all pairs if fb is NULL).
+constexpr int kInferThreads = 256;
+constexpr int kHalf = HID / 2;
+
+__global__ void __launch_bounds__(kInferThreads) mlp_infer_kernel(AfGeom g, MlpNorm n, const float *__restrict__ P,
+                                                                  const __nv_bfloat16 *__restrict__ W2b,
+                                                                  const __nv_bfloat16 *__restrict__ W3b,
+                                                                  const float2 *__restrict__ elem_pol,
+                                                                  const float2 *__restrict__ pix_pol,
+                                                                  const AfScal *__restrict__ scal, float c_fixed,
+                                                                  const uint8_t *__restrict__ fb,
+                                                                  float *__restrict__ phi_out,
+                                                                  float *__restrict__ tl_out, int *__restrict__ err)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sW2 = smem, *sW3 = smem + TB, *sH = smem + 2 * TB;
+    __shared__ __align__(16) float sW1[HID * 4], sB1[HID], sB2[HID], sB3[HID], sW4[2 * HID];
+    __shared__ float2 sY[TILE];                 // the second half's partial outputs
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
-    const int b = threadIdx.x, warp = b >> 5, lane = b & 31, row = 32 * warp + lane;
-    if (warp == 0) tc::tmem_alloc(&tslot, HID);
+    const int b = threadIdx.x, warp = b >> 5, lane = b & 31;
+    const int quad = warp & 3, half = warp >> 2, row = 32 * quad + lane, c0 = half * kHalf;
+    if (warp == 0) {
+        tc::tmem_alloc(&tslot, HID);
+        tc::tmem_relinquish();       // no further allocation: let the SM's other CTA allocate
+    }
     if (b == 0) { tc::mbar_init(&mbar, 1); tc::fence_mbar_init(); }
     stage_weight(sW2, W2b);
     stage_weight(sW3, W3b);
+    for (int k = b; k < HID * 4; k += kInferThreads) sW1[k] = P[OFF_W1 + k];
+    for (int k = b; k < HID; k += kInferThreads) {
+        sB1[k] = P[OFF_B1 + k];
+        sB2[k] = P[OFF_B2 + k];
+        sB3[k] = P[OFF_B3 + k];
+    }
+    for (int k = b; k < 2 * HID; k += kInferThreads) sW4[k] = P[OFF_W4 + k];
+    const float b40 = P[OFF_B4], b41 = P[OFF_B4 + 1];
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tslot;
+    const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
     const float c = c_fixed > 0.f ? c_fixed : 1.0f / scal->sbar;
     uint32_t phase = 0;
     bool ok = true;
     const long total = (long)g.ne * g.npix;
     const long ntiles = (total + TILE - 1) / TILE;
     for (long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const long idx = t * TILE + b;
+        const long idx = t * TILE + row;
         const bool live = idx < total;
         const int e = live ? (int)(idx / g.npix) : 0, p = live ? (int)(idx - (long)e * g.npix) : 0;
         const float2 ep = elem_pol[e], pp = pix_pol[p];
         float x[4];
         features(n, ep.x, pp.y, pp.x, c, x);
-        for (int cc = 0; cc < HID; cc += 32) {
+        // layer 1 (4 -> 128, FP32): this thread's 64 columns of its row
+#pragma unroll
+        for (int cc = 0; cc < kHalf; cc += 32) {
             float v[32];
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
-                const float *w = P + OFF_W1 + (cc + k) * 4;
-                v[k] = tanh_fast(fmaf(w[0], x[0], fmaf(w[1], x[1], fmaf(w[2], x[2], fmaf(w[3], x[3], P[OFF_B1 + cc + k])))));
+                const float4 w = *reinterpret_cast<const float4 *>(sW1 + (c0 + cc + k) * 4);
+                v[k] = tanh_fast(fmaf(w.x, x[0], fmaf(w.y, x[1], fmaf(w.z, x[2], fmaf(w.w, x[3], sB1[c0 + cc + k])))));
             }
-            store_row32(sH, b, cc, v);
+            store_row32(sH, row, c0 + cc, v);
         }
         ok = run_mma(tmem, sH, 0, sW2, 0, &mbar, phase) && ok;
         __syncthreads();                                   // the MMA has consumed H1
-        for (int cc = 0; cc < HID; cc += 32) {
-            float v[32];
-            row_chunk(tmem, cc, v);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) v[k] = tanh_fast(v[k] + P[OFF_B2 + cc + k]);
-            store_row32(sH, row, cc, v);
+        for (int cc = 0; cc < kHalf; cc += 32) {
+            float v[32];
+            tc::tmem_ld32(trow + c0 + cc, v);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) v[k] = tanh_fast(v[k] + sB2[c0 + cc + k]);
+            store_row32(sH, row, c0 + cc, v);
         }
         ok = run_mma(tmem, sH, 0, sW3, 0, &mbar, phase) && ok;
-        float y0 = P[OFF_B4], y1 = P[OFF_B4 + 1];
-        for (int cc = 0; cc < HID; cc += 32) {
+        float y0 = 0.0f, y1 = 0.0f;
+#pragma unroll
+        for (int cc = 0; cc < kHalf; cc += 32) {
             float v[32];
-            row_chunk(tmem, cc, v);
+            tc::tmem_ld32(trow + c0 + cc, v);
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
-                const float h = __bfloat162float(__float2bfloat16_rn(tanh_fast(v[k] + P[OFF_B3 + cc + k])));
-                y0 = fmaf(P[OFF_W4 + cc + k], h, y0);
-                y1 = fmaf(P[OFF_W4 + HID + cc + k], h, y1);
+                const float h = round_bf16(tanh_fast(v[k] + sB3[c0 + cc + k]));
+                y0 = fmaf(sW4[c0 + cc + k], h, y0);
+                y1 = fmaf(sW4[HID + c0 + cc + k], h, y1);
             }
         }
-        if (live && (!fb || !fb[idx])) {
-            phi_out[idx] = ep.x + y0 * n.y0_s;
-            if (tl_out) tl_out[idx] = n.y1_c + y1 * n.y1_s;
+        if (half == 1) sY[row] = make_float2(y0, y1);
+        __syncthreads();                                   // sY ready; sH free for the next tile
+        if (half == 0 && live && (!fb || !fb[idx])) {
+            const float2 q = sY[row];
+            phi_out[idx] = ep.x + (b40 + y0 + q.x) * n.y0_s;
+            if (tl_out) tl_out[idx] = n.y1_c + (b41 + y1 + q.y) * n.y1_s;
         }
-        __syncthreads();                                   // sH is rewritten by the next tile
     }
     if (!ok && b == 0) atomicExch(err, 1);
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) {
-        tc::tmem_dealloc(tmem, HID);
-        tc::tmem_relinquish();
-    }
+    if (warp == 0) tc::tmem_dealloc(tmem, HID);
 }
 
 // Validation at one medium speed: delay error of the surrogate's exit angle
@@ -513,6 +547,10 @@ cudaError_t mlp_setup_attributes()
     cudaError_t e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrainSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kInferSmem);
+    // the largest shared-memory carveout, so that two inference CTAs fit on an SM
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
     return e;
 }
 
@@ -566,7 +604,7 @@ cudaError_t mlp_train_step(af_plan_t pl, const float4 *X, const float2 *Y, long 
 cudaError_t mlp_infer(af_plan_t pl, float c_fixed, const uint8_t *fb, float *phi_out, float *tl_out)
 {
     if ((long)pl->g.ne * pl->g.npix == 0) return cudaSuccess;
-    mlp_infer_kernel<<<pl->sm_count * 2, 128, kInferSmem, pl->stream>>>(
+    mlp_infer_kernel<<<pl->sm_count * 2, kInferThreads, kInferSmem, pl->stream>>>(
         pl->g, pl->mlp_norm, pl->mlp_p, reinterpret_cast<const __nv_bfloat16 *>(pl->mlp_w2b),
         reinterpret_cast<const __nv_bfloat16 *>(pl->mlp_w3b), pl->elem_pol, pl->pix_pol, pl->scal, c_fixed, fb,
         phi_out, tl_out, &pl->scal->mlp_err);
