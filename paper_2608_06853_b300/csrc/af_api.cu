@@ -236,7 +236,7 @@ af_status af_destroy(af_plan_t pl)
     for (int k = 0; k < 2 * kTimingCap; ++k)
         if (pl->ev[k]) cudaEventDestroy(pl->ev[k]);
     void *ptrs[] = {pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->D, pl->B, pl->G, pl->z,
-                    pl->mask, pl->patch_sum, pl->patch_cnt, pl->gdel, pl->gpart, pl->gpad, pl->scal,
+                    pl->mask, pl->patch_sum, pl->patch_cnt, pl->gdel, pl->gpart, pl->gpad, pl->scal, pl->stat_part,
                     pl->mlp_p, pl->mlp_m, pl->mlp_v, pl->mlp_g, pl->mlp_w2b, pl->mlp_w3b, pl->sur_fb};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -425,6 +425,7 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
     AF_ALLOC(pl->patch_sum, g.n_patch * sizeof(double));
     AF_ALLOC(pl->patch_cnt, g.n_patch * sizeof(int));
     AF_ALLOC(pl->scal, sizeof(AfScal));
+    AF_ALLOC(pl->stat_part, kStatBlocks * sizeof(double4));
     pl->smem_grid = padded_grid_bytes(c);
     pl->delay = delays_shape(pl->smem_grid, pl->sm_count);
     pl->rayadj = rayadj_shape(c->nx, c->nz, g.pitch, pl->sm_count);

@@ -131,55 +131,52 @@ __device__ __forceinline__ float arg_sign(float2 z)
 // G[b][p] = dL_CMPE/dB_b(p): an image is the first member of at most one pair
 // ((i,j) ~ (i+1,j-1)) and the second member of at most one ((i-1,j+1) ~ (i,j)).
 //   first:  w j z B2 / |z|^2     second: -w j conj(z) B1 / |z|^2,  w = sgn(arg z) / max(1, M)
+// Grid: (pixel blocks, image b); the image's two pairs are the same for the block.
 __global__ void __launch_bounds__(256) cmpe_backward_kernel(AfGeom g, const float2 *__restrict__ B,
                                                             const float2 *__restrict__ z,
                                                             const uint8_t *__restrict__ mask,
                                                             AfScal *scal,
                                                             float2 *__restrict__ G)
 {
-    const long total = (long)g.nb * g.npix;
+    const int n = g.nsub, b = blockIdx.y, i = b / n, j = b - i * n;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && b == 0 && threadIdx.x == 0) scal->gmax_bits = 0;   // read by the ray adjoint
+    if (p >= g.npix) return;
     const float inv_m = scal->inv_m;
-    const int n = g.nsub;
-    if (blockIdx.x == 0 && threadIdx.x == 0) scal->gmax_bits = 0;   // read by the ray adjoint
-    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long)gridDim.x * blockDim.x) {
-        const int b = (int)(idx / g.npix), p = (int)(idx - (long)b * g.npix);
-        const int i = b / n, j = b - i * n, P = p / g.patch_npix;
-        float gr = 0.0f, gi = 0.0f;
-        int k = pair_index(i, j, n);
-        if (k >= 0) {
-            const long o = (long)P * g.npair + k;
-            if (mask[o]) {
-                const float2 zz = z[o];
-                const float mag2 = zz.x * zz.x + zz.y * zz.y;
-                const float sg = arg_sign(zz);
-                if (sg != 0.0f && mag2 > 0.0f) {
-                    const float w = sg * inv_m / mag2;
-                    const float2 c = B[(long)((i + 1) * n + (j - 1)) * g.npix + p];
-                    const float tr = zz.x * c.x - zz.y * c.y, ti = zz.x * c.y + zz.y * c.x;
-                    gr += -w * ti;
-                    gi += w * tr;
-                }
+    const int P = p / g.patch_npix;
+    const int k1 = pair_index(i, j, n), k2 = pair_index(i - 1, j + 1, n);
+    float gr = 0.0f, gi = 0.0f;
+    if (k1 >= 0) {
+        const long o = (long)P * g.npair + k1;
+        if (mask[o]) {
+            const float2 zz = z[o];
+            const float mag2 = zz.x * zz.x + zz.y * zz.y;
+            const float sg = arg_sign(zz);
+            if (sg != 0.0f && mag2 > 0.0f) {
+                const float w = sg * inv_m / mag2;
+                const float2 c = B[(long)((i + 1) * n + (j - 1)) * g.npix + p];
+                const float tr = zz.x * c.x - zz.y * c.y, ti = zz.x * c.y + zz.y * c.x;
+                gr += -w * ti;
+                gi += w * tr;
             }
         }
-        k = pair_index(i - 1, j + 1, n);
-        if (k >= 0) {
-            const long o = (long)P * g.npair + k;
-            if (mask[o]) {
-                const float2 zz = z[o];
-                const float mag2 = zz.x * zz.x + zz.y * zz.y;
-                const float sg = arg_sign(zz);
-                if (sg != 0.0f && mag2 > 0.0f) {
-                    const float w = sg * inv_m / mag2;
-                    const float2 a = B[(long)((i - 1) * n + (j + 1)) * g.npix + p];
-                    const float ur = zz.x * a.x + zz.y * a.y, ui = zz.x * a.y - zz.y * a.x;
-                    gr += w * ui;
-                    gi += -w * ur;
-                }
-            }
-        }
-        G[idx] = make_float2(gr, gi);
     }
+    if (k2 >= 0) {
+        const long o = (long)P * g.npair + k2;
+        if (mask[o]) {
+            const float2 zz = z[o];
+            const float mag2 = zz.x * zz.x + zz.y * zz.y;
+            const float sg = arg_sign(zz);
+            if (sg != 0.0f && mag2 > 0.0f) {
+                const float w = sg * inv_m / mag2;
+                const float2 a = B[(long)((i - 1) * n + (j + 1)) * g.npix + p];
+                const float ur = zz.x * a.x + zz.y * a.y, ui = zz.x * a.y - zz.y * a.x;
+                gr += w * ui;
+                gi += -w * ur;
+            }
+        }
+    }
+    G[(long)b * g.npix + p] = make_float2(gr, gi);
 }
 
 // Full-aperture image |sum_ij B_ij(p)| (Figs. 2, 4) and the integrated CMPE
@@ -239,13 +236,12 @@ cudaError_t launch_cmpe_backward(af_plan_t pl)
 {
     const long total = (long)pl->g.nb * pl->g.npix;
     if (total == 0) return cudaSuccess;
-    long blocks = (total + 255) / 256;
-    if (blocks > 65535L * 8) blocks = 65535L * 8;
     if (pl->g.npair == 0) {
         cudaError_t e = cudaMemsetAsync(pl->G, 0, total * sizeof(float2), pl->stream);
         if (e != cudaSuccess) return e;
         return cudaMemsetAsync(&pl->scal->gmax_bits, 0, sizeof(int), pl->stream);
     }
-    cmpe_backward_kernel<<<(int)blocks, 256, 0, pl->stream>>>(pl->g, pl->B, pl->z, pl->mask, pl->scal, pl->G);
+    const dim3 blocks((pl->g.npix + 255) / 256, pl->g.nb);
+    cmpe_backward_kernel<<<blocks, 256, 0, pl->stream>>>(pl->g, pl->B, pl->z, pl->mask, pl->scal, pl->G);
     return cudaGetLastError();
 }

@@ -11,17 +11,19 @@ namespace {
 // deadzone D_k(x) = max(0, |x| - k)  (Sec. II-D)
 __device__ __forceinline__ float deadzone(float x, float k) { return fmaxf(fabsf(x) - k, 0.0f); }
 
-// One CTA: c_med = mean(1/s) in double, the two regularisers of Eq. 10-11 on
-// c = 1/s, and the numeric check of the slowness map.
-__global__ void __launch_bounds__(1024) grid_stats_kernel(AfGeom g, const float *__restrict__ s,
-                                                          AfScal *scal)
+// c_med = mean(1/s) (Sec. III-A), the two regularisers of Eq. 10-11 on c = 1/s,
+// and the numeric check of the slowness map, in two steps: kStatBlocks CTAs
+// write partial sums {sum 1/s, sum of the Eq. 10 terms, sum of the Eq. 11 terms,
+// bad-value flag}, and one CTA adds them in a fixed order.
+__global__ void __launch_bounds__(256) grid_stats_partial_kernel(AfGeom g, const float *__restrict__ s,
+                                                                 double4 *__restrict__ part)
 {
-    __shared__ double red[3][32];
+    __shared__ double red[3][8];
     // per-thread partial sums in float (float64 throughput is low on this GPU); the
     // sum of 1/s, which sets c_med and with it every delay, is compensated (Kahan)
     float pc = 0.0f, pc_comp = 0.0f, pa = 0.0f, pb = 0.0f;
     int bad = 0;
-    for (int k = threadIdx.x; k < g.ng; k += blockDim.x) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.ng; k += gridDim.x * blockDim.x) {
         int j = k / g.nx, i = k - j * g.nx;
         float sv = s[k];
         if (!(sv > 0.0f) || !isfinite(sv)) bad = 1;
@@ -43,29 +45,34 @@ __global__ void __launch_bounds__(1024) grid_stats_kernel(AfGeom g, const float 
         acc_b += __shfl_xor_sync(0xffffffffu, acc_b, o);
     }
     bad = __syncthreads_or(bad);
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) { red[0][w] = acc_c; red[1][w] = acc_a; red[2][w] = acc_b; }
     __syncthreads();
-    if (w == 0) {
-        int nw = blockDim.x >> 5;
-        acc_c = l < nw ? red[0][l] : 0.0;
-        acc_a = l < nw ? red[1][l] : 0.0;
-        acc_b = l < nw ? red[2][l] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) {
-            acc_c += __shfl_xor_sync(0xffffffffu, acc_c, o);
-            acc_a += __shfl_xor_sync(0xffffffffu, acc_a, o);
-            acc_b += __shfl_xor_sync(0xffffffffu, acc_b, o);
-        }
-        if (l == 0) {
-            double cmed = acc_c / g.ng;
-            scal->sbar = (float)(1.0 / cmed);
-            scal->rtv = (float)(acc_a * g.na_inv);
-            scal->rsv = (float)(acc_b * g.nb_inv);
-            scal->fp64_solves = 0;
-            scal->n_apod = 0;
-            if (bad) scal->numeric_flag = 1;
-        }
+    if (threadIdx.x == 0) {
+        double c = 0.0, a = 0.0, b = 0.0;
+        for (int k = 0; k < 8; ++k) { c += red[0][k]; a += red[1][k]; b += red[2][k]; }
+        part[blockIdx.x] = make_double4(c, a, b, bad ? 1.0 : 0.0);
     }
+}
+
+__global__ void grid_stats_final_kernel(AfGeom g, const double4 *__restrict__ part, int nparts, AfScal *scal)
+{
+    if (threadIdx.x != 0) return;
+    double c = 0.0, a = 0.0, b = 0.0, bad = 0.0;
+    for (int k = 0; k < nparts; ++k) {
+        const double4 v = part[k];
+        c += v.x;
+        a += v.y;
+        b += v.z;
+        bad += v.w;
+    }
+    const double cmed = c / g.ng;
+    scal->sbar = (float)(1.0 / cmed);
+    scal->rtv = (float)(a * g.na_inv);
+    scal->rsv = (float)(b * g.nb_inv);
+    scal->fp64_solves = 0;
+    scal->n_apod = 0;
+    if (bad > 0.0) scal->numeric_flag = 1;
 }
 
 // Padded grid in shared memory: scalar v[jj][ii], or (PAIRS) the node pairs
@@ -320,7 +327,10 @@ DelayShape delays_shape(size_t smem_scalar, int sm_count)
 
 cudaError_t launch_grid_stats(af_plan_t pl, const float *s)
 {
-    grid_stats_kernel<<<1, 1024, 0, pl->stream>>>(pl->g, s, pl->scal);
+    grid_stats_partial_kernel<<<kStatBlocks, 256, 0, pl->stream>>>(pl->g, s, pl->stat_part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    grid_stats_final_kernel<<<1, 32, 0, pl->stream>>>(pl->g, pl->stat_part, kStatBlocks, pl->scal);
     return cudaGetLastError();
 }
 

@@ -35,6 +35,7 @@ struct AfGeom {
     float c_ref, lr, beta1, beta2, omb1, omb2, eps;   // omb = 1 - beta, formed in double
 };
 
+constexpr int kStatBlocks = 64;     // CTAs of the grid-statistics partial sums
 constexpr int kTimingCap = 4096;   // recorded stage launches per timing window
 constexpr size_t kMaxGridSmemBytes = 200 * 1024;   // largest padded slowness grid held in shared memory
 
@@ -112,6 +113,7 @@ struct af_plan_s {
     long long *gpart;    // [rayadj.blocks][ng] per-CTA partial gradients (fixed point)
     long long *gpad;     // [rayadj.blocks][padded grid] per-CTA fixed-point accumulators
     AfScal *scal;
+    double4 *stat_part;  // [kStatBlocks] partial sums of the grid statistics
     float *loss_out;     // last caller loss buffer
     const void *iq;      // last forward's inputs (kept for the adjoint)
     const float *iq_scale;

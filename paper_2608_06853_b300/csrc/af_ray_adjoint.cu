@@ -315,6 +315,7 @@ __global__ void __launch_bounds__(256) reduce_grad_kernel(AfGeom g, const float 
     if (k == 0) scal->ray_next = 0;
     if (k >= g.ng) return;
     long long tot = 0;
+#pragma unroll 8
     for (int c = 0; c < nparts; ++c) tot += gpart[(long)c * g.ng + k];
     const float gmax = __int_as_float(scal->gmax_bits);
     const float acc = gmax > 0.0f ? (float)((double)tot * ((double)gmax / (double)g.fix_scale)) : 0.0f;
