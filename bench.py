@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-jobs", type=int, default=2)
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--variants", default="bf16,f16,surrogate,batch,sweep",
+                    help="comma list of the variant runs: bf16, f16, surrogate (on the bf16 plan), "
+                         "batch, sweep (sweep, images and metrics)")
     ap.add_argument("--surrogate-samples", type=int, default=10_000_000)
     ap.add_argument("--batch-size", type=int, default=16)
     return ap.parse_args()
@@ -175,6 +178,11 @@ NCU_TRAFFIC = {"das_forward": 743.3e6 + 65.6e6, "das_adjoint": 293.2e6 + 18.4e6,
 # forward; the adjoint adds the slope terms (2), the weight conj(G) P_t P_r (4), the
 # real part (2) and the two accumulations (2) = 23.
 OPS_PER_POINT = {"delays": 50, "ray_adjoint": 46}
+
+# library kernels launched by one call of each timed stage (the DAS adjoint stage also
+# issues one memset of dL/dT, which is not a kernel of ours)
+KERNELS_PER_STAGE = {"grid_stats": 2, "delays": 1, "das_forward": 1, "cmpe_forward": 2, "cmpe_adjoint": 1,
+                     "das_adjoint": 2, "ray_adjoint": 2, "adam": 1, "surrogate": 1}
 OPS_PER_GATHER = {"das_forward": 13, "das_adjoint": 23}
 
 
@@ -267,10 +275,16 @@ def run_variants(args, p, psi, plan32, iq32, stream, dev, ms32):
     r = torch.view_as_real(iq32)
     scale = r.abs().amax(dim=(1, 2, 3)).clamp_min(1e-30).float().contiguous()
     plans = {}
+    want = set(args.variants.split(","))
     for name, dt, tdt in (("bf16", af.AF_IQ_BF16, torch.bfloat16), ("f16", af.AF_IQ_F16, torch.float16)):
+        if name not in want and not (name == "bf16" and "surrogate" in want):
+            continue
         with torch.cuda.stream(stream):
             q = (r / scale[:, None, None, None]).to(tdt).contiguous()
         pl = af.Plan(p, iq_dtype=dt, stream=stream)
+        plans[name] = (pl, q)
+        if name not in want:
+            continue
         ms, stages, _ = _time_iterations(pl, q, scale, p, stream, dev, args.steps, args.warmup)
         with torch.cuda.stream(stream):
             loss = torch.zeros(4, device=dev)
@@ -284,9 +298,22 @@ def run_variants(args, p, psi, plan32, iq32, stream, dev, ms32):
                      "loss_rel_vs_fp32": float(abs(loss[0] - ref_loss[0]) / abs(ref_loss[0])),
                      "grad_rel_l2_vs_fp32": float((g - g32).norm() / g32.norm()),
                      "stage_ms": stages}
-        plans[name] = (pl, q)
-    # lens surrogate + bf16: train on the tensor cores, validate, enable
-    pl, q = plans["bf16"]
+    if "surrogate" in want:
+        out["surrogate_bf16"] = run_surrogate(args, p, plans["bf16"], scale, s0, a32, T32, stream, dev)
+    if "batch" in want:
+        out["batch"] = run_batch(args, dev)
+    if "sweep" in want:
+        out["sweep_and_images"] = run_sweep_images(p, iq32, plan32, stream, dev)
+    return out
+
+
+def run_surrogate(args, p, plan_q, scale, s0, a32, T32, stream, dev):
+    """Lens surrogate + bf16 storage: train on the tensor cores, validate, enable, time."""
+    import torch
+    pl, q = plan_q
+    with torch.cuda.stream(stream):                 # validation uses the apodization of a forward
+        pl.af_forward(q, s0, torch.zeros(4, device=dev), scale)
+    stream.synchronize()
     t0 = time.perf_counter()
     rep = pl.surrogate_train(n_samples=args.surrogate_samples, epochs=4, tiles_per_step=32, lr=2e-3, seed=3)
     t_train = time.perf_counter() - t0
@@ -299,16 +326,13 @@ def run_variants(args, p, psi, plan32, iq32, stream, dev, ms32):
     stream.synchronize()
     on = a32 == 1
     derr = float((Ts - T32).abs()[on].max())
-    out["surrogate_bf16"] = {"iterations_per_s": 1e3 / ms, "ms_per_iteration": ms, "stage_ms": stages,
-                             "max_delay_err_s": derr, "tolerance_s": rep["tolerance"],
-                             "fallback_fraction": rep["fallback_fraction"],
-                             "rms_exit_angle_err_rad": rep["rms_angle_err"],
-                             "train_samples": int(rep["samples"]), "train_steps": int(rep["steps"]),
-                             "train_seconds": t_train, "train_loss": rep["train_loss"]}
     pl.surrogate_enable(False)
-    out["batch"] = run_batch(args, dev)
-    out["sweep_and_images"] = run_sweep_images(p, iq32, plan32, stream, dev)
-    return out
+    return {"iterations_per_s": 1e3 / ms, "ms_per_iteration": ms, "stage_ms": stages,
+            "max_delay_err_s": derr, "tolerance_s": rep["tolerance"],
+            "fallback_fraction": rep["fallback_fraction"],
+            "rms_exit_angle_err_rad": rep["rms_angle_err"],
+            "train_samples": int(rep["samples"]), "train_steps": int(rep["steps"]),
+            "train_seconds": t_train, "train_loss": rep["train_loss"]}
 
 
 def run_sweep_images(p, iq32, plan32, stream, dev):
@@ -536,8 +560,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD, "iq_dtype": args.dtype, "scatterers": args.scatterers,
                    "l2": "inputs larger than L2 (384 MiB channel data), no flush",
                    "parallelism": f"independent acquisitions x{world}"},
-        "gpu_launches": sum(v_[1] for v_ in stages.values()) + stages["ray_adjoint"][1]
-                        + stages["cmpe_forward"][1],
+        "gpu_launches": sum(v_[1] * KERNELS_PER_STAGE[k] for k, v_ in stages.items()),
         "stage_ms": {k: v_[0] / max(v_[1], 1) for k, v_ in stages.items()},
         "hbm_gbs_algorithmic": it_bytes / (ms_max / args.steps * 1e-3) / 1e9,
         "roofline": roof,

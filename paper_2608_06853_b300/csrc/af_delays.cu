@@ -55,17 +55,25 @@ __global__ void __launch_bounds__(256) grid_stats_partial_kernel(AfGeom g, const
     }
 }
 
-__global__ void grid_stats_final_kernel(AfGeom g, const double4 *__restrict__ part, int nparts, AfScal *scal)
+// one warp: lane l adds partials l, l + 32, ..., then a fixed xor tree
+__global__ void __launch_bounds__(32) grid_stats_final_kernel(AfGeom g, const double4 *__restrict__ part,
+                                                              int nparts, AfScal *scal)
 {
-    if (threadIdx.x != 0) return;
     double c = 0.0, a = 0.0, b = 0.0, bad = 0.0;
-    for (int k = 0; k < nparts; ++k) {
+    for (int k = threadIdx.x; k < nparts; k += 32) {
         const double4 v = part[k];
         c += v.x;
         a += v.y;
         b += v.z;
         bad += v.w;
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if (threadIdx.x != 0) return;
     const double cmed = c / g.ng;
     scal->sbar = (float)(1.0 / cmed);
     scal->rtv = (float)(a * g.na_inv);
