@@ -429,6 +429,7 @@ def run_batch(args, dev, n_iter=100, n_scat=20_000):
         ms = e0.elapsed_time(e1)
         res[name] = {"iterations_per_s": len(probs) * n_iter / (ms * 1e-3), "job_ms": ms,
                      "numeric_ok": all(pl.af_sync_status() == af.AF_OK for pl in br.plans)}
+    br.close()
     return res
 
 

@@ -46,7 +46,7 @@ typedef enum {
     AF_ERR_DTYPE = 3,        /* unknown iq_dtype, or a scale array missing for a 16-bit dtype */
     AF_ERR_CUDA = 4,         /* a CUDA runtime call failed (message names it) */
     AF_ERR_NUMERIC = 5,      /* non-positive or non-finite slowness seen on the device */
-    AF_ERR_TIMEOUT = 6,      /* reserved for bounded device waits */
+    AF_ERR_TIMEOUT = 6,      /* a bounded device wait (tensor-core completion) ran out */
     AF_ERR_UNSUPPORTED = 7,  /* valid but outside what this build implements */
     AF_ERR_STATE = 8         /* call order violated (e.g. af_adjoint before af_forward) */
 } af_status;
@@ -126,7 +126,8 @@ af_status af_workspace_bytes(const af_config *cfg, size_t *bytes);
  * allocate the plan's workspaces.  stream: a cudaStream_t (or NULL). */
 af_status af_plan(const af_config *cfg, void *stream, af_plan_t *out);
 
-/* Forward pass (spec steps a-e): loss of Eq. 12 at slowness d_slowness.
+/* Forward pass (Eq. 1-8, Eq. 10-12 and the CMPE of Sec. II-D): loss of Eq. 12
+ * at slowness d_slowness.
  *  d_iq        Psi, [n_elem][n_elem][n_samp] complex, layout per iq_dtype.
  *              Must stay valid and unchanged until the matching af_adjoint.
  *  d_iq_scale  [n_elem] float per-transmit scale for 16-bit dtypes, else NULL.
@@ -151,6 +152,34 @@ af_status af_iterate(af_plan_t plan, const void *d_iq, const float *d_iq_scale,
 
 /* Release the plan's device memory.  NULL is accepted. */
 af_status af_destroy(af_plan_t plan);
+
+/* ---- batches of independent acquisitions (one job, one graph launch) ----
+ * A batch owns one plan per configuration, each on a non-blocking stream of its
+ * own, so the members run concurrently.  `stream` is the caller's stream: the
+ * batch calls fork from it and join back to it (stream order is kept; it may be
+ * the legacy default stream).  Errors as af_plan; on failure nothing is kept. */
+typedef struct af_batch_s *af_batch_t;
+af_status af_batch_plan(int n, const af_config *const *cfgs, void *stream, af_batch_t *out);
+/* Member k's plan (owned by the batch) for the per-plan getters and settings. */
+af_status af_batch_plan_of(af_batch_t batch, int k, af_plan_t *out);
+/* One af_iterate of every member.  Each argument is a host array of n device
+ * pointers, member k's buffers as in af_iterate; d_iq_scale may be NULL when no
+ * member has 16-bit data.  Asynchronous; no allocation. */
+af_status af_batch_iterate(af_batch_t batch, const void *const *d_iq, const float *const *d_iq_scale,
+                           float *const *d_s, float *const *d_grad, float *const *d_m,
+                           float *const *d_v, int step, float *const *d_loss);
+/* Record n_iter iterations of every member (Adam steps first_step ..
+ * first_step + n_iter - 1) into one CUDA graph by stream capture; nothing runs.
+ * The graph keeps the device pointers: keep the buffers for its launches.
+ * AF_ERR_STATE if a member's stage timing is on.  Replaces a previous graph. */
+af_status af_batch_capture(af_batch_t batch, const void *const *d_iq, const float *const *d_iq_scale,
+                           float *const *d_s, float *const *d_grad, float *const *d_m,
+                           float *const *d_v, float *const *d_loss, int first_step, int n_iter);
+/* Launch the captured graph, ordered after the caller stream's earlier work and
+ * before its later work.  AF_ERR_STATE if nothing was captured. */
+af_status af_batch_launch(af_batch_t batch);
+/* Release the batch, its plans, streams and graph.  NULL is accepted. */
+af_status af_batch_destroy(af_batch_t batch);
 
 /* Move the image points of a plan (same n_patch x patch_npix, host arrays, read
  * during the call).  Used by the global-speed sweep of Sec. II-C / III-A, whose
@@ -316,8 +345,8 @@ af_status af_surrogate_grad(af_plan_t plan, const float *d_X, const float *d_Y, 
  * [K][M] (1); B is bf16 [N][K] (b_mn_major = 0) or [K][N] (1); D is [M][N].
  * M, N multiples of 128, K a multiple of 64, operands 16-byte aligned.
  * *d_err (device int, caller-zeroed) is set to 1 if an MMA completion wait
- * timed out.  No counterpart in the paper (the MLP surrogate is the north
- * star's learned lens-time model). */
+ * timed out.  No counterpart in the paper: it is the building block of the
+ * learned lens-time model (the MLP surrogate below). */
 af_status af_gemm_bf16(const void *d_A, const void *d_B, float *d_D, int M, int N, int K,
                        int a_mn_major, int b_mn_major, int *d_err, void *stream);
 

@@ -65,14 +65,17 @@ ProblemFields = ("elem_x", "elem_z", "lens_mode", "arc_cx", "arc_cz", "lens_radi
 
 _lib = None
 
-# name -> (restype, argtypes) of every exported entry point of include/af.h
 _VP = ctypes.c_void_p
+_PA = ctypes.POINTER(ctypes.c_void_p)   # host array of device pointers
+
+
 class AfMetrics(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("cf_mean", "loc", "cmcc", "contrast_db", "cnr", "gcnr",
                                                 "mean_in", "mean_out")] + \
                [("n_in", ctypes.c_longlong), ("n_out", ctypes.c_longlong)]
 
 
+# name -> (restype, argtypes) of every exported entry point of include/af.h
 _SIGNATURES = {
     "af_check_config": (ctypes.c_int, [ctypes.POINTER(AfConfig)]),
     "af_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(AfConfig), ctypes.POINTER(ctypes.c_size_t)]),
@@ -82,6 +85,13 @@ _SIGNATURES = {
     "af_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int]),
     "af_iterate": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
     "af_destroy": (ctypes.c_int, [_VP]),
+    "af_batch_plan": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.POINTER(AfConfig)), _VP,
+                                      ctypes.POINTER(_VP)]),
+    "af_batch_plan_of": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(_VP)]),
+    "af_batch_iterate": (ctypes.c_int, [_VP, _PA, _PA, _PA, _PA, _PA, _PA, ctypes.c_int, _PA]),
+    "af_batch_capture": (ctypes.c_int, [_VP, _PA, _PA, _PA, _PA, _PA, _PA, _PA, ctypes.c_int, ctypes.c_int]),
+    "af_batch_launch": (ctypes.c_int, [_VP]),
+    "af_batch_destroy": (ctypes.c_int, [_VP]),
     "af_sync_status": (ctypes.c_int, [_VP]),
     "af_set_pixels": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "af_get_delays": (ctypes.c_int, [_VP, _VP, _VP]),
@@ -233,6 +243,15 @@ class Plan:
 
     def __init__(self, problem, iq_dtype: int = AF_IQ_C64, stream=None):
         import torch
+        self._describe(problem, iq_dtype, stream if stream is not None else torch.cuda.current_stream())
+        cfg, keep = make_config(problem, iq_dtype)
+        h = ctypes.c_void_p()
+        _check(self.lib.af_plan(ctypes.byref(cfg), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
+               "af_plan")
+        self.handle = h
+        self._owner = None
+
+    def _describe(self, problem, iq_dtype, stream):
         self.lib = load()
         self.problem = problem
         self.iq_dtype = iq_dtype
@@ -241,16 +260,24 @@ class Plan:
         self.nsub = self.ne // int(problem.sub_width)
         self.npair = (self.nsub - 1) * (self.nsub - 2) if self.nsub >= 3 else 0
         self.nx, self.nz = int(problem.nx), int(problem.nz)
-        self.stream = stream if stream is not None else torch.cuda.current_stream()
-        cfg, keep = make_config(problem, iq_dtype)
+        self.stream = stream
+
+    @classmethod
+    def batch_member(cls, batch, k: int, problem, iq_dtype: int, stream):
+        """Member k of an af_batch_t (af_batch_plan_of): the batch owns the plan,
+        this object keeps the batch alive and never destroys the plan."""
+        self = cls.__new__(cls)
+        self._describe(problem, iq_dtype, stream)
         h = ctypes.c_void_p()
-        _check(self.lib.af_plan(ctypes.byref(cfg), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
-               "af_plan")
+        _check(self.lib.af_batch_plan_of(batch.handle, int(k), ctypes.byref(h)), "af_batch_plan_of")
         self.handle = h
+        self._owner = batch
+        return self
 
     def close(self):
         if getattr(self, "handle", None):
-            self.lib.af_destroy(self.handle)
+            if getattr(self, "_owner", None) is None:
+                self.lib.af_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

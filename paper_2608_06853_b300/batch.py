@@ -1,78 +1,99 @@
 """Batched autofocus of independent acquisitions as one CUDA graph.
 
-Each acquisition has its own plan (af_plan) and stream.  `BatchRunner.capture`
-records `iterations` calls of af_iterate for every acquisition, each on its
-own stream forked from and joined back to a capture stream, into one CUDA
-graph; `replay()` then runs the whole job (all acquisitions, all iterations)
-with a single graph launch.  The af_* calls of an iteration allocate nothing
-and never synchronise, so they are capturable; the Adam step index is a
-launch argument and is captured per iteration.  This module only sequences
-calls: every step of the computation runs in the library's kernels.
+A thin binding of the batch calls of the C ABI (af_batch_plan, af_batch_iterate,
+af_batch_capture, af_batch_launch): the library owns one plan and one stream per
+acquisition, forks them from the caller's stream and joins them back.
+`BatchRunner.capture` records `iterations` calls of af_iterate for every
+acquisition into one CUDA graph; `replay()` runs the whole job (all
+acquisitions, all iterations) with a single graph launch.  This module only
+marshals arguments: every step of the computation runs in the library's
+kernels.
 """
 from __future__ import annotations
 
+import ctypes
+
 import torch
 
-from . import Plan
+from . import AfConfig, Plan, _check, iq_view, load, make_config
+
+
+def _array(tensors):
+    """Host array of the tensors' device pointers (NULL for None)."""
+    out = (ctypes.c_void_p * len(tensors))()
+    for k, t in enumerate(tensors):
+        if t is not None:
+            if not t.is_cuda or not t.is_contiguous():
+                raise ValueError("contiguous device tensors only")
+            out[k] = t.data_ptr()
+    return out
 
 
 class BatchRunner:
-    def __init__(self, problems, iqs, scales=None, iq_dtype=0, device=None):
+    def __init__(self, problems, iqs, scales=None, iq_dtype=0, device=None, stream=None):
+        self.lib = load()
         self.device = device or torch.device("cuda", torch.cuda.current_device())
-        self.streams = [torch.cuda.Stream(device=self.device) for _ in problems]
-        self.plans = [Plan(p, iq_dtype=iq_dtype, stream=st) for p, st in zip(problems, self.streams)]
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.problems = list(problems)
-        self.iqs = list(iqs)
-        self.scales = list(scales) if scales is not None else [None] * len(problems)
-        self.s0 = [torch.from_numpy(p.initial_slowness()).to(self.device) for p in problems]
-        self.s = [x.clone() for x in self.s0]
-        self.m = [torch.zeros_like(x) for x in self.s0]
-        self.v = [torch.zeros_like(x) for x in self.s0]
-        self.g = [torch.zeros_like(x) for x in self.s0]
-        self.loss = [torch.zeros(4, device=self.device) for _ in problems]
-        self.graph = None
+        n = len(self.problems)
+        cfgs = [make_config(p, iq_dtype) for p in self.problems]     # (config, kept arrays)
+        self._cfgs = cfgs
+        cfg_ptrs = (ctypes.POINTER(AfConfig) * n)(*[ctypes.pointer(c) for c, _ in cfgs])
+        h = ctypes.c_void_p()
+        _check(self.lib.af_batch_plan(n, cfg_ptrs, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
+               "af_batch_plan")
+        self.handle = h
+        self.plans = [Plan.batch_member(self, k, p, iq_dtype, self.stream) for k, p in enumerate(self.problems)]
+        self.iqs = [iq_view(x) for x in iqs]
+        self.scales = list(scales) if scales is not None else [None] * n
+        with torch.cuda.stream(self.stream):
+            self.s0 = [torch.from_numpy(p.initial_slowness()).to(self.device) for p in self.problems]
+            self.s = [x.clone() for x in self.s0]
+            self.m = [torch.zeros_like(x) for x in self.s0]
+            self.v = [torch.zeros_like(x) for x in self.s0]
+            self.g = [torch.zeros_like(x) for x in self.s0]
+            self.loss = [torch.zeros(4, device=self.device) for _ in self.problems]
+        self._ptrs = [_array(x) for x in (self.iqs, self.scales, self.s, self.g, self.m, self.v, self.loss)]
+        self.captured = False
 
     def reset(self):
         """Initial slowness and zero Adam moments (outside the graph)."""
-        for k in range(len(self.plans)):
-            self.s[k].copy_(self.s0[k])
-            self.m[k].zero_()
-            self.v[k].zero_()
+        with torch.cuda.stream(self.stream):
+            for k in range(len(self.problems)):
+                self.s[k].copy_(self.s0[k])
+                self.m[k].zero_()
+                self.v[k].zero_()
         torch.cuda.synchronize(self.device)
 
-    def _issue(self, iterations, first_step=1):
-        for k, plan in enumerate(self.plans):
-            with torch.cuda.stream(self.streams[k]):
-                for it in range(first_step, first_step + iterations):
-                    plan.af_iterate(self.iqs[k], self.s[k], self.g[k], self.m[k], self.v[k], it, self.loss[k],
-                                    self.scales[k])
+    def run_eager(self, iterations, first_step=1):
+        """The same calls without a graph: one af_batch_iterate per iteration."""
+        iq, sc, s, g, m, v, loss = self._ptrs
+        for it in range(first_step, first_step + iterations):
+            _check(self.lib.af_batch_iterate(self.handle, iq, sc, s, g, m, v, int(it), loss), "af_batch_iterate")
 
-    def run_eager(self, iterations):
-        """The same calls without a graph, stream by stream."""
-        cur = torch.cuda.current_stream(self.device)
-        for st in self.streams:
-            st.wait_stream(cur)
-        self._issue(iterations)
-        for st in self.streams:
-            cur.wait_stream(st)
-
-    def capture(self, iterations, warmup=True):
+    def capture(self, iterations, warmup=True, first_step=1):
         """Record `iterations` autofocus iterations of every acquisition into one graph."""
         if warmup:                                   # first calls set up warm starts outside capture
             self.run_eager(1)
             torch.cuda.synchronize(self.device)
             self.reset()
-        self.graph = torch.cuda.CUDAGraph()
-        cap = torch.cuda.Stream(device=self.device)
-        cap.wait_stream(torch.cuda.current_stream(self.device))
-        with torch.cuda.graph(self.graph, stream=cap):
-            for st in self.streams:
-                st.wait_stream(cap)
-            self._issue(iterations)
-            for st in self.streams:
-                cap.wait_stream(st)
-        torch.cuda.synchronize(self.device)
-        return self.graph
+        iq, sc, s, g, m, v, loss = self._ptrs
+        _check(self.lib.af_batch_capture(self.handle, iq, sc, s, g, m, v, loss, int(first_step), int(iterations)),
+               "af_batch_capture")
+        self.captured = True
 
     def replay(self):
-        self.graph.replay()
+        _check(self.lib.af_batch_launch(self.handle), "af_batch_launch")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            for p in self.plans:
+                p.handle = None
+            self.lib.af_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -121,3 +121,25 @@ def test_plan_without_gpu_fails_cleanly():
     st = af.load().af_plan(ctypes.byref(c), None, ctypes.byref(h))
     assert st == af.AF_ERR_CUDA
     assert not h.value
+
+
+def test_batch_calls_validate_arguments_on_the_host():
+    """The batch entry points reject bad arguments before any CUDA call."""
+    lib = af.load()
+    h = ctypes.c_void_p(123)
+    assert lib.af_batch_plan(0, None, None, ctypes.byref(h)) == af.AF_ERR_ARG
+    assert not h.value                                   # *out cleared on failure
+    assert lib.af_batch_plan(1, None, None, None) == af.AF_ERR_ARG
+    good, keep = af.make_config(synth.config_tiny())
+    bad, keep2 = af.make_config(dataclasses.replace(synth.config_tiny(), c_lens=0.0))
+    arr = (ctypes.POINTER(af.AfConfig) * 2)(ctypes.pointer(good), ctypes.pointer(bad))
+    assert lib.af_batch_plan(2, arr, None, ctypes.byref(h)) == af.AF_ERR_ARG   # member 1 invalid
+    arr2 = (ctypes.POINTER(af.AfConfig) * 2)(ctypes.pointer(good), None)
+    assert lib.af_batch_plan(2, arr2, None, ctypes.byref(h)) == af.AF_ERR_ARG  # NULL member
+    assert b"configuration 1" in lib.af_last_error()
+    p = ctypes.c_void_p()
+    assert lib.af_batch_plan_of(None, 0, ctypes.byref(p)) == af.AF_ERR_ARG
+    assert lib.af_batch_launch(None) == af.AF_ERR_ARG
+    assert lib.af_batch_iterate(None, None, None, None, None, None, None, 1, None) == af.AF_ERR_ARG
+    assert lib.af_batch_capture(None, None, None, None, None, None, None, None, 1, 1) == af.AF_ERR_ARG
+    assert lib.af_batch_destroy(None) == af.AF_OK
