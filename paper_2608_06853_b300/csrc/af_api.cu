@@ -219,7 +219,7 @@ af_status af_workspace_bytes(const af_config *c, size_t *bytes)
     const size_t nsub = ne / c->sub_width, nb = nsub * nsub, npair = (size_t)n_pairs(c);
     const size_t ng = (size_t)c->nx * c->nz;
     size_t b = 0;
-    b += ne * (sizeof(float4) + sizeof(float2)) + npix * 2 * sizeof(float2);
+    b += ne * (sizeof(float4) + sizeof(float2)) + npix * (2 * sizeof(float2) + sizeof(int2));
     b += ne * npix * (sizeof(float) + sizeof(float4) + sizeof(float));   // phi, D, gdel
     b += 2 * nb * npix * sizeof(float2);                                  // B, G
     b += (size_t)c->n_patch * npair * (sizeof(float2) + 1);               // z, mask
@@ -235,7 +235,7 @@ af_status af_destroy(af_plan_t pl)
     if (!pl) return AF_OK;
     for (int k = 0; k < 2 * kTimingCap; ++k)
         if (pl->ev[k]) cudaEventDestroy(pl->ev[k]);
-    void *ptrs[] = {pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->D, pl->B, pl->G, pl->z,
+    void *ptrs[] = {pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->D, pl->nrange, pl->B, pl->G, pl->z,
                     pl->mask, pl->patch_sum, pl->patch_cnt, pl->gdel, pl->gpart, pl->gpad, pl->scal, pl->stat_part,
                     pl->mlp_p, pl->mlp_m, pl->mlp_v, pl->mlp_g, pl->mlp_w2b, pl->mlp_w3b, pl->sur_fb};
     for (void *p : ptrs)
@@ -417,6 +417,7 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
     AF_ALLOC(pl->pix_pol, npix * sizeof(float2));
     AF_ALLOC(pl->phi, nep * sizeof(float));
     AF_ALLOC(pl->D, nep * sizeof(float4));
+    AF_ALLOC(pl->nrange, npix * sizeof(int2));
     AF_ALLOC(pl->gdel, nep * sizeof(float));
     AF_ALLOC(pl->B, nbp * sizeof(float2));
     AF_ALLOC(pl->G, nbp * sizeof(float2));

@@ -30,9 +30,11 @@ template <> struct Sample<AF_IQ_F16> {
 constexpr int kWarps = 8;   // warps per CTA; warp w takes receive blocks w, w + 8, ...
 
 // Gather of one transmit for the W receivers held by a lane: all 2W loads are
-// issued before any is used (indices clamped into the trace, out-of-range
-// samples get weight 0), so a warp keeps 2W loads in flight.
-template <int W, typename S>
+// issued before any is used, so a warp keeps 2W loads in flight.  CHECK: the
+// indices are clamped into the trace and out-of-range samples get weight 0;
+// without CHECK the caller has shown that every sample n, n + 1 of the W
+// receivers lies in the trace.
+template <int W, typename S, bool CHECK>
 __device__ __forceinline__ void gather_w(const typename S::T *__restrict__ base, int ns, int nt,
                                          float ft, const int (&nr)[W], const float (&fr)[W],
                                          float2 (&a)[W], float2 (&b)[W], float (&f)[W], float (&on)[W])
@@ -44,10 +46,15 @@ __device__ __forceinline__ void gather_w(const typename S::T *__restrict__ base,
         int n = nt + nr[k];
         float fk = ft + fr[k];
         if (fk >= 1.0f) { fk -= 1.0f; ++n; }
-        const bool valid = (unsigned)n < (unsigned)lim;
-        idx[k] = k * ns + (valid ? n : 0);
         f[k] = fk;
-        on[k] = valid ? 1.0f : 0.0f;
+        if (CHECK) {
+            const bool valid = (unsigned)n < (unsigned)lim;
+            idx[k] = k * ns + (valid ? n : 0);
+            on[k] = valid ? 1.0f : 0.0f;
+        } else {
+            idx[k] = k * ns + n;
+            on[k] = 1.0f;
+        }
     }
 #pragma unroll
     for (int k = 0; k < W; ++k) {
@@ -56,34 +63,72 @@ __device__ __forceinline__ void gather_w(const typename S::T *__restrict__ base,
     }
 }
 
-// Forward: CTA = 8 warps on 8 neighbouring tiles of 32 pixels (256
-// consecutive pixels, about three laterally adjacent patches), all with the
-// same receive block j = blockIdx.y.  The warps walk the transmits in the same
-// order, so the trace windows one warp pulls into L1 serve the other seven.
-// The gathers are latency bound: the transmit loop is unrolled by two so that
-// a lane has the 4W loads of two transmits in flight (2 CTAs of 256 per SM).
-template <int W, int DT>
-__global__ void __launch_bounds__(256, 2) das_forward_kernel(AfGeom g, const void *__restrict__ iq,
-                                                             const float *__restrict__ scale,
-                                                             const float4 *__restrict__ D,
-                                                             float2 *__restrict__ B)
+// Receive side of a lane (block j, pixel p) in registers.  A receiver outside
+// the aperture gets phasor 0 and the sample index of a live receiver of the
+// block, so it adds exactly nothing and its samples lie where the live ones
+// do.  Returns the mask of live receivers (bit k: receiver j W + k), 0 when
+// the whole block is outside the aperture.
+template <int W>
+__device__ __forceinline__ unsigned receive_side(const float4 *__restrict__ D, int npix, int j, int p,
+                                                 int (&nr)[W], float (&fr)[W], float2 (&pr)[W])
 {
-    using S = Sample<DT>;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int p = (blockIdx.x * kWarps + warp) * 32 + lane;
-    const int j = blockIdx.y;
-    if (p >= g.npix) return;
-    const typename S::T *psi = reinterpret_cast<const typename S::T *>(iq);
-    int nr[W];
-    float fr[W];
-    float2 pr[W];
+    int live = 0;
+    unsigned mask = 0u;
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-        const float4 d = D[(long)(j * W + k) * g.npix + p];
+        const float4 d = D[(long)(j * W + k) * npix + p];
         nr[k] = __float_as_int(d.x);
         fr[k] = d.y;
         pr[k] = make_float2(d.z, d.w);
+        if (nr[k] != AF_APOD_OFF) { live = nr[k]; mask |= 1u << k; }
     }
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        if (nr[k] == AF_APOD_OFF) {
+            nr[k] = live;
+            fr[k] = 0.0f;
+            pr[k] = make_float2(0.0f, 0.0f);
+        }
+    }
+    return mask;
+}
+
+// Every gather of pixel p reads samples n and n + 1 with n = n_t + n_r + carry
+// <= 2 max n + 1, n >= 2 min n, where r = {min n, -max n} over the pixel's live
+// one-way indices (written by the delay kernel).  True when all of them lie in
+// [0, ns - 1], so that the gathers need no range check.
+__device__ __forceinline__ bool pixel_in_trace(int2 r, int ns)
+{
+    return r.x >= 0 && 2LL * -(long long)r.y <= (long long)ns - 3;
+}
+
+template <int W, typename S, bool CHECK>
+__device__ __forceinline__ float2 das_transmit(const typename S::T *__restrict__ base, int ns, int nt, float ft,
+                                               const int (&nr)[W], const float (&fr)[W], const float2 (&pr)[W])
+{
+    float2 a[W], b[W];
+    float f[W], on[W];
+    gather_w<W, S, CHECK>(base, ns, nt, ft, nr, fr, a, b, f, on);
+    float sr = 0.0f, si = 0.0f;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        float vr = fmaf(f[k], b[k].x - a[k].x, a[k].x);
+        float vi = fmaf(f[k], b[k].y - a[k].y, a[k].y);
+        if (CHECK) { vr *= on[k]; vi *= on[k]; }
+        sr = fmaf(pr[k].x, vr, fmaf(-pr[k].y, vi, sr));
+        si = fmaf(pr[k].x, vi, fmaf(pr[k].y, vr, si));
+    }
+    return make_float2(sr, si);
+}
+
+// B_ij(p) for every transmit block i of one lane (receive block j)
+template <int W, int DT, bool CHECK>
+__device__ __forceinline__ void das_forward_blocks(const AfGeom &g, const typename Sample<DT>::T *__restrict__ psi,
+                                                   const float *__restrict__ scale, const float4 *__restrict__ D,
+                                                   float2 *__restrict__ B, int j, int p, const int (&nr)[W],
+                                                   const float (&fr)[W], const float2 (&pr)[W])
+{
+    using S = Sample<DT>;
     float4 dnext = D[p];
     for (int i = 0; i < g.nsub; ++i) {
         float ar = 0.0f, ai = 0.0f;
@@ -95,24 +140,50 @@ __global__ void __launch_bounds__(256, 2) das_forward_kernel(AfGeom g, const voi
             const int nt = __float_as_int(dt.x);
             if (nt == AF_APOD_OFF) continue;
             const typename S::T *base = psi + ((long)t * g.ne + j * W) * g.ns;
-            float2 a[W], b[W];
-            float f[W], on[W];
-            gather_w<W, S>(base, g.ns, nt, dt.y, nr, fr, a, b, f, on);
-            float sr = 0.0f, si = 0.0f;
-#pragma unroll
-            for (int k = 0; k < W; ++k) {
-                const float vr = on[k] * fmaf(f[k], b[k].x - a[k].x, a[k].x);
-                const float vi = on[k] * fmaf(f[k], b[k].y - a[k].y, a[k].y);
-                sr = fmaf(pr[k].x, vr, fmaf(-pr[k].y, vi, sr));
-                si = fmaf(pr[k].x, vi, fmaf(pr[k].y, vr, si));
-            }
+            const float2 sv = das_transmit<W, S, CHECK>(base, g.ns, nt, dt.y, nr, fr, pr);
             float cr = dt.z, ci = dt.w;
             if (DT != AF_IQ_C64) { const float sc = scale[t]; cr *= sc; ci *= sc; }
-            ar = fmaf(cr, sr, fmaf(-ci, si, ar));
-            ai = fmaf(cr, si, fmaf(ci, sr, ai));
+            ar = fmaf(cr, sv.x, fmaf(-ci, sv.y, ar));
+            ai = fmaf(cr, sv.y, fmaf(ci, sv.x, ai));
         }
         B[(long)(i * g.nsub + j) * g.npix + p] = make_float2(ar, ai);
     }
+}
+
+// Forward: CTA = 8 warps on 8 neighbouring tiles of 32 pixels (256
+// consecutive pixels, about three laterally adjacent patches), all with the
+// same receive block j = blockIdx.y.  The warps walk the transmits in the same
+// order, so the trace windows one warp pulls into L1 serve the other seven.
+// The gathers are latency bound: the transmit loop is unrolled by two so that
+// a lane has the 4W loads of two transmits in flight (2 CTAs of 256 per SM).
+// A warp whose receive block is outside the aperture for all its pixels only
+// writes zeros; a warp whose pixels' samples all lie in the trace runs the
+// gathers without range checks.
+template <int W, int DT>
+__global__ void __launch_bounds__(256, 2) das_forward_kernel(AfGeom g, const void *__restrict__ iq,
+                                                             const float *__restrict__ scale,
+                                                             const float4 *__restrict__ D,
+                                                             const int2 *__restrict__ nrange,
+                                                             float2 *__restrict__ B)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p = (blockIdx.x * kWarps + warp) * 32 + lane;
+    const int j = blockIdx.y;
+    if (p >= g.npix) return;
+    const typename Sample<DT>::T *psi = reinterpret_cast<const typename Sample<DT>::T *>(iq);
+    int nr[W];
+    float fr[W];
+    float2 pr[W];
+    const bool live = receive_side<W>(D, g.npix, j, p, nr, fr, pr) != 0u;
+    const unsigned act = __activemask();
+    if (!__any_sync(act, live)) {
+        for (int i = 0; i < g.nsub; ++i) B[(long)(i * g.nsub + j) * g.npix + p] = make_float2(0.0f, 0.0f);
+        return;
+    }
+    if (__all_sync(act, pixel_in_trace(nrange[p], g.ns)))
+        das_forward_blocks<W, DT, false>(g, psi, scale, D, B, j, p, nr, fr, pr);
+    else
+        das_forward_blocks<W, DT, true>(g, psi, scale, D, B, j, p, nr, fr, pr);
 }
 
 // Adjoint: same CTA shape as the forward (8 neighbouring pixel tiles, one
@@ -121,39 +192,47 @@ __global__ void __launch_bounds__(256, 2) das_forward_kernel(AfGeom g, const voi
 // dL/dT_t and dL/dT_r.  A lane sums the transmit role over its block's W
 // receivers and the receive role over all transmits, then adds both into the
 // zeroed dL/dT table with coalesced atomic adds (one per transmit and one per
-// receiver of the block).
-template <int W, int DT>
-__global__ void __launch_bounds__(256, 2) das_adjoint_kernel(AfGeom g, const void *__restrict__ iq,
-                                                             const float *__restrict__ scale,
-                                                             const float4 *__restrict__ D,
-                                                             const float2 *__restrict__ G,
-                                                             float *__restrict__ gdel)
+// live receiver of the block).
+template <int W, typename S, bool CHECK>
+__device__ __forceinline__ float adj_transmit(const AfGeom &g, const typename S::T *__restrict__ base, int nt,
+                                              float ft, float xr, float xi, const int (&nr)[W],
+                                              const float (&fr)[W], const float2 (&pr)[W], float (&gr)[W])
 {
-    using S = Sample<DT>;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int p = (blockIdx.x * kWarps + warp) * 32 + lane;
-    const int j = blockIdx.y;
-    if (p >= g.npix) return;
-    const typename S::T *psi = reinterpret_cast<const typename S::T *>(iq);
-    int nr[W];
-    float fr[W];
-    float2 pr[W];
-    float gr[W];
+    float2 a[W], b[W];
+    float f[W], on[W];
+    gather_w<W, S, CHECK>(base, g.ns, nt, ft, nr, fr, a, b, f, on);
+    float gt = 0.0f;
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-        const float4 d = D[(long)(j * W + k) * g.npix + p];
-        nr[k] = __float_as_int(d.x);
-        fr[k] = d.y;
-        pr[k] = make_float2(d.z, d.w);
-        gr[k] = 0.0f;
+        const float sx = b[k].x - a[k].x, sy = b[k].y - a[k].y;
+        const float vr = fmaf(f[k], sx, a[k].x), vi = fmaf(f[k], sy, a[k].y);
+        float yr = fmaf(xr, pr[k].x, -xi * pr[k].y);
+        float yi = fmaf(xr, pr[k].y, xi * pr[k].x);
+        if (CHECK) { yr *= on[k]; yi *= on[k]; }
+        const float dr = fmaf(g.fs, sx, -g.wd * vi);
+        const float di = fmaf(g.fs, sy, g.wd * vr);
+        const float q = fmaf(yr, dr, -yi * di);
+        gt += q;
+        gr[k] += q;
     }
+    return gt;
+}
+
+template <int W, int DT, bool CHECK>
+__device__ __forceinline__ void das_adjoint_blocks(const AfGeom &g, const typename Sample<DT>::T *__restrict__ psi,
+                                                   const float *__restrict__ scale, const float4 *__restrict__ D,
+                                                   const float2 *__restrict__ G, float *__restrict__ gdel, int j,
+                                                   int p, bool live, const int (&nr)[W], const float (&fr)[W],
+                                                   const float2 (&pr)[W], float (&gr)[W])
+{
+    using S = Sample<DT>;
     float4 dnext = D[p];
     for (int i = 0; i < g.nsub; ++i) {
         const float2 Gv = G[(long)(i * g.nsub + j) * g.npix + p];
         // every term of transmit block i is weighted by conj(G_ij(p)): where the CMPE
         // mask leaves G_ij(p) = 0 the block adds exactly nothing, so it is skipped
         // (by the whole warp when no lane has a gradient, else lane by lane)
-        const bool gzero = Gv.x == 0.0f && Gv.y == 0.0f;
+        const bool gzero = (Gv.x == 0.0f && Gv.y == 0.0f) || !live;
         if (__all_sync(__activemask(), gzero)) {
             if ((i + 1) * W < g.ne) dnext = D[(long)(i + 1) * W * g.npix + p];
             continue;
@@ -171,27 +250,42 @@ __global__ void __launch_bounds__(256, 2) das_adjoint_kernel(AfGeom g, const voi
             const float xr = sc * fmaf(Gv.x, dt.z, Gv.y * dt.w);
             const float xi = sc * fmaf(Gv.x, dt.w, -Gv.y * dt.z);
             const typename S::T *base = psi + ((long)t * g.ne + j * W) * g.ns;
-            float2 a[W], b[W];
-            float f[W], on[W];
-            gather_w<W, S>(base, g.ns, nt, dt.y, nr, fr, a, b, f, on);
-            float gt = 0.0f;
-#pragma unroll
-            for (int k = 0; k < W; ++k) {
-                const float sx = b[k].x - a[k].x, sy = b[k].y - a[k].y;
-                const float vr = fmaf(f[k], sx, a[k].x), vi = fmaf(f[k], sy, a[k].y);
-                const float yr = on[k] * fmaf(xr, pr[k].x, -xi * pr[k].y);
-                const float yi = on[k] * fmaf(xr, pr[k].y, xi * pr[k].x);
-                const float dr = fmaf(g.fs, sx, -g.wd * vi);
-                const float di = fmaf(g.fs, sy, g.wd * vr);
-                const float q = fmaf(yr, dr, -yi * di);
-                gt += q;
-                gr[k] += q;
-            }
+            const float gt = adj_transmit<W, S, CHECK>(g, base, nt, dt.y, xr, xi, nr, fr, pr, gr);
             atomicAdd(&gdel[(long)t * g.npix + p], gt);
         }
     }
+}
+
+template <int W, int DT>
+__global__ void __launch_bounds__(256, 2) das_adjoint_kernel(AfGeom g, const void *__restrict__ iq,
+                                                             const float *__restrict__ scale,
+                                                             const float4 *__restrict__ D,
+                                                             const int2 *__restrict__ nrange,
+                                                             const float2 *__restrict__ G,
+                                                             float *__restrict__ gdel)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p = (blockIdx.x * kWarps + warp) * 32 + lane;
+    const int j = blockIdx.y;
+    if (p >= g.npix) return;
+    const typename Sample<DT>::T *psi = reinterpret_cast<const typename Sample<DT>::T *>(iq);
+    int nr[W];
+    float fr[W];
+    float2 pr[W];
+    float gr[W];
+    const unsigned rmask = receive_side<W>(D, g.npix, j, p, nr, fr, pr);
+    const bool live = rmask != 0u;
+    const unsigned act = __activemask();
+    if (!__any_sync(act, live)) return;        // adds nothing
 #pragma unroll
-    for (int k = 0; k < W; ++k) atomicAdd(&gdel[(long)(j * W + k) * g.npix + p], gr[k]);
+    for (int k = 0; k < W; ++k) gr[k] = 0.0f;
+    if (__all_sync(act, pixel_in_trace(nrange[p], g.ns)))
+        das_adjoint_blocks<W, DT, false>(g, psi, scale, D, G, gdel, j, p, live, nr, fr, pr, gr);
+    else
+        das_adjoint_blocks<W, DT, true>(g, psi, scale, D, G, gdel, j, p, live, nr, fr, pr, gr);
+#pragma unroll
+    for (int k = 0; k < W; ++k)
+        if (rmask >> k & 1u) atomicAdd(&gdel[(long)(j * W + k) * g.npix + p], gr[k]);
 }
 
 // max |dL/dT| for the fixed-point scale of the ray adjoint (non-negative floats
@@ -211,7 +305,7 @@ cudaError_t launch_fwd_t(af_plan_t pl)
 {
     const dim3 blocks((pl->g.npix + 32 * kWarps - 1) / (32 * kWarps), pl->g.nsub);
     das_forward_kernel<W, DT><<<blocks, 32 * kWarps, 0, pl->stream>>>(
-        pl->g, pl->iq, pl->iq_scale, pl->D, pl->B);
+        pl->g, pl->iq, pl->iq_scale, pl->D, pl->nrange, pl->B);
     return cudaGetLastError();
 }
 
@@ -222,8 +316,8 @@ cudaError_t launch_adj_t(af_plan_t pl)
     cudaError_t e = cudaMemsetAsync(pl->gdel, 0, n * sizeof(float), pl->stream);
     if (e != cudaSuccess) return e;
     const dim3 blocks((pl->g.npix + 32 * kWarps - 1) / (32 * kWarps), pl->g.nsub);
-    das_adjoint_kernel<W, DT><<<blocks, 32 * kWarps, 0, pl->stream>>>(pl->g, pl->iq, pl->iq_scale, pl->D, pl->G,
-                                                                       pl->gdel);
+    das_adjoint_kernel<W, DT><<<blocks, 32 * kWarps, 0, pl->stream>>>(pl->g, pl->iq, pl->iq_scale, pl->D,
+                                                                       pl->nrange, pl->G, pl->gdel);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     gdel_max_kernel<<<pl->sm_count * 4, 256, 0, pl->stream>>>(pl->gdel, n, &pl->scal->gmax_bits);

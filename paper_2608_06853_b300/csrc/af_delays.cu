@@ -125,7 +125,8 @@ __global__ void __launch_bounds__(PAIRS ? 768 : 256) delays_kernel(AfGeom g, con
                                                      const float2 *__restrict__ pix_pol,
                                                      float *__restrict__ phi, int warm,
                                                      const uint8_t *__restrict__ sur_fb,
-                                                     float4 *__restrict__ D, AfScal *scal)
+                                                     float4 *__restrict__ D, int2 *__restrict__ nrange,
+                                                     AfScal *scal)
 {
     extern __shared__ float sm[];
     const float sbar = scal->sbar;
@@ -279,6 +280,8 @@ __global__ void __launch_bounds__(PAIRS ? 768 : 256) delays_kernel(AfGeom g, con
         float ps, pc;
         sincospif(2.0f * cyc, &ps, &pc);
         D[idx] = make_float4(__int_as_float(ni), fr, pc, ps);
+        atomicMin(&nrange[p].x, ni);
+        atomicMin(&nrange[p].y, -ni);
     }
     // counters
     for (int o = 16; o > 0; o >>= 1) {
@@ -346,15 +349,18 @@ cudaError_t launch_delays(af_plan_t pl, const float *s)
 {
     if ((long)pl->g.ne * pl->g.npix == 0) return cudaSuccess;
     const DelayShape &sh = pl->delay;
+    // sample-index range per pixel: both fields start at 0x7F7F7F7F (above any index)
+    cudaError_t err = cudaMemsetAsync(pl->nrange, 0x7F, (size_t)pl->g.npix * sizeof(int2), pl->stream);
+    if (err != cudaSuccess) return err;
     if (sh.pairs)
         delays_kernel<true><<<sh.blocks, sh.threads, sh.smem, pl->stream>>>(
             pl->g, s, pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->have_phi ? 1 : 0,
-            pl->use_surrogate ? pl->sur_fb : nullptr, pl->D, pl->scal);
+            pl->use_surrogate ? pl->sur_fb : nullptr, pl->D, pl->nrange, pl->scal);
     else
         delays_kernel<false><<<sh.blocks, sh.threads, sh.smem, pl->stream>>>(
             pl->g, s, pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->have_phi ? 1 : 0,
-            pl->use_surrogate ? pl->sur_fb : nullptr, pl->D, pl->scal);
-    cudaError_t err = cudaGetLastError();
+            pl->use_surrogate ? pl->sur_fb : nullptr, pl->D, pl->nrange, pl->scal);
+    err = cudaGetLastError();
     if (err == cudaSuccess) pl->have_phi = true;
     return err;
 }

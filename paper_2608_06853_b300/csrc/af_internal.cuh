@@ -104,6 +104,7 @@ struct af_plan_s {
     // workspaces
     float *phi;          // [ne][npix] exit angles
     float4 *D;           // [ne][npix] {sample index (int bits), fraction, Re P, Im P}
+    int2 *nrange;        // [npix] {min n, min -n} over the pixel's live one-way sample indices n
     float2 *B, *G;       // [nb][npix] images and dL/dB
     float2 *z;           // [n_patch][npair] CMPE cross terms
     uint8_t *mask;       // [n_patch][npair]
