@@ -243,24 +243,37 @@ __global__ void __launch_bounds__(PAIRS ? 768 : 256) delays_kernel(AfGeom g, con
         const float gx0 = (qx - g.x0) * g.inv_dx, gz0 = (qz - g.z0) * g.inv_dz;
         const float gdx = (px.x - qx) * g.inv_dx * g.inv_nseg;
         const float gdz = (px.y - qz) * g.inv_dz * g.inv_nseg;
-        float sum = 0.0f, comp = 0.0f;
-        for (int k = 0; k <= g.nseg; ++k) {
-            const float gx = fmaf((float)k, gdx, gx0), gz = fmaf((float)k, gdz, gz0);
+        // interpolated value at endpoint kf, added into the running partial sum
+        auto point = [&](float kf, float part) {
+            const float gx = fmaf(kf, gdx, gx0), gz = fmaf(kf, gdz, gz0);
             const float fx = floorf(gx), fz = floorf(gz);
             const int i0 = min(max((int)fx, -1), g.nx - 1), j0 = min(max((int)fz, -1), g.nz - 1);
             float wx[4], wz[4];
             keys_weights(gx - fx, wx);
             keys_weights(gz - fz, wz);
             const int row = (j0 + 1) * P + (i0 + 1);           // padded node (i0-1, j0-1)
-            float v = 0.0f;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) v = fmaf(wz[b], GridTaps<PAIRS>::row(sm, row + b * P, wx), v);
-            // Kahan summation of the N+1 endpoint values
+            for (int b = 0; b < 4; ++b) part = fmaf(wz[b], GridTaps<PAIRS>::row(sm, row + b * P, wx), part);
+            return part;
+        };
+        // the N+1 endpoint values in partial sums of 4, Kahan-summed
+        float sum = 0.0f, comp = 0.0f, kf = 0.0f;
+        auto kahan = [&](float v) {
             const float y = v - comp;
             const float t = sum + y;
             comp = (t - sum) - y;
             sum = t;
+        };
+        const float kend = (float)g.nseg;
+        for (; kf + 3.0f <= kend; kf += 4.0f) {
+            float part = point(kf, 0.0f);
+            part = point(kf + 1.0f, part);
+            part = point(kf + 2.0f, part);
+            kahan(point(kf + 3.0f, part));
         }
+        float part = 0.0f;
+        for (; kf <= kend; kf += 1.0f) part = point(kf, part);
+        kahan(part);
         const float mean_fs = (sum - comp) * g.inv_nseg1 * g.fs;
         // one-way delay in samples, shifted by (t_ttp - t0) fs / 2
         ff U = ff_mul(L, sfs);

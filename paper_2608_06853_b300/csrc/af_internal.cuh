@@ -190,14 +190,17 @@ __device__ __forceinline__ ff ff_dist(float ax, float az, float bx, float bz)
     return ff_sqrt(ff_add(x2, z2));
 }
 
-// Keys cubic-convolution weights (a = -1/2) for taps -1, 0, 1, 2 at fraction t
+// Keys cubic-convolution weights (a = -1/2) for taps -1, 0, 1, 2 at fraction t,
+// factored with u = 1 - t: w0 = -t u^2 / 2, w3 = -t^2 u / 2,
+// w1 = 1 - 5/2 t^2 + 3/2 t^3, and w2 = 1 - w0 - w1 - w3 (the weights sum to 1).
 __device__ __forceinline__ void keys_weights(float t, float w[4])
 {
-    float t2 = t * t, t3 = t2 * t;
-    w[0] = -0.5f * t3 + t2 - 0.5f * t;
-    w[1] = 1.5f * t3 - 2.5f * t2 + 1.0f;
-    w[2] = -1.5f * t3 + 2.0f * t2 + 0.5f * t;
-    w[3] = 0.5f * t3 - 0.5f * t2;
+    const float u = 1.0f - t;
+    const float m = (-0.5f * t) * u;
+    w[0] = m * u;
+    w[3] = m * t;
+    w[1] = fmaf(t * t, fmaf(1.5f, t, -2.5f), 1.0f);
+    w[2] = (1.0f - m) - w[1];
 }
 
 // records the message returned by af_last_error() and returns st

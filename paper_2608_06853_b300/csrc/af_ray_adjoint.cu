@@ -53,17 +53,22 @@ constexpr float kRound = 12582912.0f;   // 1.5 * 2^23
 constexpr int kRoundBits = 0x4B400000;
 constexpr int kLeadRay = kRayGroup / 2; // the middle ray of an item
 
-// padded cell of point k of a ray (gx0, gz0, gdx, gdz) and its Keys weights
-__device__ __forceinline__ void ray_stencil(const AfGeom &g, float k, float4 ry, int &ic, int &jc, float wx[4],
-                                            float wz[4])
+// padded cell of point k of a ray (gx0, gz0, gdx, gdz), the floors of its grid
+// coordinates and its Keys weights
+__device__ __forceinline__ void ray_stencil(const AfGeom &g, float k, float4 ry, int &ic, int &jc, float &fx,
+                                            float &fz, float wx[4], float wz[4])
 {
     const float gx = fmaf(k, ry.z, ry.x), gz = fmaf(k, ry.w, ry.y);
-    const float fx = floorf(gx), fz = floorf(gz);
+    fx = floorf(gx);
+    fz = floorf(gz);
     ic = min(max((int)fx, -1), g.nx - 1) + 1;
     jc = min(max((int)fz, -1), g.nz - 1) + 1;
     keys_weights(gx - fx, wx);
     keys_weights(gz - fz, wz);
 }
+
+// t in [0, 1) (as bits: +0 up to the largest float below 1)
+__device__ __forceinline__ bool unit_fraction(float t) { return __float_as_uint(t) < 0x3F800000u; }
 
 // 16 atomics of one stencil whose values carry the rounding constant
 __device__ __forceinline__ void add_stencil(int *row, int pitch, const float (&W)[16])
@@ -87,9 +92,9 @@ __device__ __forceinline__ void run_queued(const AfGeom &g, int ent, int *acci, 
     const float4 cc = rayc[r];
     const int2 gb = rayb[r];
     const float cm = pick_c(cc, m);
-    float wx[4], wz[4], W[16];
+    float wx[4], wz[4], W[16], fx, fz;
     int i1, j1;
-    ray_stencil(g, (float)k, rays[m * T + r], i1, j1, wx, wz);
+    ray_stencil(g, (float)k, rays[m * T + r], i1, j1, fx, fz, wx, wz);
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         const float cb = cm * wz[b];
@@ -217,11 +222,11 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
                 const float kf = (float)k;
                 const float4 cc = rayc[r];
                 const int2 gb = rayb[r];
-                float W[16];
+                float W[16], fx0, fz0;
                 int i0, j0;
                 {
                     float wx[4], wz[4];
-                    ray_stencil(g, kf, rays[kLeadRay * T + r], i0, j0, wx, wz);
+                    ray_stencil(g, kf, rays[kLeadRay * T + r], i0, j0, fx0, fz0, wx, wz);
                     const float cl = pick_c(cc, kLeadRay);
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
@@ -233,11 +238,15 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
 #pragma unroll
                 for (int m = 0; m < kRayGroup; ++m) {
                     if (m == kLeadRay) continue;
+                    // the point shares the lead's cell when its coordinates have the
+                    // lead's floors; its fractions are then exactly its own
+                    const float4 rm = rays[m * T + r];
+                    const float tx = fmaf(kf, rm.z, rm.x) - fx0, tz = fmaf(kf, rm.w, rm.y) - fz0;
                     float wx[4], wz[4];
-                    int i1, j1;
-                    ray_stencil(g, kf, rays[m * T + r], i1, j1, wx, wz);
+                    keys_weights(tx, wx);
+                    keys_weights(tz, wz);
                     const float cm = pick_c(cc, m);
-                    const bool away = i1 != i0 || j1 != j0;
+                    const bool away = !(unit_fraction(tx) && unit_fraction(tz));
                     const float cmerge = away ? 0.0f : cm;
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
