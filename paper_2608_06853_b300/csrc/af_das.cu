@@ -132,7 +132,7 @@ __device__ __forceinline__ void das_forward_blocks(const AfGeom &g, const typena
     float4 dnext = D[p];
     for (int i = 0; i < g.nsub; ++i) {
         float ar = 0.0f, ai = 0.0f;
-#pragma unroll 2
+#pragma unroll 1
         for (int tt = 0; tt < W; ++tt) {
             const int t = i * W + tt;
             const float4 dt = dnext;
@@ -154,13 +154,15 @@ __device__ __forceinline__ void das_forward_blocks(const AfGeom &g, const typena
 // consecutive pixels, about three laterally adjacent patches), all with the
 // same receive block j = blockIdx.y.  The warps walk the transmits in the same
 // order, so the trace windows one warp pulls into L1 serve the other seven.
-// The gathers are latency bound: the transmit loop is unrolled by two so that
-// a lane has the 4W loads of two transmits in flight (2 CTAs of 256 per SM).
+// The gathers are latency bound: 4 CTAs of 256 per SM (64 registers) keep more
+// loads in flight than 2 CTAs with the transmit loop unrolled by two (0.61 ms
+// against 0.64 ms on the 128-element workload, although the complex64 variant
+// spills a few registers).
 // A warp whose receive block is outside the aperture for all its pixels only
 // writes zeros; a warp whose pixels' samples all lie in the trace runs the
 // gathers without range checks.
 template <int W, int DT>
-__global__ void __launch_bounds__(256, 2) das_forward_kernel(AfGeom g, const void *__restrict__ iq,
+__global__ void __launch_bounds__(256, 4) das_forward_kernel(AfGeom g, const void *__restrict__ iq,
                                                              const float *__restrict__ scale,
                                                              const float4 *__restrict__ D,
                                                              const int2 *__restrict__ nrange,

@@ -3,6 +3,8 @@
 // Fermat's principle, Eq. 1 straight-ray bicubic slowness sum, Sec. III-A).
 #include <math.h>
 
+#include <type_traits>
+
 #include "af_internal.cuh"
 #include "af_lens.cuh"
 
@@ -117,7 +119,7 @@ template <> struct GridTaps<true> {
 // slowness deviation s - sbar staged once per CTA in shared memory, padded by
 // two edge-replicated nodes on every side so that each of the 16 taps of a
 // point inside the grid box reads the clamp-to-edge value without a branch.
-template <bool PAIRS>
+template <bool PAIRS, int PF = 0>
 __global__ void __launch_bounds__(PAIRS ? 768 : 256) delays_kernel(AfGeom g, const float *__restrict__ s,
                                                      const float4 *__restrict__ elem,
                                                      const float2 *__restrict__ elem_pol,
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(PAIRS ? 768 : 256) delays_kernel(AfGeom g, con
 {
     extern __shared__ float sm[];
     const float sbar = scal->sbar;
-    const int P = g.pitch, rows = g.nz + 4;
+    const int P = PF ? PF : g.pitch, rows = g.nz + 4;   // PF: the pitch as a compile-time constant
     for (int k = threadIdx.x; k < P * rows; k += blockDim.x) {
         int jj = k / P, ii = k - jj * P;
         int i = min(max(ii - 2, 0), g.nx - 1), j = min(max(jj - 2, 0), g.nz - 1);
@@ -243,37 +245,55 @@ __global__ void __launch_bounds__(PAIRS ? 768 : 256) delays_kernel(AfGeom g, con
         const float gx0 = (qx - g.x0) * g.inv_dx, gz0 = (qz - g.z0) * g.inv_dz;
         const float gdx = (px.x - qx) * g.inv_dx * g.inv_nseg;
         const float gdz = (px.y - qz) * g.inv_dz * g.inv_nseg;
-        // interpolated value at endpoint kf, added into the running partial sum
-        auto point = [&](float kf, float part) {
-            const float gx = fmaf(kf, gdx, gx0), gz = fmaf(kf, gdz, gz0);
-            const float fx = floorf(gx), fz = floorf(gz);
-            const int i0 = min(max((int)fx, -1), g.nx - 1), j0 = min(max((int)fz, -1), g.nz - 1);
-            float wx[4], wz[4];
-            keys_weights(gx - fx, wx);
-            keys_weights(gz - fz, wz);
-            const int row = (j0 + 1) * P + (i0 + 1);           // padded node (i0-1, j0-1)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) part = fmaf(wz[b], GridTaps<PAIRS>::row(sm, row + b * P, wx), part);
-            return part;
-        };
+        // The endpoints' grid coordinates fmaf(k, gd, g0) are monotone in k, so the
+        // first and last bound all of them: when both lie in [-1, n) every cell index
+        // is inside the padded grid and the per-point clamps can be left out (a NaN
+        // coordinate fails the test and takes the clamped loop).
+        const float kend = (float)g.nseg;
+        const float gx1 = fmaf(kend, gdx, gx0), gz1 = fmaf(kend, gdz, gz0);
+        const bool inside = fminf(gx0, gx1) >= -1.0f && fmaxf(gx0, gx1) < (float)g.nx &&
+                            fminf(gz0, gz1) >= -1.0f && fmaxf(gz0, gz1) < (float)g.nz;
         // the N+1 endpoint values in partial sums of 4, Kahan-summed
-        float sum = 0.0f, comp = 0.0f, kf = 0.0f;
+        float sum = 0.0f, comp = 0.0f;
         auto kahan = [&](float v) {
             const float y = v - comp;
             const float t = sum + y;
             comp = (t - sum) - y;
             sum = t;
         };
-        const float kend = (float)g.nseg;
-        for (; kf + 3.0f <= kend; kf += 4.0f) {
-            float part = point(kf, 0.0f);
-            part = point(kf + 1.0f, part);
-            part = point(kf + 2.0f, part);
-            kahan(point(kf + 3.0f, part));
-        }
-        float part = 0.0f;
-        for (; kf <= kend; kf += 1.0f) part = point(kf, part);
-        kahan(part);
+        auto ray_sum = [&](auto clamp) {
+            // interpolated value at endpoint kf, added into the running partial sum
+            auto point = [&](float kf, float part) {
+                const float gx = fmaf(kf, gdx, gx0), gz = fmaf(kf, gdz, gz0);
+                const float fx = floorf(gx), fz = floorf(gz);
+                int i0 = (int)fx, j0 = (int)fz;
+                if (decltype(clamp)::value) {
+                    i0 = min(max(i0, -1), g.nx - 1);
+                    j0 = min(max(j0, -1), g.nz - 1);
+                }
+                float wx[4], wz[4];
+                keys_weights(gx - fx, wx);
+                keys_weights(gz - fz, wz);
+                const int row = (j0 + 1) * P + (i0 + 1);           // padded node (i0-1, j0-1)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) part = fmaf(wz[b], GridTaps<PAIRS>::row(sm, row + b * P, wx), part);
+                return part;
+            };
+            float kf = 0.0f;
+            for (; kf + 3.0f <= kend; kf += 4.0f) {
+                float part = point(kf, 0.0f);
+                part = point(kf + 1.0f, part);
+                part = point(kf + 2.0f, part);
+                kahan(point(kf + 3.0f, part));
+            }
+            float part = 0.0f;
+            for (; kf <= kend; kf += 1.0f) part = point(kf, part);
+            kahan(part);
+        };
+        if (inside)
+            ray_sum(std::false_type{});
+        else
+            ray_sum(std::true_type{});
         const float mean_fs = (sum - comp) * g.inv_nseg1 * g.fs;
         // one-way delay in samples, shifted by (t_ttp - t0) fs / 2
         ff U = ff_mul(L, sfs);
@@ -327,6 +347,10 @@ __global__ void export_delays_kernel(AfGeom g, const float4 *__restrict__ D, dou
 
 // launch shape of the delay kernel: the paired grid (one 768-thread CTA per SM)
 // when it fits in shared memory, else the scalar grid (256-thread CTAs)
+// padded row pitch of 128-wide grids ((nx + 4) | 1), compiled into one instance
+// so that the four tap rows of a point sit at constant offsets
+constexpr int kDelayPitch128 = 133;
+
 DelayShape delays_shape(size_t smem_scalar, int sm_count)
 {
     DelayShape sh;
@@ -338,6 +362,8 @@ DelayShape delays_shape(size_t smem_scalar, int sm_count)
     // grid any plan may use, the occupancy query uses this plan's size
     if (sh.pairs) {
         cudaFuncSetAttribute(delays_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kMaxGridSmemBytes);
+        cudaFuncSetAttribute(delays_kernel<true, kDelayPitch128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kMaxGridSmemBytes);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, delays_kernel<true>, 768, sh.smem);
     } else {
@@ -365,7 +391,11 @@ cudaError_t launch_delays(af_plan_t pl, const float *s)
     // sample-index range per pixel: both fields start at 0x7F7F7F7F (above any index)
     cudaError_t err = cudaMemsetAsync(pl->nrange, 0x7F, (size_t)pl->g.npix * sizeof(int2), pl->stream);
     if (err != cudaSuccess) return err;
-    if (sh.pairs)
+    if (sh.pairs && pl->g.pitch == kDelayPitch128)
+        delays_kernel<true, kDelayPitch128><<<sh.blocks, sh.threads, sh.smem, pl->stream>>>(
+            pl->g, s, pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->have_phi ? 1 : 0,
+            pl->use_surrogate ? pl->sur_fb : nullptr, pl->D, pl->nrange, pl->scal);
+    else if (sh.pairs)
         delays_kernel<true><<<sh.blocks, sh.threads, sh.smem, pl->stream>>>(
             pl->g, s, pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->have_phi ? 1 : 0,
             pl->use_surrogate ? pl->sur_fb : nullptr, pl->D, pl->nrange, pl->scal);

@@ -79,19 +79,21 @@ __device__ __forceinline__ void add_stencil(int *row, int pitch, const float (&W
         for (int a = 0; a < 4; ++a) atomicAdd(row + b * pitch + a, __float_as_int(W[b * 4 + a]) - kRoundBits);
 }
 
-__device__ __forceinline__ float pick_c(const float4 &cc, int m)
+// grid copy of an item (rayb = 1: copy B) as (base, row pitch)
+template <bool DUAL>
+__device__ __forceinline__ int2 copy_of(const RayGrid &rg, int b)
 {
-    return m == 0 ? cc.x : (m == 1 ? cc.y : cc.z);
+    return DUAL && b ? make_int2(rg.base_b, rg.pb) : make_int2(0, rg.pa);
 }
 
 // one queued point: entry = (item << 18) | (step << 2) | ray
-__device__ __forceinline__ void run_queued(const AfGeom &g, int ent, int *acci, const float4 *rays, int T,
-                                           const float4 *rayc, const int2 *rayb)
+template <bool DUAL>
+__device__ __forceinline__ void run_queued(const AfGeom &g, const RayGrid &rg, int ent, int *acci,
+                                           const float4 *rays, int T, const float *rayc, const int *rayb)
 {
     const int r = ent >> 18, k = (ent >> 2) & 0xFFFF, m = ent & 3;
-    const float4 cc = rayc[r];
-    const int2 gb = rayb[r];
-    const float cm = pick_c(cc, m);
+    const int2 gb = copy_of<DUAL>(rg, rayb[r]);
+    const float cm = rayc[m * T + r];
     float wx[4], wz[4], W[16], fx, fz;
     int i1, j1;
     ray_stencil(g, (float)k, rays[m * T + r], i1, j1, fx, fz, wx, wz);
@@ -118,8 +120,8 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
     constexpr int kQueue = 96;                       // < 32 carried + 2 x 32 new
     extern __shared__ int acci[];
     __shared__ float4 rays[kRayGroup * T];           // (gx0, gz0, gdx, gdz), ray m of item r at m * T + r
-    __shared__ float4 rayc[T];                       // dL/dT |q - r| / (N + 1), scaled; .w unused
-    __shared__ int2 rayb[T];                         // grid copy: (base, row pitch)
+    __shared__ float rayc[kRayGroup * T];            // dL/dT |q - r| / (N + 1), scaled, ray m at m * T + r
+    __shared__ int rayb[T];                          // grid copy of the item (1: copy B)
     __shared__ int fq[WARPS][kQueue];                // queued points
     __shared__ int wcount[WARPS];
     __shared__ long s_blk;
@@ -136,6 +138,7 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
     const long nitems = (long)g.ne * ngroups;
     const long nblk = S > 0.0f ? (nitems + T - 1) / T : 0;
     constexpr int kBlocksPerFlush = kRayItemsPerFlush / T;
+    static_assert(kBlocksPerFlush >= 1, "a flush interval holds at most kRayItemsPerFlush items");
     if (threadIdx.x == 0) s_blk = atomicAdd(&scal->ray_next, 1);
     __syncthreads();
     long blk = s_blk;
@@ -203,9 +206,10 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
             // dead rays take the lead's path (weight 0), so they always merge
 #pragma unroll
             for (int m = 0; m < kRayGroup; ++m) rays[m * T + slot] = c[m] != 0.0f ? rp[m] : rl;
-            rayc[slot] = make_float4(c[0], kRayGroup > 1 ? c[1] : 0.f, kRayGroup > 2 ? c[2] : 0.f, 0.f);
+#pragma unroll
+            for (int m = 0; m < kRayGroup; ++m) rayc[m * T + slot] = c[m];
             const bool right_down = rl.z * rl.w >= 0.0f;
-            rayb[slot] = DUAL && !right_down ? make_int2(rg.base_b, rg.pb) : make_int2(0, rg.pa);
+            rayb[slot] = DUAL && !right_down ? 1 : 0;
         }
         if (threadIdx.x == 0) s_blk = atomicAdd(&scal->ray_next, 1);
         __syncthreads();
@@ -220,14 +224,13 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
             for (int m = 0; m < kRayGroup; ++m) apart[m] = false;
             if (q0 + lane < npt_total) {
                 const float kf = (float)k;
-                const float4 cc = rayc[r];
-                const int2 gb = rayb[r];
+                const int2 gb = copy_of<DUAL>(rg, rayb[r]);
                 float W[16], fx0, fz0;
                 int i0, j0;
                 {
                     float wx[4], wz[4];
                     ray_stencil(g, kf, rays[kLeadRay * T + r], i0, j0, fx0, fz0, wx, wz);
-                    const float cl = pick_c(cc, kLeadRay);
+                    const float cl = rayc[kLeadRay * T + r];
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
                         const float cb = cl * wz[b];
@@ -245,7 +248,7 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
                     float wx[4], wz[4];
                     keys_weights(tx, wx);
                     keys_weights(tz, wz);
-                    const float cm = pick_c(cc, m);
+                    const float cm = rayc[m * T + r];
                     const bool away = !(unit_fraction(tx) && unit_fraction(tz));
                     const float cmerge = away ? 0.0f : cm;
 #pragma unroll
@@ -271,13 +274,13 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
                 nq -= 32;
                 const int ent = fq[warp][nq + lane];
                 __syncwarp();
-                run_queued(g, ent, acci, rays, T, rayc, rayb);
+                run_queued<DUAL>(g, rg, ent, acci, rays, T, rayc, rayb);
             }
             r += dr;
             k += dk;
             if (k >= npts) { k -= npts; ++r; }
         }
-        if (lane < nq) run_queued(g, fq[warp][lane], acci, rays, T, rayc, rayb);   // last partial batch
+        if (lane < nq) run_queued<DUAL>(g, rg, fq[warp][lane], acci, rays, T, rayc, rayb);   // last partial batch
         blk = s_blk;
         __syncthreads();                             // table and queue free for the next block
         if (++since_flush == kBlocksPerFlush || blk >= nblk) {
@@ -397,7 +400,10 @@ static size_t ray_grid_bytes(const RayGrid &rg, bool dual)
 }
 
 // ray-adjoint launch shape of a plan: the two-copy layout when it fits in
-// shared memory (16 warps, one CTA per SM), else one odd-pitch copy (8 warps)
+// shared memory, one CTA per SM, with 24 warps when the CTA's item tables fit
+// beside the two copies (more warps hide the shared-memory atomics: 0.80 ms
+// against 0.83 ms with 16 warps on a 128 x 128 grid), else 16 warps; otherwise
+// one odd-pitch copy (8 warps)
 RayAdjShape rayadj_shape(int nx, int nz, int pitch, int sm_count)
 {
     RayAdjShape sh;
@@ -408,9 +414,24 @@ RayAdjShape rayadj_shape(int nx, int nz, int pitch, int sm_count)
     sh.threads = sh.dual ? 512 : 256;
     int n = 0;
     if (sh.dual) {
-        cudaFuncSetAttribute(ray_adjoint_kernel<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kRayDualMaxBytes);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ray_adjoint_kernel<16, true>, 512, sh.smem);
+        int dev = 0, optin = 0;
+        cudaFuncAttributes a24{};
+        const bool known = cudaGetDevice(&dev) == cudaSuccess &&
+                           cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) ==
+                               cudaSuccess &&
+                           cudaFuncGetAttributes(&a24, ray_adjoint_kernel<24, true>) == cudaSuccess;
+        // 1 KB kept free for the per-CTA reservation
+        if (known && a24.sharedSizeBytes + sh.smem + 1024 <= (size_t)optin &&
+            cudaFuncSetAttribute(ray_adjoint_kernel<24, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)a24.sharedSizeBytes - 1024) == cudaSuccess) {
+            sh.threads = 768;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ray_adjoint_kernel<24, true>, 768, sh.smem);
+        } else {
+            cudaGetLastError();
+            cudaFuncSetAttribute(ray_adjoint_kernel<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kRayDualMaxBytes);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ray_adjoint_kernel<16, true>, 512, sh.smem);
+        }
     } else {
         // the attribute is per function, shared by every plan: set it to the largest
         // grid any plan may use, the occupancy query uses this plan's size
@@ -428,7 +449,10 @@ cudaError_t launch_ray_adjoint(af_plan_t pl, const float *s, float *grad)
     if ((long)pl->g.ne * pl->g.npix > 0) {
         const RayAdjShape &sh = pl->rayadj;
         const RayGrid rg = ray_grid_layout(pl->g.nx, pl->g.nz, sh.dual, pl->g.pitch);
-        if (sh.dual)
+        if (sh.dual && sh.threads == 768)
+            ray_adjoint_kernel<24, true><<<sh.blocks, 768, sh.smem, pl->stream>>>(
+                pl->g, rg, pl->elem, pl->pix, pl->phi, pl->gdel, pl->scal, pl->gpad, pl->gpart);
+        else if (sh.dual)
             ray_adjoint_kernel<16, true><<<sh.blocks, 512, sh.smem, pl->stream>>>(
                 pl->g, rg, pl->elem, pl->pix, pl->phi, pl->gdel, pl->scal, pl->gpad, pl->gpart);
         else
