@@ -167,17 +167,17 @@ def run_reference(args, rank, world):
 # capture of the full workload (second iteration), per kernel; None once the kernel
 # changed after the capture (see profiles/).  The adjoint stages' traffic follows
 # the CMPE mask of the captured iteration.
-NCU_TRAFFIC = {"das_forward": 743.3e6 + 65.6e6, "das_adjoint": 293.2e6 + 18.4e6,
-               "ray_adjoint": 26.2e6 + 1.9e6, "delays": 15.6e6 + 23.4e6}
+NCU_TRAFFIC = {"das_forward": 613.5e6 + 86.1e6, "das_adjoint": 285.5e6 + 16.5e6,
+               "ray_adjoint": 26.2e6 + 1.7e6, "delays": 15.9e6 + 23.9e6}
 
 # algorithmic FP32 lane-operations per unit, from the arithmetic of the method.
 # Ray point: position (2) + cell and fraction (4) + two Keys weight sets (2 x 10) + 16
-# taps and 4 row combinations (20), plus a 4-op compensated sum in the forward ray sum.
+# taps and 4 row combinations (20), plus the addition into the ray sum in the forward.
 # Gather (one live (transmit, receiver, pixel) triple): delay and fraction add with
 # carry (3) + 2 sample loads + complex lerp (4) + receive phasor and accumulate (4) = 13
 # forward; the adjoint adds the slope terms (2), the weight conj(G) P_t P_r (4), the
 # real part (2) and the two accumulations (2) = 23.
-OPS_PER_POINT = {"delays": 50, "ray_adjoint": 46}
+OPS_PER_POINT = {"delays": 47, "ray_adjoint": 46}
 
 # library kernels launched by one call of each timed stage (the DAS adjoint stage also
 # issues one memset of dL/dT, which is not a kernel of ours)

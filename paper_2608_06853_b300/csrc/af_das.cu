@@ -29,6 +29,15 @@ template <> struct Sample<AF_IQ_F16> {
 
 constexpr int kWarps = 8;   // warps per CTA; warp w takes receive blocks w, w + 8, ...
 
+// Forward launch per sample type: CTAs of 256 per SM and transmit-loop unroll,
+// measured on the 128-element workload (forward ms):
+//   complex64: 2 CTAs, unroll 2: 0.64; 3 CTAs, unroll 2: 0.70; 4 CTAs, none: 0.61
+//   bf16:      2 CTAs, unroll 2: 0.65; 3 CTAs, none: 0.52;     4 CTAs, none: 0.93
+//   f16:       2 CTAs, unroll 2: 0.64; 3 CTAs, none: 0.65;     4 CTAs, none: 1.06
+template <int DT> struct FwdLaunch { static constexpr int kMinBlocks = 2, kUnroll = 2; };
+template <> struct FwdLaunch<AF_IQ_C64> { static constexpr int kMinBlocks = 4, kUnroll = 1; };
+template <> struct FwdLaunch<AF_IQ_BF16> { static constexpr int kMinBlocks = 3, kUnroll = 1; };
+
 // Gather of one transmit for the W receivers held by a lane: all 2W loads are
 // issued before any is used, so a warp keeps 2W loads in flight.  CHECK: the
 // indices are clamped into the trace and out-of-range samples get weight 0;
@@ -132,7 +141,7 @@ __device__ __forceinline__ void das_forward_blocks(const AfGeom &g, const typena
     float4 dnext = D[p];
     for (int i = 0; i < g.nsub; ++i) {
         float ar = 0.0f, ai = 0.0f;
-#pragma unroll 1
+#pragma unroll(FwdLaunch<DT>::kUnroll)
         for (int tt = 0; tt < W; ++tt) {
             const int t = i * W + tt;
             const float4 dt = dnext;
@@ -154,15 +163,13 @@ __device__ __forceinline__ void das_forward_blocks(const AfGeom &g, const typena
 // consecutive pixels, about three laterally adjacent patches), all with the
 // same receive block j = blockIdx.y.  The warps walk the transmits in the same
 // order, so the trace windows one warp pulls into L1 serve the other seven.
-// The gathers are latency bound: 4 CTAs of 256 per SM (64 registers) keep more
-// loads in flight than 2 CTAs with the transmit loop unrolled by two (0.61 ms
-// against 0.64 ms on the 128-element workload, although the complex64 variant
-// spills a few registers).
+// The gathers are latency bound; the CTAs per SM and the unroll of the transmit
+// loop are chosen per sample type (FwdLaunch).
 // A warp whose receive block is outside the aperture for all its pixels only
 // writes zeros; a warp whose pixels' samples all lie in the trace runs the
 // gathers without range checks.
 template <int W, int DT>
-__global__ void __launch_bounds__(256, 4) das_forward_kernel(AfGeom g, const void *__restrict__ iq,
+__global__ void __launch_bounds__(256, FwdLaunch<DT>::kMinBlocks) das_forward_kernel(AfGeom g, const void *__restrict__ iq,
                                                              const float *__restrict__ scale,
                                                              const float4 *__restrict__ D,
                                                              const int2 *__restrict__ nrange,
