@@ -28,6 +28,10 @@ template <> struct Sample<AF_IQ_F16> {
 };
 
 constexpr int kWarps = 8;   // warps per CTA; warp w takes receive blocks w, w + 8, ...
+// The adjoint's CTAs hold 4 warps (4 CTAs per SM): a warp whose transmit blocks
+// all have a zero image gradient finishes at once, and a small CTA hands its
+// slot on sooner (0.30 ms against 0.33 ms with 8-warp CTAs, 128 elements).
+constexpr int kAdjWarps = 4;
 
 // Forward launch per sample type: CTAs of 256 per SM and transmit-loop unroll,
 // measured on the 128-element workload (forward ms):
@@ -195,8 +199,8 @@ __global__ void __launch_bounds__(256, FwdLaunch<DT>::kMinBlocks) das_forward_ke
         das_forward_blocks<W, DT, true>(g, psi, scale, D, B, j, p, nr, fr, pr);
 }
 
-// Adjoint: same CTA shape as the forward (8 neighbouring pixel tiles, one
-// receive block j = blockIdx.y).  For one gather dL/dtau =
+// Adjoint: CTAs of kAdjWarps neighbouring pixel tiles with one receive block
+// j = blockIdx.y.  For one gather dL/dtau =
 // Re(conj(G) exp(j 2 pi fd tau) (fs dPsi/du + j 2 pi fd Psi(u))); it is added to
 // dL/dT_t and dL/dT_r.  A lane sums the transmit role over its block's W
 // receivers and the receive role over all transmits, then adds both into the
@@ -266,7 +270,7 @@ __device__ __forceinline__ void das_adjoint_blocks(const AfGeom &g, const typena
 }
 
 template <int W, int DT>
-__global__ void __launch_bounds__(256, 2) das_adjoint_kernel(AfGeom g, const void *__restrict__ iq,
+__global__ void __launch_bounds__(32 * kAdjWarps, 4) das_adjoint_kernel(AfGeom g, const void *__restrict__ iq,
                                                              const float *__restrict__ scale,
                                                              const float4 *__restrict__ D,
                                                              const int2 *__restrict__ nrange,
@@ -274,7 +278,7 @@ __global__ void __launch_bounds__(256, 2) das_adjoint_kernel(AfGeom g, const voi
                                                              float *__restrict__ gdel)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int p = (blockIdx.x * kWarps + warp) * 32 + lane;
+    const int p = (blockIdx.x * kAdjWarps + warp) * 32 + lane;
     const int j = blockIdx.y;
     if (p >= g.npix) return;
     const typename Sample<DT>::T *psi = reinterpret_cast<const typename Sample<DT>::T *>(iq);
@@ -324,8 +328,8 @@ cudaError_t launch_adj_t(af_plan_t pl)
     const long n = (long)pl->g.ne * pl->g.npix;
     cudaError_t e = cudaMemsetAsync(pl->gdel, 0, n * sizeof(float), pl->stream);
     if (e != cudaSuccess) return e;
-    const dim3 blocks((pl->g.npix + 32 * kWarps - 1) / (32 * kWarps), pl->g.nsub);
-    das_adjoint_kernel<W, DT><<<blocks, 32 * kWarps, 0, pl->stream>>>(pl->g, pl->iq, pl->iq_scale, pl->D,
+    const dim3 blocks((pl->g.npix + 32 * kAdjWarps - 1) / (32 * kAdjWarps), pl->g.nsub);
+    das_adjoint_kernel<W, DT><<<blocks, 32 * kAdjWarps, 0, pl->stream>>>(pl->g, pl->iq, pl->iq_scale, pl->D,
                                                                        pl->nrange, pl->G, pl->gdel);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

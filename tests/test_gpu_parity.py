@@ -262,6 +262,26 @@ def test_large_grid_fallback_layouts():
     assert rel_l2(run.dLds, ray) <= 1e-4
 
 
+@pytest.mark.parametrize("nx,nz", [(128, 128), (128, 136)])
+def test_ray_adjoint_launch_shapes(nx, nz):
+    """The ray adjoint's two-copy layouts against the oracle. On a 128 x 128 grid
+    the two copies (165 KB) leave room for the 24-warp CTA's item tables. On a
+    128 x 136 grid (179 KB) they do not, and the 16-warp CTA runs. The 128-wide
+    grids also take the delay kernel's compile-time pitch. The regularisers are off,
+    so that dL/ds is the ray part alone."""
+    p = ray_only(synth.config_tiny(n_ang=4, n_rad=4, patch_w=5, nx=nx, nz=nz))
+    psi = synth.simulate(p, 600, seed=23)
+    s = smooth_speed(p, 8)
+    run = Run(p, psi, s)
+    o = oracle.Oracle(p)
+    T, _, _ = o.delays(s.astype(np.float64), apod_in=run.apod)
+    on = run.apod == 1
+    assert np.abs(run.T - T)[on].max() <= DELAY_TOL
+    ray = o.ray_adjoint(s.astype(np.float64), run.phi, run.apod, run.gdel)
+    assert np.linalg.norm(ray) > 0
+    assert rel_l2(run.dLds, ray) <= 1e-4
+
+
 def test_degenerate_cases():
     """No patches: loss and gradient are the regulariser's; < 3 subapertures: no CMPE terms."""
     base = synth.config_tiny(n_ang=2, n_rad=2, patch_w=3)
