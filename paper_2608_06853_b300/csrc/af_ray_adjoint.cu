@@ -230,12 +230,17 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
                 {
                     float wx[4], wz[4];
                     ray_stencil(g, kf, rays[kLeadRay * T + r], i0, j0, fx0, fz0, wx, wz);
+                    // rank-1 stencil rows on the packed FP32 pipe: one paired FMA is two
+                    // round-to-nearest FMAs, so W is the same as with scalar fmaf
                     const float cl = rayc[kLeadRay * T + r];
+                    const float2 x01 = make_float2(wx[0], wx[1]), x23 = make_float2(wx[2], wx[3]);
+                    const float2 kR = make_float2(kRound, kRound);
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
                         const float cb = cl * wz[b];
-#pragma unroll
-                        for (int a = 0; a < 4; ++a) W[b * 4 + a] = fmaf(cb, wx[a], kRound);
+                        const float2 c2 = make_float2(cb, cb);
+                        const float2 lo = __ffma2_rn(c2, x01, kR), hi = __ffma2_rn(c2, x23, kR);
+                        W[b * 4 + 0] = lo.x; W[b * 4 + 1] = lo.y; W[b * 4 + 2] = hi.x; W[b * 4 + 3] = hi.y;
                     }
                 }
 #pragma unroll
@@ -251,11 +256,14 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
                     const float cm = rayc[m * T + r];
                     const bool away = !(unit_fraction(tx) && unit_fraction(tz));
                     const float cmerge = away ? 0.0f : cm;
+                    const float2 x01 = make_float2(wx[0], wx[1]), x23 = make_float2(wx[2], wx[3]);
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
                         const float cb = cmerge * wz[b];
-#pragma unroll
-                        for (int a = 0; a < 4; ++a) W[b * 4 + a] = fmaf(cb, wx[a], W[b * 4 + a]);
+                        const float2 c2 = make_float2(cb, cb);
+                        const float2 lo = __ffma2_rn(c2, x01, make_float2(W[b * 4 + 0], W[b * 4 + 1]));
+                        const float2 hi = __ffma2_rn(c2, x23, make_float2(W[b * 4 + 2], W[b * 4 + 3]));
+                        W[b * 4 + 0] = lo.x; W[b * 4 + 1] = lo.y; W[b * 4 + 2] = hi.x; W[b * 4 + 3] = hi.y;
                     }
                     apart[m] = away && cm != 0.0f;
                 }

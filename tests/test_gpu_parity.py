@@ -192,12 +192,18 @@ def test_adam_step_parity(tiny_case):
 
 def test_ragged_and_variant_shapes():
     """Pixel count not a multiple of 32, no lens, sub_width 2 and 8, printed Eq. 4; one
-    CTA's pixels spread over the whole depth range; an odd trace length; the Eq. 6
-    conventional lens model and non-zero t_ttp / t0."""
+    CTA's pixels spread over the whole depth range; an odd trace length; samples
+    outside the trace for some pixels; the Eq. 6 conventional lens model and non-zero
+    t_ttp / t0."""
     cases = [
         dict(n_ang=3, n_rad=3, patch_w=3),                      # 81 pixels
         dict(n_ang=1, n_rad=8, patch_w=5),                      # 200 pixels over 8-50 mm depth
         dict(n_ang=3, n_rad=3, patch_w=3, ns=1023),             # 1023 samples per trace
+        # a third of the pixels need samples past the end of a 600-sample trace, or
+        # (first sample at 20 us) before its start: their warps gather with range
+        # checks, the others without
+        dict(n_ang=3, n_rad=3, patch_w=3, ns=600),
+        dict(n_ang=3, n_rad=3, patch_w=3, t0=2.0e-5),
         # Eq. 6 conventional model: straight rays from the elements plus one scalar
         # offset (lens correction + envelope peak) on every round trip; and the
         # bent-ray model with an envelope offset and a late first sample
