@@ -168,7 +168,7 @@ def run_reference(args, rank, world):
 # changed after the capture (see profiles/).  The adjoint stages' traffic follows
 # the CMPE mask of the captured iteration.
 NCU_TRAFFIC = {"das_forward": 613.5e6 + 86.1e6, "das_adjoint": 286.8e6 + 17.0e6,
-               "ray_adjoint": 26.2e6 + 1.9e6, "delays": 15.9e6 + 23.9e6}
+               "ray_adjoint": 26.2e6 + 1.9e6, "delays": 15.9e6 + 23.7e6}
 
 # algorithmic FP32 lane-operations per unit, from the arithmetic of the method.
 # Ray point: position (2) + cell and fraction (4) + two Keys weight sets (2 x 10) + 16

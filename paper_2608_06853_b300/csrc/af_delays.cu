@@ -264,19 +264,21 @@ __global__ void __launch_bounds__(PAIRS ? 768 : 256) delays_kernel(AfGeom g, con
         auto ray_sum = [&](auto clamp) {
             // interpolated value at endpoint kf, added into the running partial sum
             auto point = [&](float kf, float part) {
-                const float gx = fmaf(kf, gdx, gx0), gz = fmaf(kf, gdz, gz0);
-                const float fx = floorf(gx), fz = floorf(gz);
+                // position, fractions and Keys weights of both axes as packed pairs
+                // (the same round-to-nearest steps as the scalar forms)
+                const float2 gg = __ffma2_rn(make_float2(kf, kf), make_float2(gdx, gdz), make_float2(gx0, gz0));
+                const float fx = floorf(gg.x), fz = floorf(gg.y);
                 int i0 = (int)fx, j0 = (int)fz;
                 if (decltype(clamp)::value) {
                     i0 = min(max(i0, -1), g.nx - 1);
                     j0 = min(max(j0, -1), g.nz - 1);
                 }
-                float wx[4], wz[4];
-                keys_weights(gx - fx, wx);
-                keys_weights(gz - fz, wz);
+                float2 w[4];
+                keys_weights2(__ffma2_rn(make_float2(fx, fz), make_float2(-1.0f, -1.0f), gg), w);
+                const float wx[4] = {w[0].x, w[1].x, w[2].x, w[3].x};
                 const int row = (j0 + 1) * P + (i0 + 1);           // padded node (i0-1, j0-1)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) part = fmaf(wz[b], GridTaps<PAIRS>::row(sm, row + b * P, wx), part);
+                for (int b = 0; b < 4; ++b) part = fmaf(w[b].y, GridTaps<PAIRS>::row(sm, row + b * P, wx), part);
                 return part;
             };
             float kf = 0.0f;

@@ -203,6 +203,19 @@ __device__ __forceinline__ void keys_weights(float t, float w[4])
     w[2] = (1.0f - m) - w[1];
 }
 
+// Keys weights of the two axes at once on the packed FP32 pipe: w[a] = (wx[a],
+// wz[a]) for t = (tx, tz), the same round-to-nearest steps as keys_weights
+__device__ __forceinline__ void keys_weights2(float2 t, float2 (&w)[4])
+{
+    const float2 one = make_float2(1.0f, 1.0f), neg = make_float2(-1.0f, -1.0f);
+    const float2 u = __ffma2_rn(neg, t, one);
+    const float2 m = __fmul2_rn(__fmul2_rn(make_float2(-0.5f, -0.5f), t), u);
+    w[0] = __fmul2_rn(m, u);
+    w[3] = __fmul2_rn(m, t);
+    w[1] = __ffma2_rn(__fmul2_rn(t, t), __ffma2_rn(make_float2(1.5f, 1.5f), t, make_float2(-2.5f, -2.5f)), one);
+    w[2] = __ffma2_rn(neg, w[1], __ffma2_rn(neg, m, one));
+}
+
 // records the message returned by af_last_error() and returns st
 af_status af_set_error(af_status st, const char *fmt, ...);
 
