@@ -27,20 +27,21 @@ template <> struct Sample<AF_IQ_F16> {
     static __device__ __forceinline__ float2 load(const T *p) { return __half22float2(__ldg(p)); }
 };
 
-constexpr int kWarps = 8;   // warps per CTA; warp w takes receive blocks w, w + 8, ...
 // The adjoint's CTAs hold 4 warps (4 CTAs per SM): a warp whose transmit blocks
 // all have a zero image gradient finishes at once, and a small CTA hands its
 // slot on sooner (0.30 ms against 0.33 ms with 8-warp CTAs, 128 elements).
 constexpr int kAdjWarps = 4;
 
-// Forward launch per sample type: CTAs of 256 per SM and transmit-loop unroll,
-// measured on the 128-element workload (forward ms):
-//   complex64: 2 CTAs, unroll 2: 0.64; 3 CTAs, unroll 2: 0.70; 4 CTAs, none: 0.61
+// Forward launch per sample type: warps per CTA, CTAs per SM and transmit-loop
+// unroll, measured on the 128-element workload (forward ms; 8-warp CTAs unless
+// stated):
+//   complex64: 2 CTAs, unroll 2: 0.64; 3 CTAs, unroll 2: 0.70; 4 CTAs, none: 0.61;
+//              4-warp CTAs, 8 per SM, none: 0.59
 //   bf16:      2 CTAs, unroll 2: 0.65; 3 CTAs, none: 0.52;     4 CTAs, none: 0.93
 //   f16:       2 CTAs, unroll 2: 0.64; 3 CTAs, none: 0.65;     4 CTAs, none: 1.06
-template <int DT> struct FwdLaunch { static constexpr int kMinBlocks = 2, kUnroll = 2; };
-template <> struct FwdLaunch<AF_IQ_C64> { static constexpr int kMinBlocks = 4, kUnroll = 1; };
-template <> struct FwdLaunch<AF_IQ_BF16> { static constexpr int kMinBlocks = 3, kUnroll = 1; };
+template <int DT> struct FwdLaunch { static constexpr int kWarps = 8, kMinBlocks = 2, kUnroll = 2; };
+template <> struct FwdLaunch<AF_IQ_C64> { static constexpr int kWarps = 4, kMinBlocks = 8, kUnroll = 1; };
+template <> struct FwdLaunch<AF_IQ_BF16> { static constexpr int kWarps = 8, kMinBlocks = 3, kUnroll = 1; };
 
 // Gather of one transmit for the W receivers held by a lane: all 2W loads are
 // issued before any is used, so a warp keeps 2W loads in flight.  CHECK: the
@@ -163,24 +164,25 @@ __device__ __forceinline__ void das_forward_blocks(const AfGeom &g, const typena
     }
 }
 
-// Forward: CTA = 8 warps on 8 neighbouring tiles of 32 pixels (256
-// consecutive pixels, about three laterally adjacent patches), all with the
-// same receive block j = blockIdx.y.  The warps walk the transmits in the same
-// order, so the trace windows one warp pulls into L1 serve the other seven.
-// The gathers are latency bound; the CTAs per SM and the unroll of the transmit
-// loop are chosen per sample type (FwdLaunch).
+// Forward: CTA = 4 or 8 warps on as many neighbouring tiles of 32 pixels (128 or
+// 256 consecutive pixels, one to three laterally adjacent patches), all with
+// the same receive block j = blockIdx.y.  The warps walk the transmits in the
+// same order, so the trace windows one warp pulls into L1 serve the others.
+// The gathers are latency bound; the CTA size, the CTAs per SM and the unroll
+// of the transmit loop are chosen per sample type (FwdLaunch).
 // A warp whose receive block is outside the aperture for all its pixels only
 // writes zeros; a warp whose pixels' samples all lie in the trace runs the
 // gathers without range checks.
 template <int W, int DT>
-__global__ void __launch_bounds__(256, FwdLaunch<DT>::kMinBlocks) das_forward_kernel(AfGeom g, const void *__restrict__ iq,
+__global__ void __launch_bounds__(32 * FwdLaunch<DT>::kWarps, FwdLaunch<DT>::kMinBlocks)
+    das_forward_kernel(AfGeom g, const void *__restrict__ iq,
                                                              const float *__restrict__ scale,
                                                              const float4 *__restrict__ D,
                                                              const int2 *__restrict__ nrange,
                                                              float2 *__restrict__ B)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int p = (blockIdx.x * kWarps + warp) * 32 + lane;
+    const int p = (blockIdx.x * FwdLaunch<DT>::kWarps + warp) * 32 + lane;
     const int j = blockIdx.y;
     if (p >= g.npix) return;
     const typename Sample<DT>::T *psi = reinterpret_cast<const typename Sample<DT>::T *>(iq);
@@ -316,8 +318,9 @@ __global__ void __launch_bounds__(256) gdel_max_kernel(const float *__restrict__
 template <int W, int DT>
 cudaError_t launch_fwd_t(af_plan_t pl)
 {
-    const dim3 blocks((pl->g.npix + 32 * kWarps - 1) / (32 * kWarps), pl->g.nsub);
-    das_forward_kernel<W, DT><<<blocks, 32 * kWarps, 0, pl->stream>>>(
+    constexpr int kW = FwdLaunch<DT>::kWarps;
+    const dim3 blocks((pl->g.npix + 32 * kW - 1) / (32 * kW), pl->g.nsub);
+    das_forward_kernel<W, DT><<<blocks, 32 * kW, 0, pl->stream>>>(
         pl->g, pl->iq, pl->iq_scale, pl->D, pl->nrange, pl->B);
     return cudaGetLastError();
 }
