@@ -167,7 +167,7 @@ def run_reference(args, rank, world):
 # capture of the full workload (second iteration), per kernel; None once the kernel
 # changed after the capture (see profiles/).  The adjoint stages' traffic follows
 # the CMPE mask of the captured iteration.
-NCU_TRAFFIC = {"das_forward": None, "das_adjoint": 286.8e6 + 17.0e6,
+NCU_TRAFFIC = {"das_forward": 617.4e6 + 85.0e6, "das_adjoint": 286.8e6 + 17.0e6,
                "ray_adjoint": 26.2e6 + 1.9e6, "delays": 15.9e6 + 23.7e6}
 
 # algorithmic FP32 lane-operations per unit, from the arithmetic of the method.
