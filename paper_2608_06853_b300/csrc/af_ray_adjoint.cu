@@ -39,8 +39,9 @@ namespace {
 // max|dL/dT|.  Shared memory holds int32 (integer atomics are several times
 // faster than float ones); one ray adds at most max|dL/dT| (5 cell diagonals +
 // L/(N+1)) to a node and fix_scale is set on the host so that kRayFlushRays
-// rays stay below 2^30, so after kRayItemsPerFlush items the integer grids are
-// added into the CTA's int64 accumulator in global memory and cleared.  All
+// rays stay below 2^30, so after whole blocks of at most kRayItemsPerFlush items
+// the integer grids are added into the CTA's int64 accumulator in global memory
+// and cleared.  All
 // sums are integer sums up to the final conversion, so the result does not
 // depend on which CTA took which block.  Rounding adds 1.5 * 2^23 in the last
 // FMA of a value (|value| < 2^22), so each partial sum is rounded to an integer.
