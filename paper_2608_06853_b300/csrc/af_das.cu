@@ -37,11 +37,13 @@ constexpr int kAdjWarps = 4;
 // stated):
 //   complex64: 2 CTAs, unroll 2: 0.64; 3 CTAs, unroll 2: 0.70; 4 CTAs, none: 0.61;
 //              4-warp CTAs, 8 per SM, none: 0.59
-//   bf16:      2 CTAs, unroll 2: 0.65; 3 CTAs, none: 0.52;     4 CTAs, none: 0.93
-//   f16:       2 CTAs, unroll 2: 0.64; 3 CTAs, none: 0.65;     4 CTAs, none: 1.06
-template <int DT> struct FwdLaunch { static constexpr int kWarps = 8, kMinBlocks = 2, kUnroll = 2; };
+//   bf16:      2 CTAs, unroll 2: 0.65; 3 CTAs, none: 0.52;     4 CTAs, none: 0.93;
+//              4-warp CTAs, 6 per SM, none: 0.50
+//   f16:       2 CTAs, unroll 2: 0.64; 3 CTAs, none: 0.65;     4 CTAs, none: 1.06;
+//              4-warp CTAs, 4 per SM, unroll 2: 0.55
+template <int DT> struct FwdLaunch { static constexpr int kWarps = 4, kMinBlocks = 4, kUnroll = 2; };
 template <> struct FwdLaunch<AF_IQ_C64> { static constexpr int kWarps = 4, kMinBlocks = 8, kUnroll = 1; };
-template <> struct FwdLaunch<AF_IQ_BF16> { static constexpr int kWarps = 8, kMinBlocks = 3, kUnroll = 1; };
+template <> struct FwdLaunch<AF_IQ_BF16> { static constexpr int kWarps = 4, kMinBlocks = 6, kUnroll = 1; };
 
 // Gather of one transmit for the W receivers held by a lane: all 2W loads are
 // issued before any is used, so a warp keeps 2W loads in flight.  CHECK: the
