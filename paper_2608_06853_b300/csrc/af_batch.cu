@@ -53,19 +53,24 @@ af_status check_args(const af_batch_s *b, const BatchArgs &a)
     return AF_OK;
 }
 
-// one iteration of every member, forked from `origin` and joined back to it
+// one iteration of every member, forked from `origin` and joined back to it;
+// when a member fails, the members issued so far (the failing one included,
+// which may have enqueued part of its work) are still joined, so later work on
+// `origin` stays ordered after everything this call enqueued
 af_status issue(af_batch_s *b, cudaStream_t origin, const BatchArgs &a, int step)
 {
     BT_CHECK(cudaEventRecord(b->fork, origin));
-    for (int k = 0; k < b->n; ++k) {
+    af_status st = AF_OK;
+    int issued = 0;
+    for (int k = 0; k < b->n && st == AF_OK; ++k) {
         BT_CHECK(cudaStreamWaitEvent(b->streams[k], b->fork, 0));
-        const af_status st = af_iterate(b->plans[k], a.iq[k], a.scale ? a.scale[k] : nullptr, a.s[k], a.grad[k],
-                                        a.m[k], a.v[k], step, a.loss[k]);
-        if (st != AF_OK) return st;
+        st = af_iterate(b->plans[k], a.iq[k], a.scale ? a.scale[k] : nullptr, a.s[k], a.grad[k], a.m[k], a.v[k],
+                        step, a.loss[k]);
         BT_CHECK(cudaEventRecord(b->done[k], b->streams[k]));
+        issued = k + 1;
     }
-    for (int k = 0; k < b->n; ++k) BT_CHECK(cudaStreamWaitEvent(origin, b->done[k], 0));
-    return AF_OK;
+    for (int k = 0; k < issued; ++k) BT_CHECK(cudaStreamWaitEvent(origin, b->done[k], 0));
+    return st;
 }
 
 void release(af_batch_s *b)
