@@ -186,12 +186,15 @@ KERNELS_PER_STAGE = {"grid_stats": 2, "delays": 1, "das_forward": 1, "cmpe_forwa
 OPS_PER_GATHER = {"das_forward": 13, "das_adjoint": 23}
 
 
-def stage_roofline(stage, ms, launches, p, iq_bytes, pk, gathers):
+def stage_roofline(stage, ms, launches, p, iq_bytes, pk, units):
     """Roofline entry of one stage: algorithmic lane operations per launch divided by
     its average launch time, against the FP32 lane rate (the binding roofline of every
     stage of this path: the channel data is read once per pass, 805 MB per iteration,
-    far below what HBM moves in the time the arithmetic takes).  The delay-and-sum
-    stages also carry their algorithmic HBM bytes against the measured copy peak."""
+    far below what HBM moves in the time the arithmetic takes).  `units` are the live
+    units one launch processes: gathers for the delay-and-sum stages, rays (of
+    nseg + 1 points) for the ray stages.  The delay-and-sum stages also carry their
+    algorithmic HBM bytes against the measured copy peak."""
+    gathers = units
     ne, npix = p.ne, p.npix
     nb = p.nsub * p.nsub
     avg_s = ms / launches * 1e-3
@@ -201,7 +204,7 @@ def stage_roofline(stage, ms, launches, p, iq_bytes, pk, gathers):
     if stage in OPS_PER_GATHER:
         ops = gathers * OPS_PER_GATHER[stage]
     else:
-        ops = ne * npix * (p.nseg + 1) * OPS_PER_POINT.get(stage, 0)
+        ops = units * (p.nseg + 1) * OPS_PER_POINT.get(stage, 0)
     achieved = ops / avg_s / 1e12
     out = {"bound": "alu", "achieved": achieved, "peak": lanes / 1e12, "unit": "Tlane-op/s",
            "frac": achieved / (lanes / 1e12), "traffic": NCU_TRAFFIC.get(stage), "kernel": stage,
@@ -490,15 +493,20 @@ def run_ours(args, rank, world, local_rank):
     counters["numeric_ok"] = plan.af_sync_status() == af.AF_OK
     # live gathers (last timed iteration) of the forward: sum over pixels of (elements
     # that see the pixel)^2; of the adjoint: only those of images whose gradient is
-    # non-zero (it skips the rest, whose terms are exactly zero)
+    # non-zero (it skips the rest, whose terms are exactly zero).  Live rays: the
+    # delay kernel sums the rays of apodized-in pairs, the ray adjoint those whose
+    # dL/dT is non-zero.
     _, apod = plan.delays()
     G = plan.image_grad()
+    gdel = plan.delay_grad()
     stream.synchronize()
+    live_rays = {"delays": int(apod.sum().item()), "ray_adjoint": int((gdel != 0).sum().item())}
     n_blk = apod.view(p.nsub, p.sub_width, p.npix).sum(dim=1, dtype=torch.int64).double()
     nz = (G.view(p.nsub, p.nsub, p.npix) != 0).double()
     gathers = {"das_forward": int((n_blk.sum(dim=0) ** 2).sum().item()),
                "das_adjoint": int(torch.einsum("ijp,ip,jp->", nz, n_blk, n_blk).item())}
-    del apod, G, nz
+    del apod, G, nz, gdel
+    units = {**gathers, **live_rays}
     clk = clocks.stop() if clocks else None
     value, t_max = combine_ranks(ms * 1e-3, args.steps, world, dev)
     ms_max = t_max * 1e3
@@ -546,8 +554,8 @@ def run_ours(args, rank, world, local_rank):
     pk = peaks()
     ranked = sorted(((v_[0], k) for k, v_ in stages.items() if v_[1] > 0), reverse=True)
     dom = ranked[0][1]
-    roof = stage_roofline(dom, stages[dom][0], stages[dom][1], p, iq_bytes, pk, gathers.get(dom, 0))
-    stage_roof = {k: stage_roofline(k, v_[0], v_[1], p, iq_bytes, pk, gathers.get(k, 0))["frac"]
+    roof = stage_roofline(dom, stages[dom][0], stages[dom][1], p, iq_bytes, pk, units.get(dom, 0))
+    stage_roof = {k: stage_roofline(k, v_[0], v_[1], p, iq_bytes, pk, units.get(k, 0))["frac"]
                   for k, v_ in stages.items() if v_[1] > 0 and k in ("delays", "das_forward", "das_adjoint",
                                                                    "ray_adjoint")}
     # achieved HBM GB/s of the whole iteration by algorithmic bytes (channel data read twice)
@@ -567,6 +575,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof,
         "stage_alu_frac": stage_roof,
         "live_gathers": gathers,
+        "live_rays": live_rays,
         "loss": final_loss,
         "counters": counters,
         "clocks": clk,
