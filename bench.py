@@ -32,7 +32,7 @@ METRIC = "autofocus iterations/s (fwd+adjoint), 128×128-FSA; GB/s vs HBM peak; 
 WORKLOAD = ("128-element curvilinear FSA 128x128x3072 complex IQ at 14 MHz, 60 mm radius, 1.2 mm lens at "
             "1000 m/s, 128x128 slowness grid, 400 patches of 9x9 pixels, 64 ray segments, 3-layer medium")
 SEED = 20261203
-N_SCATTERERS = 150_000
+SPECKLE_PER_CELL = 10.0        # scatterers per resolution cell (lambda^2) of the workload
 
 
 def parse():
@@ -42,13 +42,18 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dtype", default="c64", choices=["c64", "bf16", "f16"])
-    ap.add_argument("--scatterers", type=int, default=N_SCATTERERS)
+    ap.add_argument("--scatterers", type=int, default=0,
+                    help="scatterers of the synthetic acquisition (default: 10 per resolution cell)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-jobs", type=int, default=2)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--variants", default="bf16,f16,surrogate,batch,sweep",
                     help="comma list of the variant runs: bf16, f16, surrogate (on the bf16 plan), "
                          "batch, sweep (sweep, images and metrics)")
+    ap.add_argument("--split", default="acquisitions", choices=["acquisitions", "patches"],
+                    help="N > 1: independent acquisitions per rank (weak scaling, default) or one "
+                         "acquisition's patches split over the ranks (strong scaling; two all-reduces "
+                         "per iteration)")
     ap.add_argument("--surrogate-samples", type=int, default=10_000_000)
     ap.add_argument("--batch-size", type=int, default=16)
     return ap.parse_args()
@@ -105,46 +110,64 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_sample(problem, psi, s, n_patches, seed=0):
+def oracle_sample(problem, psi, s, n_patches, seed=0, parallel=False):
     """One forward + adjoint + Adam step of the FP64 oracle on n_patches of the
-    workload's patches; returns (seconds, fraction of the per-iteration work)."""
+    workload's patches (all of them if n_patches >= n_patch); returns (seconds,
+    fraction of the per-iteration work).  parallel: the OpenMP build of the same
+    oracle source on all host cores, else the single-threaded build."""
     import dataclasses
 
     import oracle
-    rng = np.random.default_rng(seed)
-    patches = np.sort(rng.choice(problem.n_patch, n_patches, replace=False))
-    pix = np.concatenate([np.arange(P * problem.patch_npix, (P + 1) * problem.patch_npix) for P in patches])
-    sub = dataclasses.replace(problem, n_patch=len(patches), pix_x=problem.pix_x[pix], pix_z=problem.pix_z[pix])
-    o = oracle.Oracle(sub)
+    if n_patches >= problem.n_patch:
+        sub = problem
+        n_patches = problem.n_patch
+    else:
+        rng = np.random.default_rng(seed)
+        patches = np.sort(rng.choice(problem.n_patch, n_patches, replace=False))
+        pix = np.concatenate([np.arange(P * problem.patch_npix, (P + 1) * problem.patch_npix) for P in patches])
+        sub = dataclasses.replace(problem, n_patch=len(patches), pix_x=problem.pix_x[pix],
+                                  pix_z=problem.pix_z[pix])
+    o = oracle.Oracle(sub, parallel=parallel)
     sd = s.astype(np.float64)
     t0 = time.perf_counter()
     parts, g, _, _ = o.loss_grad(psi, sd)
-    o.adam(sd, g, np.zeros_like(sd), np.zeros_like(sd), 1, problem.lr)
+    o.adam(sd, g, np.zeros_like(sd), np.zeros_like(sd), 1, problem.lr, c_unit=problem.c_unit)
     dt = time.perf_counter() - t0
     return dt, n_patches / problem.n_patch
 
 
 def make_problem(rank: int, n_scat: int):
+    """The full-size workload and its seeded echoes (complex64 numpy array).  The echoes
+    are simulated by the input generator's GPU kernels when a GPU is present (about 7e5
+    scatterers at 10 per resolution cell), else by its host code."""
+    import torch
+
     import synth
     p = synth.config_full()
-    psi = synth.simulate(p, n_scat, seed=SEED + rank)
-    return p, psi
+    n = n_scat or synth.speckle_count(p, SPECKLE_PER_CELL)
+    if torch.cuda.is_available():
+        psi = synth.simulate_gpu(p, n, seed=SEED + rank).cpu().numpy()
+        torch.cuda.empty_cache()
+    else:
+        psi = synth.simulate(p, n, seed=SEED + rank)
+    return p, psi, n
 
 
 def run_reference(args, rank, world):
     """--impl reference: the oracle as it stands, on the host cores, rank 0 only."""
     if rank != 0:
         return
-    import synth
-    p, psi = make_problem(0, args.scatterers)
+    import oracle
+    p, psi, n_scat = make_problem(0, args.scatterers)
     s = p.initial_slowness()
-    n_patches = 4
+    n_patches = 20
+    cores = oracle.omp_threads()
     for _ in range(args.warmup):
-        oracle_sample(p, psi, s, n_patches)
+        oracle_sample(p, psi, s, n_patches, parallel=True)
     units = 0.0
     t_total = 0.0
     for k in range(args.steps):
-        dt, frac = oracle_sample(p, psi, s, n_patches, seed=k)
+        dt, frac = oracle_sample(p, psi, s, n_patches, seed=k, parallel=True)
         t_total += dt
         units += frac
     value = units / t_total
@@ -153,10 +176,10 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded speckle, 3-layer medium)",
-        "config": {"workload": WORKLOAD, "sample": f"{n_patches} of 400 patches per step"},
-        "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": 1, "kind": "oracle",
-                         "sample": f"one forward+adjoint+step on {n_patches} of 400 patches per step, "
-                                   "scaled by the pixel fraction"},
+        "config": {"workload": WORKLOAD, "scatterers": n_scat, "sample": f"{n_patches} of 400 patches per step"},
+        "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": cores, "kind": "oracle",
+                         "sample": f"one forward+adjoint+step on {n_patches} of 400 patches per step "
+                                   f"(OpenMP build of the oracle, {cores} threads), scaled by the pixel fraction"},
         "e2e": {"value": value, "unit": "iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -186,7 +209,16 @@ KERNELS_PER_STAGE = {"grid_stats": 2, "delays": 1, "das_forward": 1, "cmpe_forwa
 OPS_PER_GATHER = {"das_forward": 13, "das_adjoint": 23}
 
 
-def stage_roofline(stage, ms, launches, p, iq_bytes, pk, units):
+def lane_peak(sm_count: int, clk, pk):
+    """FP32 lane-operation rate: SMs (queried from the device) x 128 FP32 lanes x the SM
+    clock (median sampled under load during the timed region, else the maximum)."""
+    mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2032.0)
+    src = "median sampled during the timed region" if (clk or {}).get("sm_mhz") else "maximum SM clock"
+    return sm_count * 128 * mhz * 1e6, (f"derived: {sm_count} SMs (queried) x 128 FP32 lanes x {mhz:.0f} MHz "
+                                        f"({src}); not a measured FMA peak")
+
+
+def stage_roofline(stage, ms, launches, p, iq_bytes, pk, units, peak):
     """Roofline entry of one stage: algorithmic lane operations per launch divided by
     its average launch time, against the FP32 lane rate (the binding roofline of every
     stage of this path: the channel data is read once per pass, 805 MB per iteration,
@@ -199,8 +231,7 @@ def stage_roofline(stage, ms, launches, p, iq_bytes, pk, units):
     nb = p.nsub * p.nsub
     avg_s = ms / launches * 1e-3
     hbm = pk.get("hbm_gbs", 6400.0)
-    # FP32 lane-operation bound: SMs x 128 lanes x max SM clock (derived, not measured)
-    lanes = 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6
+    lanes, peak_source = peak
     if stage in OPS_PER_GATHER:
         ops = gathers * OPS_PER_GATHER[stage]
     else:
@@ -209,7 +240,7 @@ def stage_roofline(stage, ms, launches, p, iq_bytes, pk, units):
     out = {"bound": "alu", "achieved": achieved, "peak": lanes / 1e12, "unit": "Tlane-op/s",
            "frac": achieved / (lanes / 1e12), "traffic": NCU_TRAFFIC.get(stage), "kernel": stage,
            "algorithmic_ops": ops, "avg_launch_ms": ms / launches,
-           "peak_source": "derived: 148 SMs x 128 FP32 lanes x max SM clock"}
+           "peak_source": peak_source}
     if stage in OPS_PER_GATHER:
         # channel data once + one-way tables + images (dL/dB and dL/dT for the adjoint)
         bytes_ = iq_bytes + ne * npix * 16 + nb * npix * 8
@@ -224,17 +255,63 @@ def stage_roofline(stage, ms, launches, p, iq_bytes, pk, units):
 
 
 # ---------------------------------------------------------------- ranks
-def combine_ranks(seconds: float, units_per_rank: float, world: int, device=None):
+def combine_ranks(seconds: float, units_per_rank: float, world: int, device=None, independent: bool = True):
     """Whole-job throughput: units of all ranks / max over ranks of the timed seconds.
-    Each rank runs an independent acquisition (no data-path collective); the only
-    collective is this max of the timings."""
+    independent: each rank runs its own acquisition (no data-path collective; the only
+    collective is this max of the timings); else the ranks share one acquisition (patch
+    split) and the job's units are one rank's."""
     import torch
     t = torch.tensor([seconds], dtype=torch.float64, device=device)
     if world > 1:
         import torch.distributed as dist
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     t_max = float(t.item())
-    return world * units_per_rank / t_max, t_max
+    return (world if independent else 1) * units_per_rank / t_max, t_max
+
+
+# ---------------------------------------------------------------- FP64 reference
+def oracle_reference(p, psi, plan, iq, stream, dev):
+    """Timed FP64 oracle (OpenMP build of the oracle source, all host cores) of one whole
+    forward + adjoint + step at the initial map, with the float32 plan's apodization bits
+    and CMPE mask injected (the decisions taken in float; see the parity tests), plus the
+    oracle's images.  Returns the timing, the references and the float32 plan's errors."""
+    import torch
+
+    import oracle
+    s0 = p.initial_slowness()
+    with torch.cuda.stream(stream):
+        loss = torch.zeros(4, device=dev)
+        g = torch.zeros((p.nz, p.nx), device=dev)
+        plan.af_forward(iq, torch.from_numpy(s0).to(dev), loss)
+        plan.af_adjoint(g)
+        _, apod = plan.delays()
+        _, mask, _ = plan.cmpe()
+        B = plan.images()
+    stream.synchronize()
+    apod, mask = apod.cpu().numpy(), mask.cpu().numpy()
+    o = oracle.Oracle(p, parallel=True)
+    sd = s0.astype(np.float64)
+    t0 = time.perf_counter()
+    parts, grad, _, _ = o.loss_grad(psi, sd, apod_in=apod, mask_in=mask)
+    o.adam(sd, grad, np.zeros_like(sd), np.zeros_like(sd), 1, p.lr, c_unit=p.c_unit)
+    dt = time.perf_counter() - t0
+    T, _, _ = o.delays(sd, apod_in=apod)
+    B_or = o.das(psi, T, apod)
+    ref = {"seconds": dt, "cores": oracle.omp_threads(), "nproc": os.cpu_count(), "parts": parts,
+           "grad": grad, "B": B_or, "apod": apod, "mask": mask}
+    ref.update({"fp32_" + k: v for k, v in precision_errors(ref, loss, g, B).items()})
+    return ref
+
+
+def precision_errors(ref, loss, g, B):
+    """Errors of a GPU result against the FP64 oracle: images (relative L2), loss of
+    Eq. 12 (relative) and dL/ds (relative L2)."""
+    Bg = B.cpu().numpy().astype(np.complex128)
+    gg = g.cpu().numpy().astype(np.float64)
+    L = float(loss[0])
+    return {"image_rel_l2": float(np.linalg.norm(Bg - ref["B"]) / np.linalg.norm(ref["B"])),
+            "loss_rel": abs(L - ref["parts"][0]) / abs(ref["parts"][0]),
+            "grad_rel_l2": float(np.linalg.norm(gg - ref["grad"]) / np.linalg.norm(ref["grad"]))}
 
 
 # ---------------------------------------------------------------- variants
@@ -259,9 +336,10 @@ def _time_iterations(plan, iq, scale, p, stream, dev, steps, warmup):
     return ms, {k: v_[0] / max(v_[1], 1) for k, v_ in stages.items()}, loss.cpu().numpy().tolist()
 
 
-def run_variants(args, p, psi, plan32, iq32, stream, dev, ms32):
+def run_variants(args, p, psi, plan32, iq32, stream, dev, ms32, ref=None):
     """16-bit channel-data storage (per-transmit scale) and the lens surrogate + bf16 form,
-    each timed on the same workload, with their error against the float32 GPU result."""
+    each timed on the same workload, with their error against the float32 GPU result and,
+    when `ref` holds the FP64 oracle's result, against the oracle."""
     import torch
 
     import paper_2608_06853_b300 as af
@@ -301,6 +379,8 @@ def run_variants(args, p, psi, plan32, iq32, stream, dev, ms32):
                      "loss_rel_vs_fp32": float(abs(loss[0] - ref_loss[0]) / abs(ref_loss[0])),
                      "grad_rel_l2_vs_fp32": float((g - g32).norm() / g32.norm()),
                      "stage_ms": stages}
+        if ref is not None:
+            out[name]["vs_fp64_oracle"] = precision_errors(ref, loss, g, B)
     if "surrogate" in want:
         out["surrogate_bf16"] = run_surrogate(args, p, plans["bf16"], scale, s0, a32, T32, stream, dev)
     if "batch" in want:
@@ -401,8 +481,7 @@ def run_batch(args, dev, n_iter=100, n_scat=20_000):
     t0 = time.perf_counter()
     for k in range(args.batch_size):
         p = synth.config_batch_member(k)
-        psi = synth.simulate(p, n_scat, seed=SEED + 1000 + k)
-        r = torch.view_as_real(torch.from_numpy(psi).to(dev))
+        r = torch.view_as_real(synth.simulate_gpu(p, n_scat, seed=SEED + 1000 + k))
         sc = r.abs().amax(dim=(1, 2, 3)).clamp_min(1e-30).float().contiguous()
         iqs.append((r / sc[:, None, None, None]).to(torch.bfloat16).contiguous())
         scales.append(sc)
@@ -446,10 +525,19 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     if world > 1 and not dist.is_initialized():
         dist.init_process_group("nccl", device_id=dev)
-    p, psi = make_problem(rank, args.scatterers)
+    sharded = args.split == "patches" and world > 1
+    # patch split: every rank holds the same acquisition; else each its own
+    p, psi, n_scat = make_problem(0 if sharded else rank, args.scatterers)
     dtype = {"c64": af.AF_IQ_C64, "bf16": af.AF_IQ_BF16, "f16": af.AF_IQ_F16}[args.dtype]
     stream = torch.cuda.Stream(device=dev)
-    plan = af.Plan(p, iq_dtype=dtype, stream=stream)
+    if sharded:
+        from paper_2608_06853_b300.shard import ShardedPlan
+        splan = ShardedPlan(p, rank, world, iq_dtype=dtype, stream=stream)
+        plan = splan.plan
+        iterate = splan.iterate
+    else:
+        plan = af.Plan(p, iq_dtype=dtype, stream=stream)
+        iterate = plan.af_iterate
     with torch.cuda.stream(stream):
         x = torch.from_numpy(psi).to(dev)
         if dtype == af.AF_IQ_C64:
@@ -468,7 +556,7 @@ def run_ours(args, rank, world, local_rank):
         loss = torch.zeros(4, device=dev)
     stream.synchronize()
     for it in range(1, args.warmup + 1):
-        plan.af_iterate(iq, s, g, m, v, it, loss, scale)
+        iterate(iq, s, g, m, v, it, loss, scale)
     stream.synchronize()
 
     def barrier():
@@ -476,41 +564,54 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
 
     clocks = ClockSampler(local_rank) if rank == 0 else None
+    state0 = [x.clone() for x in (s, m, v)]        # for the untimed recount of live units
     plan.set_timing(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
     e0.record(stream)
     for it in range(args.warmup + 1, args.warmup + args.steps + 1):
-        plan.af_iterate(iq, s, g, m, v, it, loss, scale)
+        iterate(iq, s, g, m, v, it, loss, scale)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1)
     stages = plan.stage_times()
     plan.set_timing(False)
+    clk = clocks.stop() if clocks else None
+    final_loss = loss.cpu().numpy().tolist()
     counters = plan.counters()
     counters["numeric_ok"] = plan.af_sync_status() == af.AF_OK
-    # live gathers (last timed iteration) of the forward: sum over pixels of (elements
-    # that see the pixel)^2; of the adjoint: only those of images whose gradient is
-    # non-zero (it skips the rest, whose terms are exactly zero).  Live rays: the
-    # delay kernel sums the rays of apodized-in pairs, the ray adjoint those whose
-    # dL/dT is non-zero.
-    _, apod = plan.delays()
-    G = plan.image_grad()
-    gdel = plan.delay_grad()
-    stream.synchronize()
-    live_rays = {"delays": int(apod.sum().item()), "ray_adjoint": int((gdel != 0).sum().item())}
-    n_blk = apod.view(p.nsub, p.sub_width, p.npix).sum(dim=1, dtype=torch.int64).double()
-    nz = (G.view(p.nsub, p.nsub, p.npix) != 0).double()
-    gathers = {"das_forward": int((n_blk.sum(dim=0) ** 2).sum().item()),
-               "das_adjoint": int(torch.einsum("ijp,ip,jp->", nz, n_blk, n_blk).item())}
-    del apod, G, nz, gdel
-    units = {**gathers, **live_rays}
-    clk = clocks.stop() if clocks else None
-    value, t_max = combine_ranks(ms * 1e-3, args.steps, world, dev)
+    # Live units, averaged over the timed iterations: the same iterations are run again
+    # untimed from the saved state and counted after each.  Forward gathers: sum over
+    # pixels of (elements that see the pixel)^2; adjoint gathers: only those of images
+    # whose gradient is non-zero (the kernel skips the rest, whose terms are exactly
+    # zero).  Rays: the delay kernel sums those of apodized-in pairs, the ray adjoint
+    # those whose dL/dT is non-zero.
+    with torch.cuda.stream(stream):
+        for x, x0 in zip((s, m, v), state0):
+            x.copy_(x0)
+    acc = {"das_forward": 0, "das_adjoint": 0, "delays": 0, "ray_adjoint": 0}
+    for it in range(args.warmup + 1, args.warmup + args.steps + 1):
+        iterate(iq, s, g, m, v, it, loss, scale)
+        _, apod = plan.delays()
+        G = plan.image_grad()
+        gdel = plan.delay_grad()
+        stream.synchronize()
+        n_blk = apod.view(p.nsub, p.sub_width, p.npix).sum(dim=1, dtype=torch.int64).double()
+        nz = (G.view(p.nsub, p.nsub, p.npix) != 0).double()
+        acc["delays"] += int(apod.sum().item())
+        acc["ray_adjoint"] += int((gdel != 0).sum().item())
+        acc["das_forward"] += int((n_blk.sum(dim=0) ** 2).sum().item())
+        acc["das_adjoint"] += int(torch.einsum("ijp,ip,jp->", nz, n_blk, n_blk).item())
+        del apod, G, nz, gdel
+    units = {k: v_ / args.steps for k, v_ in acc.items()}
+    live_rays = {k: units[k] for k in ("delays", "ray_adjoint")}
+    gathers = {k: units[k] for k in ("das_forward", "das_adjoint")}
+    # whole-job throughput: all ranks' iterations (independent acquisitions), or the one
+    # acquisition's iterations (patch split)
+    value, t_max = combine_ranks(ms * 1e-3, args.steps, world, dev, independent=not sharded)
     ms_max = t_max * 1e3
-    final_loss = loss.cpu().numpy().tolist()
 
     # end to end: one autofocus job = upload of the acquisition and the initial map from
     # pinned host memory, N_i = 100 iterations, read back of the final map and loss
@@ -537,25 +638,34 @@ def run_ours(args, rank, world, local_rank):
             v.zero_()
         iq_arg = torch.view_as_complex(d_iq) if dtype == af.AF_IQ_C64 else d_iq
         for it in range(1, n_iter + 1):
-            plan.af_iterate(iq_arg, s, g, m, v, it, loss, d_scale)
+            iterate(iq_arg, s, g, m, v, it, loss, d_scale)
         with torch.cuda.stream(stream):
             h_out.copy_(s, non_blocking=True)
             h_loss.copy_(loss, non_blocking=True)
         stream.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_value, _ = combine_ranks(e2e_s, args.e2e_jobs * n_iter, world, dev) if args.e2e_jobs else (0.0, 0.0)
+    e2e_value, _ = (combine_ranks(e2e_s, args.e2e_jobs * n_iter, world, dev, independent=not sharded)
+                    if args.e2e_jobs else (0.0, 0.0))
+
+    # the FP64 oracle (OpenMP build, all host cores) on the whole iteration at the initial
+    # map, with the float32 plan's apodization and CMPE mask: the all-core CPU baseline and
+    # the reference of every dtype's error
+    ref = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and dtype == af.AF_IQ_C64:
+        ref = oracle_reference(p, psi, plan, iq, stream, dev)
 
     variants = None
-    if not args.no_variants and dtype == af.AF_IQ_C64:
-        variants = run_variants(args, p, psi, plan, iq, stream, dev, ms_max / args.steps)
+    if not args.no_variants and dtype == af.AF_IQ_C64 and not sharded:
+        variants = run_variants(args, p, psi, plan, iq, stream, dev, ms_max / args.steps, ref)
 
     if rank != 0:
         return
     pk = peaks()
+    peak = lane_peak(torch.cuda.get_device_properties(dev).multi_processor_count, clk, pk)
     ranked = sorted(((v_[0], k) for k, v_ in stages.items() if v_[1] > 0), reverse=True)
     dom = ranked[0][1]
-    roof = stage_roofline(dom, stages[dom][0], stages[dom][1], p, iq_bytes, pk, units.get(dom, 0))
-    stage_roof = {k: stage_roofline(k, v_[0], v_[1], p, iq_bytes, pk, units.get(k, 0))["frac"]
+    roof = stage_roofline(dom, stages[dom][0], stages[dom][1], p, iq_bytes, pk, units.get(dom, 0), peak)
+    stage_roof = {k: stage_roofline(k, v_[0], v_[1], p, iq_bytes, pk, units.get(k, 0), peak)["frac"]
                   for k, v_ in stages.items() if v_[1] > 0 and k in ("delays", "das_forward", "das_adjoint",
                                                                    "ray_adjoint")}
     # achieved HBM GB/s of the whole iteration by algorithmic bytes (channel data read twice)
@@ -563,12 +673,15 @@ def run_ours(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "strong" if sharded else "weak", "vs_baseline": None,
         "dtype": {"c64": "f32", "bf16": "bf16-storage/f32", "f16": "f16-storage/f32"}[args.dtype],
         "data": "synthetic (seeded speckle, 3-layer medium); inputs larger than L2, no flush",
-        "config": {"workload": WORKLOAD, "iq_dtype": args.dtype, "scatterers": args.scatterers,
+        "config": {"workload": WORKLOAD, "iq_dtype": args.dtype, "scatterers": n_scat,
+                   "speckle": f"{SPECKLE_PER_CELL:g} scatterers per resolution cell (lambda^2)",
                    "l2": "inputs larger than L2 (384 MiB channel data), no flush",
-                   "parallelism": f"independent acquisitions x{world}"},
+                   "parallelism": (f"one acquisition's patches over {world} ranks (all-reduce of the CMPE "
+                                   "totals and of dL/ds per iteration)") if sharded
+                   else f"independent acquisitions x{world}"},
         "gpu_launches": sum(v_[1] * KERNELS_PER_STAGE[k] for k, v_ in stages.items()),
         "stage_ms": {k: v_[0] / max(v_[1], 1) for k, v_ in stages.items()},
         "hbm_gbs_algorithmic": it_bytes / (ms_max / args.steps * 1e-3) / 1e9,
@@ -576,6 +689,7 @@ def run_ours(args, rank, world, local_rank):
         "stage_alu_frac": stage_roof,
         "live_gathers": gathers,
         "live_rays": live_rays,
+        "live_units_note": f"mean over the {args.steps} timed iterations (untimed recount)",
         "loss": final_loss,
         "counters": counters,
         "clocks": clk,
@@ -584,12 +698,17 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": int(d2h),
                 "step": f"one autofocus job: upload + {n_iter} iterations + read back"},
     }
-    if world == 1 and not args.no_cpu_baseline:
+    if ref is not None:
         n_patches = 40
         dt, frac = oracle_sample(p, psi, p.initial_slowness(), n_patches)
-        line["cpu_baseline"] = {"value": frac / dt, "unit": "iterations/s", "cores": 1, "kind": "oracle",
-                                "sample": f"one forward+adjoint+step on {n_patches} of 400 patches "
-                                          f"({100 * frac:.0f} % of pixels, {dt:.1f} s), scaled by the pixel fraction"}
+        line["cpu_baseline"] = {
+            "value": 1.0 / ref["seconds"], "unit": "iterations/s", "cores": ref["cores"], "kind": "oracle",
+            "sample": f"one whole forward+adjoint+step of the workload ({ref['seconds']:.1f} s) by the OpenMP "
+                      f"build of the oracle source on {ref['cores']} threads ({ref['nproc']} host cores)",
+            "single_thread": {"value": frac / dt, "unit": "iterations/s", "cores": 1,
+                              "sample": f"one forward+adjoint+step on {n_patches} of 400 patches "
+                                        f"({100 * frac:.0f} % of pixels, {dt:.1f} s), scaled by the pixel fraction"}}
+        line["error_vs_fp64_oracle"] = {k: v_ for k, v_ in ref.items() if k.startswith("fp32")}
     print(json.dumps(line), flush=True)
 
 

@@ -12,7 +12,7 @@
  *                (Sec. II-D) and Eq. 10-12 regularisation.
  *   af_adjoint : dL/ds by a hand-written adjoint of af_forward (Fig. 1g),
  *                exit points and masks held constant.
- *   af_step    : the Eq. 9 update, run as Adam on u = s * c_ref.
+ *   af_step    : the Eq. 9 update of the sound speed, run as Adam on c in km/s.
  *
  * Conventions shared by every entry point
  *  - Units are SI (m, s, s/m, Hz).  z grows into the tissue.
@@ -62,6 +62,10 @@ enum { AF_LENS_BENT_RAY = 0, /* Eq. 7-8: Fermat exit point on a curved lens surf
                                 conventional model of Eq. 6) */
        AF_LENS_PLANAR = 2 }; /* Eq. 7-8 with a flat lens (linear array) */
 
+/* update rule of af_step */
+enum { AF_OPT_ADAM = 0,      /* Eq. 9 with Adam moments (beta1, beta2, eps) on c */
+       AF_OPT_GD = 1 };      /* Eq. 9 as printed: c <- c - lr dL/dc (m, v unused) */
+
 /* apodization */
 enum { AF_APOD_FNUMBER = 0,  /* |x'| <= z' / (2F), z' > 0 (usual f-number reading of Eq. 4) */
        AF_APOD_PRINTED = 1 };/* |x'| <= (F/2) z', z' > 0 (Eq. 4 as printed) */
@@ -89,8 +93,13 @@ enum { AF_APOD_FNUMBER = 0,  /* |x'| <= z' / (2F), z' > 0 (usual f-number readin
  *   pair, sample n at time t0 + n / fs, demodulation frequency fd.
  * Subapertures: blocks of sub_width consecutive elements; image
  *   B_ij = transmit block i, receive block j.
- * Table II: rho_thresh, fnum, nseg, w1, kx1, kz1, w2, kx2, kz2, lr.
- * Adam (Eq. 9 as Adam): beta1, beta2, eps on u = s * c_ref.
+ * Table II: rho_thresh, fnum, nseg, w1, kx1, kz1, w2, kx2, kz2, lr, as printed.
+ *   Eq. 9-11 act on the sound speed in units of c_unit m/s (1000: km/s) with
+ *   positions in mm: kx1, kz1 in c_unit/mm, kx2, kz2 in c_unit/mm^2, lr in
+ *   c_unit per step.  Table II's values read this way allow gradients of
+ *   10 m/s per mm and take Adam steps of 3 m/s (phantom) or 50 m/s (in vivo).
+ * Update (Eq. 9) on c = 1 / (c_unit s): optimizer AF_OPT_ADAM (Adam with beta1,
+ *   beta2, eps) or AF_OPT_GD (the plain gradient step as printed).
  */
 #define AF_MAX_NSEG 65535
 
@@ -112,7 +121,8 @@ typedef struct {
     int sub_width;
     double rho_thresh;
     double w1, kx1, kz1, w2, kx2, kz2;
-    double lr, beta1, beta2, eps, c_ref;
+    double lr, beta1, beta2, eps, c_unit;
+    int optimizer;
 } af_config;
 
 /* Host-only validation of a configuration (no CUDA call).  Returns AF_OK or
@@ -140,8 +150,9 @@ af_status af_forward(af_plan_t plan, const void *d_iq, const float *d_iq_scale,
  * Delays are recomputed from the stored one-way tables, not stored per pair. */
 af_status af_adjoint(af_plan_t plan, float *d_grad);
 
-/* Eq. 9 update as Adam on u = s * c_ref (step counts from 1):
- * updates d_slowness, d_adam_m, d_adam_v ([nz][nx] float each) in place. */
+/* Eq. 9 update of c = 1 / (c_unit s) (step counts from 1): AF_OPT_ADAM updates
+ * d_slowness, d_adam_m, d_adam_v ([nz][nx] float each) in place; AF_OPT_GD updates
+ * d_slowness only (d_adam_m and d_adam_v may then be NULL). */
 af_status af_step(af_plan_t plan, const float *d_grad, float *d_slowness,
                   float *d_adam_m, float *d_adam_v, int step);
 
@@ -254,6 +265,25 @@ af_status af_image_metrics(af_plan_t plan, const uint8_t *d_roi, int nbins, af_m
  * stream; allocates npix floats of scratch. */
 af_status af_speed_mae(af_plan_t plan, const float *d_s, const float *d_c_true, double *h_mae);
 
+/* ---- patch-sharded runs (one acquisition over several GPUs) ----
+ * L_CMPE (Sec. II-D) is a sum over patches normalised by the total number M of
+ * active terms, so a problem whose patches are split over several plans (one per
+ * GPU, each with its own patch subset and the same grid, array and channel data)
+ * needs two exchanges per iteration:
+ *   af_forward on every plan;  af_cmpe_totals -> d_totals[2] = {sum over the plan's
+ *   active terms of |arg z|, number of active terms} (device doubles);  sum the
+ *   totals over the plans (e.g. an all-reduce);  af_set_cmpe_totals with the sums:
+ *   the plan's L_CMPE = sum / max(1, M) and its adjoint's normalisation become those
+ *   of the whole problem, and d_loss ([4] float, may be NULL) is rewritten as
+ *   af_forward writes it;  af_adjoint on every plan;  sum the d_grad of the plans;
+ *   af_step with the summed gradient on every plan (identical updates).
+ * Give the regularisers (w1, w2) to one plan only, or their gradient is counted
+ * once per plan.  Both calls are asynchronous on the plan's stream and need an
+ * earlier af_forward (AF_ERR_STATE).  No counterpart in the paper, which runs on
+ * one device. */
+af_status af_cmpe_totals(af_plan_t plan, double *d_totals);
+af_status af_set_cmpe_totals(af_plan_t plan, const double *d_totals, float *d_loss);
+
 /* dL/dB[b][p] (= dL/dRe B + j dL/dIm B) of the last af_adjoint,
  * [nsub*nsub][npix][2] float. */
 af_status af_get_image_grad(af_plan_t plan, float *d_G);
@@ -294,8 +324,9 @@ af_status af_get_stage_times(af_plan_t plan, float *h_ms, int *h_count);
  *  d_loss     [1] float, written with L_CMPE
  *  d_n_active [1] int, number of active CMPE terms, or NULL
  *  stream     cudaStream_t (NULL = legacy default stream)
- * The first call on a device looks up the scratch array's device address;
- * make it before any stream capture.  All calls share the scratch: calls that
+ * Every call looks up the scratch array's device address on the current device
+ * (no allocation); the first call on a device may load the library's device code
+ * there, so make it before any stream capture.  All calls share the scratch: calls that
  * overlap on the GPU race, so order them on one stream.  n_patch above
  * AF_NOALLOC_MAX_PATCHES returns AF_ERR_UNSUPPORTED.  No cudaMalloc/cudaFree. */
 #define AF_NOALLOC_MAX_PATCHES 16384
@@ -349,6 +380,17 @@ af_status af_surrogate_grad(af_plan_t plan, const float *d_X, const float *d_Y, 
  * learned lens-time model (the MLP surrogate below). */
 af_status af_gemm_bf16(const void *d_A, const void *d_B, float *d_D, int M, int N, int K,
                        int a_mn_major, int b_mn_major, int *d_err, void *stream);
+
+/* Test hook for the bounded waits of the tensor-core kernels (af_gemm_bf16, the
+ * lens-surrogate training and inference).  Each waits for its MMAs with a bounded
+ * number of tries; on a timeout it reports the error (*d_err = 1 for
+ * af_gemm_bf16, AF_ERR_TIMEOUT from af_surrogate_train), waits again with the
+ * default bound for the MMAs in flight, frees its tensor memory and returns.
+ * tries >= 0 sets the number of tries of that first wait for every such kernel the
+ * process launches afterwards (0: it gives up at once, so a test can run the
+ * error path); tries < 0 restores the default (2^26 tries, about a second).  No
+ * counterpart in the paper. */
+af_status af_set_wait_limit(int tries);
 
 /* Message of the last failing call on this host thread ("" if none). */
 const char *af_last_error(void);

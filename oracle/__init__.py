@@ -16,17 +16,31 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
-_lib = None
+_OMP_LIB_PATH = os.path.join(_HERE, "liboracle_omp.so")
+_libs = {}
 
 
-def build(force: bool = False) -> str:
-    """Compile af_oracle.c (plain -O2, IEEE arithmetic, one thread)."""
+def _compile(out: str, extra: list, force: bool) -> str:
     src = os.path.join(_HERE, "af_oracle.c")
     hdr = os.path.join(_HERE, "af_oracle.h")
     newest = max(os.path.getmtime(src), os.path.getmtime(hdr))
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", _LIB_PATH, src, "-lm"])
-    return _LIB_PATH
+    if force or not os.path.exists(out) or os.path.getmtime(out) < newest:
+        subprocess.check_call(["gcc", "-O2", "-std=c99", *extra, "-shared", "-fPIC", "-o", out, src, "-lm"])
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile af_oracle.c twice: plain -O2, IEEE arithmetic, one thread (the parity
+    judge), and the same source with -fopenmp (all host cores; for full-size checks and
+    the benchmark's all-core CPU baseline).  Returns the single-threaded library."""
+    _compile(_OMP_LIB_PATH, ["-fopenmp"], force)
+    return _compile(_LIB_PATH, ["-Wno-unknown-pragmas"], force)
+
+
+def omp_threads() -> int:
+    """Threads the OpenMP build uses (OMP_NUM_THREADS, else the host's cores)."""
+    lib = _load(True)
+    return int(lib.or_omp_threads())
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -49,14 +63,14 @@ class Geom(ctypes.Structure):
         ("sub_width", ctypes.c_int), ("rho_thresh", ctypes.c_double),
         ("w1", ctypes.c_double), ("kx1", ctypes.c_double), ("kz1", ctypes.c_double),
         ("w2", ctypes.c_double), ("kx2", ctypes.c_double), ("kz2", ctypes.c_double),
+        ("c_unit", ctypes.c_double),
     ]
 
 
-def _load():
-    global _lib
-    if _lib is None:
+def _load(parallel: bool = False):
+    if parallel not in _libs:
         build()
-        lib = ctypes.CDLL(_LIB_PATH)
+        lib = ctypes.CDLL(_OMP_LIB_PATH if parallel else _LIB_PATH)
         G = ctypes.POINTER(Geom)
         sig = {
             "or_element_angles": (None, [ctypes.c_int, _dp, _dp, _dp]),
@@ -79,15 +93,17 @@ def _load():
             "or_das_adjoint": (None, [G, _fp, _dp, _u8p, _dp, _dp]),
             "or_ray_adjoint": (None, [G, _dp, _dp, _u8p, _dp, _dp]),
             "or_loss_grad": (ctypes.c_double, [G, _fp, _dp, _u8p, _u8p, _dp, _dp, _dp, _u8p, _ip]),
+            "or_gd": (None, [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double]),
             "or_adam": (None, [ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double,
                                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
         }
+        sig["or_omp_threads"] = (ctypes.c_int, [])
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
             fn.restype = res
             fn.argtypes = args
-        _lib = lib
-    return _lib
+        _libs[parallel] = lib
+    return _libs[parallel]
 
 
 def _d(a):
@@ -99,10 +115,11 @@ def _u8(a):
 
 
 class Oracle:
-    """Holds the C geometry struct (and keeps its arrays alive)."""
+    """Holds the C geometry struct (and keeps its arrays alive).  parallel=True runs
+    the OpenMP build of the same source on all host cores."""
 
-    def __init__(self, problem):
-        self.lib = _load()
+    def __init__(self, problem, parallel: bool = False):
+        self.lib = _load(parallel)
         p = problem
         self.p = p
         self._ex = np.ascontiguousarray(p.elem_x, np.float64)
@@ -128,6 +145,7 @@ class Oracle:
         g.rho_thresh = p.rho_thresh
         g.w1, g.kx1, g.kz1 = p.w1, p.kx1, p.kz1
         g.w2, g.kx2, g.kz2 = p.w2, p.kx2, p.kz2
+        g.c_unit = p.c_unit
         self.g = g
         self.gp = ctypes.byref(g)
         self.ne = g.ne
@@ -264,10 +282,16 @@ class Oracle:
         n = self.g.n_patch * self.npair
         return parts, g, mask[:n].reshape(self.g.n_patch, self.npair), M.value
 
-    def adam(self, s, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, c_ref=1540.0):
+    def gd(self, s, grad, lr, c_unit=1000.0):
+        """Eq. 9 as printed on c in units of c_unit m/s; returns the new slowness."""
+        s = np.array(s, np.float64)
+        self.lib.or_gd(s.size, _d(s), _d(np.ascontiguousarray(grad, np.float64)), lr, c_unit)
+        return s
+
+    def adam(self, s, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, c_unit=1000.0):
         s = np.array(s, np.float64)
         m = np.array(m, np.float64)
         v = np.array(v, np.float64)
         self.lib.or_adam(s.size, _d(s), _d(np.ascontiguousarray(grad, np.float64)), _d(m), _d(v),
-                         step, lr, beta1, beta2, eps, c_ref)
+                         step, lr, beta1, beta2, eps, c_unit)
         return s, m, v

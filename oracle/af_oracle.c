@@ -6,6 +6,11 @@
  * TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
  * CPU-baseline leg are the only callers.  Plain loops in the order of the
  * paper's equations, double precision, one thread, no blocking or fusion.
+ * The same source built with -fopenmp runs the loops over elements, pixels
+ * and patches on all host cores (the `omp` pragmas below; a plain build
+ * ignores them).  Every such loop writes disjoint outputs, so that build
+ * gives the single-threaded results bit for bit, except the ray adjoint,
+ * whose per-node sums are then reduced across threads in a different order.
  *
  * Readings of passages the paper leaves open (each also listed in the
  * design notes of the repository):
@@ -24,9 +29,15 @@
  *  R6 bicubic = Keys cubic convolution (a = -1/2), clamp-to-edge indices.
  *  R7 exit points are found at the current c_med = mean(1/s) and held
  *     constant in the adjoint (Sec. III-A).
- *  R8 the update of Eq. 9 is run as Adam on u = s * c_ref.
- *  R9 Eq. 10-11: forward first differences and central second differences
- *     of c = 1/s in m/s per mm (per mm^2); N = number of difference terms.
+ *  R8 the update of Eq. 9 acts on the sound speed c, as printed, measured in
+ *     km/s (c_unit = 1000 m/s).  Both the plain gradient step as printed
+ *     (or_gd) and a step with Adam moments (or_adam) are provided; with Adam,
+ *     Table II's learning rates are speed steps of 3 m/s (phantom) and 50 m/s
+ *     (in vivo).
+ *  R9 Eq. 10-11 ("physical units"): forward first differences and central
+ *     second differences of c in km/s per mm (per mm^2), so Table II's
+ *     kappa = 0.01 allows gradients up to 10 m/s per mm; N = number of
+ *     difference terms of each family.
  *  R10 Psi(tau): linear interpolation at u = (tau - t0) fs, zero unless
  *     0 <= u < ns - 1.
  *  R11 the brute search over N_search lens points is replaced by a
@@ -37,8 +48,21 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_PI 3.14159265358979323846
+
+/* threads of the OpenMP build (1 for the plain build) */
+int or_omp_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------ */
 /* Sec. II-A, Eq. 3: element orientation from the neighbouring elements */
@@ -255,6 +279,7 @@ void or_delays(const or_geom *g, const double *s, const uint8_t *apod_in,
     double *theta = (double *)malloc(sizeof(double) * (ne > 0 ? ne : 1));
     or_element_angles(ne, g->ex, g->ez, theta);
     double sbar = 1.0 / or_mean_speed(g, s);
+#pragma omp parallel for schedule(dynamic, 1)
     for (int e = 0; e < ne; ++e) {
         for (int p = 0; p < np; ++p) {
             size_t k = (size_t)e * np + p;
@@ -285,6 +310,7 @@ void or_das(const or_geom *g, const float *psi, const double *T, const uint8_t *
     int ne = g->ne, np = g->n_patch * g->patch_npix, w = g->sub_width;
     int nsub = ne / w;
     memset(B, 0, sizeof(double) * 2 * (size_t)nsub * nsub * np);
+#pragma omp parallel for schedule(dynamic, 16)
     for (int p = 0; p < np; ++p) {
         for (int t = 0; t < ne; ++t) {
             if (!apod[(size_t)t * np + p]) continue;
@@ -332,8 +358,10 @@ double or_cmpe(const or_geom *g, const double *B, const uint8_t *mask_in,
     int npair = or_cmpe_pairs(g, NULL);
     int *pairs = (int *)malloc(sizeof(int) * 2 * (npair > 0 ? npair : 1));
     or_cmpe_pairs(g, pairs);
-    double sum = 0.0;
-    int m_count = 0;
+    size_t nt = (size_t)g->n_patch * npair;
+    double *term = (double *)malloc(sizeof(double) * (nt ? nt : 1));   /* m |arg z| */
+    uint8_t *mt = (uint8_t *)malloc(nt ? nt : 1);
+#pragma omp parallel for schedule(dynamic, 1)
     for (int P = 0; P < g->n_patch; ++P) {
         for (int k = 0; k < npair; ++k) {
             const double *B1 = B + 2 * (size_t)pairs[2 * k] * np;
@@ -355,12 +383,20 @@ double or_cmpe(const or_geom *g, const double *B, const uint8_t *mask_in,
             if (z) { z[2 * o] = zr; z[2 * o + 1] = zi; }
             if (rho) rho[o] = r;
             if (mask) mask[o] = (uint8_t)m;
-            if (m) {
-                sum += fabs(atan2(zi, zr));
-                ++m_count;
-            }
+            mt[o] = (uint8_t)m;
+            term[o] = m ? fabs(atan2(zi, zr)) : 0.0;
         }
     }
+    /* sum of the masked phase errors, patch by patch in pair order */
+    double sum = 0.0;
+    int m_count = 0;
+    for (size_t o = 0; o < nt; ++o) {
+        if (!mt[o]) continue;
+        sum += term[o];
+        ++m_count;
+    }
+    free(term);
+    free(mt);
     free(pairs);
     if (n_active) *n_active = m_count;
     return sum / (m_count > 1 ? m_count : 1);
@@ -380,6 +416,7 @@ void or_cmpe_adjoint(const or_geom *g, const double *B, const double *z,
     or_cmpe_pairs(g, pairs);
     memset(G, 0, sizeof(double) * 2 * (size_t)nsub * nsub * np);
     double inv_m = 1.0 / (n_active > 1 ? n_active : 1);
+#pragma omp parallel for schedule(dynamic, 1)
     for (int P = 0; P < g->n_patch; ++P) {
         for (int k = 0; k < npair; ++k) {
             size_t o = (size_t)P * npair + k;
@@ -419,6 +456,7 @@ void or_das_adjoint(const or_geom *g, const float *psi, const double *T,
     int ne = g->ne, np = g->n_patch * g->patch_npix, w = g->sub_width;
     int nsub = ne / w;
     memset(gT, 0, sizeof(double) * (size_t)ne * np);
+#pragma omp parallel for schedule(dynamic, 16)
     for (int p = 0; p < np; ++p) {
         for (int t = 0; t < ne; ++t) {
             if (!apod[(size_t)t * np + p]) continue;
@@ -456,6 +494,9 @@ void or_ray_adjoint(const or_geom *g, const double *s, const double *phi,
 {
     (void)s;
     int ne = g->ne, np = g->n_patch * g->patch_npix, n = g->nseg;
+    int ng = g->nx * g->nz;
+    (void)ng;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : grad[:ng])
     for (int e = 0; e < ne; ++e) {
         for (int p = 0; p < np; ++p) {
             size_t k = (size_t)e * np + p;
@@ -487,6 +528,9 @@ static double deadzone_d(double x, double k)
     return x > 0.0 ? 1.0 : -1.0;
 }
 
+/* sound speed of a slowness value in the units of Eq. 9-11 (R8, R9) */
+static double speed_u(const or_geom *g, double s) { return 1.0 / (s * g->c_unit); }
+
 void or_regularizers(const or_geom *g, const double *s, double *rtv, double *rsv)
 {
     int nx = g->nx, nz = g->nz;
@@ -495,15 +539,15 @@ void or_regularizers(const or_geom *g, const double *s, double *rtv, double *rsv
     long na = 0, nb = 0;
     for (int j = 0; j < nz; ++j)
         for (int i = 0; i < nx; ++i) {
-            double c0 = 1.0 / s[j * nx + i];
-            if (i + 1 < nx) { a += deadzone((1.0 / s[j * nx + i + 1] - c0) / hx, g->kx1); ++na; }
-            if (j + 1 < nz) { a += deadzone((1.0 / s[(j + 1) * nx + i] - c0) / hz, g->kz1); ++na; }
+            double c0 = speed_u(g, s[j * nx + i]);
+            if (i + 1 < nx) { a += deadzone((speed_u(g, s[j * nx + i + 1]) - c0) / hx, g->kx1); ++na; }
+            if (j + 1 < nz) { a += deadzone((speed_u(g, s[(j + 1) * nx + i]) - c0) / hz, g->kz1); ++na; }
             if (i >= 1 && i + 1 < nx) {
-                double d = (1.0 / s[j * nx + i + 1] - 2.0 * c0 + 1.0 / s[j * nx + i - 1]) / (hx * hx);
+                double d = (speed_u(g, s[j * nx + i + 1]) - 2.0 * c0 + speed_u(g, s[j * nx + i - 1])) / (hx * hx);
                 b += deadzone(d, g->kx2); ++nb;
             }
             if (j >= 1 && j + 1 < nz) {
-                double d = (1.0 / s[(j + 1) * nx + i] - 2.0 * c0 + 1.0 / s[(j - 1) * nx + i]) / (hz * hz);
+                double d = (speed_u(g, s[(j + 1) * nx + i]) - 2.0 * c0 + speed_u(g, s[(j - 1) * nx + i])) / (hz * hz);
                 b += deadzone(d, g->kz2); ++nb;
             }
         }
@@ -520,31 +564,31 @@ void or_regularizer_grad(const or_geom *g, const double *s, double *grad)
     if (nx < 2) na = (long)nx * (nz - 1);
     if (nz < 2) na = (long)(nx - 1) * nz;
     int n = nx * nz;
-    double *gc = (double *)calloc((size_t)n, sizeof(double));   /* dR/dc */
+    double *gc = (double *)calloc((size_t)n, sizeof(double));   /* dR/dc, c in c_unit */
     for (int j = 0; j < nz; ++j)
         for (int i = 0; i < nx; ++i) {
             int k = j * nx + i;
-            double c0 = 1.0 / s[k];
+            double c0 = speed_u(g, s[k]);
             if (na > 0 && i + 1 < nx) {
-                double d = deadzone_d((1.0 / s[k + 1] - c0) / hx, g->kx1) * g->w1 / (na * hx);
+                double d = deadzone_d((speed_u(g, s[k + 1]) - c0) / hx, g->kx1) * g->w1 / (na * hx);
                 gc[k + 1] += d; gc[k] -= d;
             }
             if (na > 0 && j + 1 < nz) {
-                double d = deadzone_d((1.0 / s[k + nx] - c0) / hz, g->kz1) * g->w1 / (na * hz);
+                double d = deadzone_d((speed_u(g, s[k + nx]) - c0) / hz, g->kz1) * g->w1 / (na * hz);
                 gc[k + nx] += d; gc[k] -= d;
             }
             if (nb > 0 && i >= 1 && i + 1 < nx) {
-                double v = (1.0 / s[k + 1] - 2.0 * c0 + 1.0 / s[k - 1]) / (hx * hx);
+                double v = (speed_u(g, s[k + 1]) - 2.0 * c0 + speed_u(g, s[k - 1])) / (hx * hx);
                 double d = deadzone_d(v, g->kx2) * g->w2 / (nb * hx * hx);
                 gc[k + 1] += d; gc[k - 1] += d; gc[k] -= 2.0 * d;
             }
             if (nb > 0 && j >= 1 && j + 1 < nz) {
-                double v = (1.0 / s[k + nx] - 2.0 * c0 + 1.0 / s[k - nx]) / (hz * hz);
+                double v = (speed_u(g, s[k + nx]) - 2.0 * c0 + speed_u(g, s[k - nx])) / (hz * hz);
                 double d = deadzone_d(v, g->kz2) * g->w2 / (nb * hz * hz);
                 gc[k + nx] += d; gc[k - nx] += d; gc[k] -= 2.0 * d;
             }
         }
-    for (int k = 0; k < n; ++k) grad[k] += -gc[k] / (s[k] * s[k]);   /* c = 1/s */
+    for (int k = 0; k < n; ++k) grad[k] += -gc[k] / (g->c_unit * s[k] * s[k]);   /* c = 1/(c_unit s) */
     free(gc);
 }
 
@@ -593,18 +637,29 @@ double or_loss_grad(const or_geom *g, const float *psi, const double *s,
     return L;
 }
 
-/* Adam on u = s * c_ref (R8); Eq. 9 is the beta1 = beta2 = 0 limit up to
- * the normalisation of the step. */
+/* Eq. 9 as printed: one gradient step on c = 1 / (s c_unit), dL/dc = -dL/ds c_unit s^2 */
+void or_gd(int n, double *s, const double *grad, double lr, double c_unit)
+{
+    for (int k = 0; k < n; ++k) {
+        double c = 1.0 / (s[k] * c_unit);
+        double gc = -grad[k] * c_unit * s[k] * s[k];
+        s[k] = 1.0 / ((c - lr * gc) * c_unit);
+    }
+}
+
+/* Adam on the sound speed c = 1 / (s c_unit) (R8); with beta1 = beta2 = 0 each
+ * step is lr times the sign of the Eq. 9 step.  dL/dc = dL/ds ds/dc with
+ * ds/dc = -c_unit s^2. */
 void or_adam(int n, double *s, const double *grad, double *m, double *v, int step,
-             double lr, double beta1, double beta2, double eps, double c_ref)
+             double lr, double beta1, double beta2, double eps, double c_unit)
 {
     double bc1 = 1.0 - pow(beta1, step), bc2 = 1.0 - pow(beta2, step);
     for (int k = 0; k < n; ++k) {
-        double gu = grad[k] / c_ref;
-        m[k] = beta1 * m[k] + (1.0 - beta1) * gu;
-        v[k] = beta2 * v[k] + (1.0 - beta2) * gu * gu;
+        double gc = -grad[k] * c_unit * s[k] * s[k];
+        m[k] = beta1 * m[k] + (1.0 - beta1) * gc;
+        v[k] = beta2 * v[k] + (1.0 - beta2) * gc * gc;
         double mh = m[k] / bc1, vh = v[k] / bc2;
-        double u = s[k] * c_ref - lr * mh / (sqrt(vh) + eps);
-        s[k] = u / c_ref;
+        double c = 1.0 / (s[k] * c_unit) - lr * mh / (sqrt(vh) + eps);
+        s[k] = 1.0 / (c * c_unit);
     }
 }

@@ -48,10 +48,15 @@ typedef struct {
     double fs, fd, t0;
     int sub_width;                 /* elements per subaperture block */
     double rho_thresh;             /* Table II correlation threshold */
-    /* Eq. 10-12 regularisation */
+    /* Eq. 10-12 regularisation; c_unit = m/s per unit of the sound speed c
+     * that Eq. 9-11 act on (1000: c in km/s, the reading R9) */
     double w1, kx1, kz1, w2, kx2, kz2;
+    double c_unit;
 } or_geom;
 
+/* threads the library runs on: 1 for the plain build, all host cores for the
+ * OpenMP build of the same source */
+int or_omp_threads(void);
 /* Eq. 3 (+ linear extrapolation at the two end elements) */
 void or_element_angles(int ne, const double *ex, const double *ez, double *theta);
 /* Eq. 2 + Eq. 4 */
@@ -107,9 +112,12 @@ double or_loss_grad(const or_geom *g, const float *psi, const double *s,
                     const uint8_t *apod_in, const uint8_t *mask_in,
                     const double *phi_in, double *grad, double parts[4],
                     uint8_t *mask_out, int *n_active);
-/* Eq. 9 generalised to Adam on the normalised slowness u = s * c_ref */
+/* Eq. 9 as printed: c <- c - lr dL/dc on c = 1 / (s * c_unit); grad is dL/ds */
+void or_gd(int n, double *s, const double *grad, double lr, double c_unit);
+/* Eq. 9 generalised to Adam on the sound speed c = 1 / (s * c_unit), i.e. c in
+ * units of c_unit m/s (R8); grad is dL/ds, s is updated in place */
 void or_adam(int n, double *s, const double *grad, double *m, double *v, int step,
-             double lr, double beta1, double beta2, double eps, double c_ref);
+             double lr, double beta1, double beta2, double eps, double c_unit);
 
 #ifdef __cplusplus
 }

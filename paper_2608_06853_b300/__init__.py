@@ -32,6 +32,7 @@ AF_ERR_NUMERIC, AF_ERR_TIMEOUT, AF_ERR_UNSUPPORTED, AF_ERR_STATE = 5, 6, 7, 8
 AF_IQ_C64, AF_IQ_BF16, AF_IQ_F16 = 0, 1, 2
 AF_LENS_BENT_RAY, AF_LENS_NONE, AF_LENS_PLANAR = 0, 1, 2
 AF_APOD_FNUMBER, AF_APOD_PRINTED = 0, 1
+AF_OPT_ADAM, AF_OPT_GD = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -53,7 +54,7 @@ class AfConfig(ctypes.Structure):
         ("w1", ctypes.c_double), ("kx1", ctypes.c_double), ("kz1", ctypes.c_double),
         ("w2", ctypes.c_double), ("kx2", ctypes.c_double), ("kz2", ctypes.c_double),
         ("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
-        ("eps", ctypes.c_double), ("c_ref", ctypes.c_double),
+        ("eps", ctypes.c_double), ("c_unit", ctypes.c_double), ("optimizer", ctypes.c_int),
     ]
 
 
@@ -61,7 +62,7 @@ ProblemFields = ("elem_x", "elem_z", "lens_mode", "arc_cx", "arc_cz", "lens_radi
                  "t_ttp", "apod_mode", "fnum", "n_patch", "patch_npix", "pix_x", "pix_z", "nx",
                  "nz", "x0", "z0", "dx", "dz", "nseg", "ns", "fs", "fd", "t0", "sub_width",
                  "rho_thresh", "w1", "kx1", "kz1", "w2", "kx2", "kz2", "lr", "beta1", "beta2",
-                 "eps", "c_ref")
+                 "eps", "c_unit", "optimizer")
 
 _lib = None
 
@@ -99,6 +100,8 @@ _SIGNATURES = {
     "af_get_images": (ctypes.c_int, [_VP, _VP]),
     "af_get_cmpe": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_int)]),
     "af_get_image_grad": (ctypes.c_int, [_VP, _VP]),
+    "af_cmpe_totals": (ctypes.c_int, [_VP, _VP]),
+    "af_set_cmpe_totals": (ctypes.c_int, [_VP, _VP, _VP]),
     "af_get_bmode": (ctypes.c_int, [_VP, _VP, _VP]),
     "af_image_metrics": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(AfMetrics)]),
     "af_speed_mae": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_double)]),
@@ -114,6 +117,7 @@ _SIGNATURES = {
     "af_surrogate_grad": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_float)]),
     "af_gemm_bf16": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, _VP, _VP]),
+    "af_set_wait_limit": (ctypes.c_int, [ctypes.c_int]),
     "af_set_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "af_get_stage_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]),
     "af_last_error": (ctypes.c_char_p, []),
@@ -179,7 +183,8 @@ def make_config(problem, iq_dtype: int = AF_IQ_C64):
     c.w1, c.kx1, c.kz1 = float(problem.w1), float(problem.kx1), float(problem.kz1)
     c.w2, c.kx2, c.kz2 = float(problem.w2), float(problem.kx2), float(problem.kz2)
     c.lr, c.beta1, c.beta2 = float(problem.lr), float(problem.beta1), float(problem.beta2)
-    c.eps, c.c_ref = float(problem.eps), float(problem.c_ref)
+    c.eps, c.c_unit = float(problem.eps), float(problem.c_unit)
+    c.optimizer = int(getattr(problem, "optimizer", AF_OPT_ADAM))
     return c, keep
 
 
@@ -213,12 +218,39 @@ AF_NOALLOC_MAX_PATCHES = 16384
 
 def af_cmpe_loss_noalloc(B, nsub: int, n_patch: int, patch_npix: int, rho_thresh: float, loss,
                          n_active=None, stream=None):
-    """L_CMPE of images B ([nsub*nsub][npix] complex64 or [..][2] float32, device) into
-    loss[0], without any device allocation by the library (see include/af.h)."""
+    """L_CMPE of images B ([nsub*nsub][npix] complex64 or [..][npix][2] float32, device) into
+    loss[0], without any device allocation by the library (see include/af.h).
+
+    The library reads nsub*nsub*n_patch*patch_npix complex values from B and writes
+    loss[0] (and n_active[0]) on the device that is current when it is called, so the
+    arguments are checked here first: shapes, dtypes and contiguity (ValueError), then
+    that every tensor is on the current CUDA device."""
     import torch
+    nsub, n_patch, patch_npix = int(nsub), int(n_patch), int(patch_npix)
+    if B.dtype == torch.complex64:
+        n_values = B.numel()
+    elif B.dtype == torch.float32 and B.dim() >= 1 and B.shape[-1] == 2:
+        n_values = B.numel() // 2
+    else:
+        raise ValueError("B must be complex64, or float32 with a last dimension of 2")
+    if n_values != nsub * nsub * n_patch * patch_npix:
+        raise ValueError(f"B holds {n_values} complex values, expected nsub^2 * n_patch * patch_npix = "
+                         f"{nsub * nsub * n_patch * patch_npix}")
+    if not B.is_contiguous():
+        raise ValueError("B must be contiguous")
+    if loss.dtype != torch.float32 or loss.numel() < 1 or not loss.is_contiguous():
+        raise ValueError("loss must be a contiguous float32 tensor with at least one element")
+    if n_active is not None and (n_active.dtype != torch.int32 or n_active.numel() < 1):
+        raise ValueError("n_active must be an int32 tensor with at least one element, or None")
+    tensors = [B, loss] + ([n_active] if n_active is not None else [])
+    if not all(t.is_cuda for t in tensors):
+        raise ValueError("B, loss and n_active must be CUDA tensors")
+    cur = torch.cuda.current_device()
+    if any(t.device.index != cur for t in tensors):
+        raise ValueError(f"B, loss and n_active must be on the current CUDA device (cuda:{cur})")
     Bv = torch.view_as_real(B) if B.dtype == torch.complex64 else B
     h = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
-    _check(load().af_cmpe_loss_noalloc(_ptr(Bv), int(nsub), int(n_patch), int(patch_npix),
+    _check(load().af_cmpe_loss_noalloc(_ptr(Bv), nsub, n_patch, patch_npix,
                                        float(rho_thresh), _ptr(loss), _ptr(n_active), h),
            "af_cmpe_loss_noalloc")
     return loss
@@ -369,6 +401,18 @@ class Plan:
         out = ctypes.c_double()
         _check(self.lib.af_speed_mae(self.handle, _ptr(s), _ptr(c_true), ctypes.byref(out)), "af_speed_mae")
         return out.value
+
+    def cmpe_totals(self, out=None):
+        """{sum of |arg z| over active CMPE terms, their number} of the last forward, as a
+        float64 device tensor [2] (af_cmpe_totals; asynchronous on the plan's stream)."""
+        import torch
+        out = torch.empty(2, dtype=torch.float64, device=self._dev()) if out is None else out
+        _check(self.lib.af_cmpe_totals(self.handle, _ptr(out)), "af_cmpe_totals")
+        return out
+
+    def set_cmpe_totals(self, totals, loss=None):
+        """Use CMPE totals summed over several plans (af_set_cmpe_totals)."""
+        _check(self.lib.af_set_cmpe_totals(self.handle, _ptr(totals), _ptr(loss)), "af_set_cmpe_totals")
 
     def image_grad(self):
         """dL/dB [nsub*nsub][npix] complex64 of the last adjoint."""

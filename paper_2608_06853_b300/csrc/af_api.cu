@@ -7,10 +7,12 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <cmath>
 #include <vector>
 
 #include "af_internal.cuh"
+#include "af_tc.cuh"
 
 namespace {
 
@@ -82,6 +84,10 @@ cudaError_t staged(af_plan_t pl, int stage, F &&launch)
 
 }  // namespace
 
+static std::atomic<uint32_t> g_wait_tries{tc::kWaitTries};
+
+uint32_t af_wait_tries() { return g_wait_tries.load(std::memory_order_relaxed); }
+
 af_status af_set_error(af_status st, const char *fmt, ...)
 {
     va_list ap;
@@ -143,8 +149,10 @@ af_status af_check_config(const af_config *c)
     const double regs[] = {c->w1, c->kx1, c->kz1, c->w2, c->kx2, c->kz2, c->lr};
     for (double r : regs)
         if (!(r >= 0) || !is_fin(r)) return fail(AF_ERR_ARG, "regulariser weights, thresholds and lr must be finite and >= 0");
-    if (!(c->beta1 >= 0 && c->beta1 < 1) || !(c->beta2 >= 0 && c->beta2 < 1) || !(c->eps > 0) || !(c->c_ref > 0))
+    if (!(c->beta1 >= 0 && c->beta1 < 1) || !(c->beta2 >= 0 && c->beta2 < 1) || !(c->eps > 0) || !(c->c_unit > 0) || !is_fin(c->c_unit))
         return fail(AF_ERR_ARG, "bad Adam parameters");
+    if (c->optimizer != AF_OPT_ADAM && c->optimizer != AF_OPT_GD)
+        return fail(AF_ERR_ARG, "unknown optimizer %d", c->optimizer);
     const long long npix = (long long)c->n_patch * c->patch_npix;
     const long long nsub = c->n_elem / c->sub_width;
     if ((long long)c->n_elem * npix >= (1LL << 31) || nsub * nsub * npix >= (1LL << 31))
@@ -333,7 +341,9 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
         const double s2 = ldexp(1.0, 20) * (c->nseg + 1) / lmax;
         g.fix_scale = (float)fmin(s1, s2);
     }
-    g.c_ref = (float)c->c_ref;
+    g.c_unit = (float)c->c_unit;
+    g.optimizer = c->optimizer;
+    g.inv_c_unit = (float)(1.0 / c->c_unit);
     g.lr = (float)c->lr;
     g.beta1 = (float)c->beta1;
     g.beta2 = (float)c->beta2;
@@ -491,7 +501,8 @@ af_status af_step(af_plan_t pl, const float *grad, float *s, float *m, float *v,
 {
     g_err[0] = 0;
     if (!pl) return fail(AF_ERR_ARG, "plan is NULL");
-    if (!grad || !s || !m || !v) return fail(AF_ERR_ARG, "d_grad, d_slowness, d_adam_m, d_adam_v must be non-NULL");
+    if (!grad || !s) return fail(AF_ERR_ARG, "d_grad and d_slowness must be non-NULL");
+    if (pl->g.optimizer == AF_OPT_ADAM && (!m || !v)) return fail(AF_ERR_ARG, "Adam needs d_adam_m and d_adam_v");
     if (step < 1) return fail(AF_ERR_ARG, "step = %d < 1", step);
     AF_CUDA(staged(pl, 7, [&] { return launch_adam(pl, grad, s, m, v, step); }));
     return AF_OK;
@@ -587,6 +598,22 @@ af_status af_get_cmpe(af_plan_t pl, float *z, uint8_t *mask, int *n_active)
         AF_CUDA(cudaStreamSynchronize(pl->stream));
         AF_CUDA(cudaMemcpy(n_active, &pl->scal->n_active, sizeof(int), cudaMemcpyDeviceToHost));
     }
+    return AF_OK;
+}
+
+af_status af_cmpe_totals(af_plan_t pl, double *d_totals)
+{
+    if (!pl || !d_totals) return fail(AF_ERR_ARG, "af_cmpe_totals: NULL argument");
+    if (!pl->have_fwd) return fail(AF_ERR_STATE, "no forward pass yet");
+    AF_CUDA(launch_cmpe_totals(pl, d_totals));
+    return AF_OK;
+}
+
+af_status af_set_cmpe_totals(af_plan_t pl, const double *d_totals, float *d_loss)
+{
+    if (!pl || !d_totals) return fail(AF_ERR_ARG, "af_set_cmpe_totals: NULL argument");
+    if (!pl->have_fwd) return fail(AF_ERR_STATE, "no forward pass yet");
+    AF_CUDA(launch_cmpe_set_totals(pl, d_totals, d_loss));
     return AF_OK;
 }
 
@@ -802,6 +829,12 @@ af_status af_get_counters(af_plan_t pl, long long *h)
     h[1] = sc.fp64_solves;
     h[2] = sc.n_active;
     h[3] = pl->g.npair;
+    return AF_OK;
+}
+
+af_status af_set_wait_limit(int tries)
+{
+    g_wait_tries.store(tries >= 0 ? (uint32_t)tries : tc::kWaitTries, std::memory_order_relaxed);
     return AF_OK;
 }
 

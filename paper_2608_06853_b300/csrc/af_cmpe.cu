@@ -9,28 +9,18 @@
 // w2 R_SV from the grid-statistics kernel.
 #include <math.h>
 
+#include "af_cmpe.cuh"
 #include "af_internal.cuh"
 
 namespace {
 
-// pair k of a patch -> (i, j) of its first image; the second is (i+1, j-1)
-__device__ __forceinline__ void pair_ij(int k, int n, int &i, int &j)
-{
-    i = k / (n - 2);
-    int jj = k - i * (n - 2);
-    j = jj < i ? jj + 1 : jj + 2;
-}
+using cmpe::pair_ij;
+using cmpe::warp_sum;
 // index of the pair whose first image is (i, j), or -1
 __device__ __forceinline__ int pair_index(int i, int j, int n)
 {
     if (i < 0 || i > n - 2 || j < 1 || j > n - 1 || j == i + 1) return -1;
     return i * (n - 2) + (j - 1) - (j > i + 1 ? 1 : 0);
-}
-
-__device__ __forceinline__ float warp_sum(float v)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
 }
 
 // one CTA per patch; warp w takes pairs w, w + 8, ...
@@ -47,30 +37,14 @@ __global__ void __launch_bounds__(256) cmpe_forward_kernel(AfGeom g, const float
     double lsum = 0.0;
     int cnt = 0;
     for (int k = w; k < g.npair; k += 8) {
-        int i, j;
-        pair_ij(k, g.nsub, i, j);
-        const float2 *B1 = B + (long)(i * g.nsub + j) * g.npix + base;
-        const float2 *B2 = B + (long)((i + 1) * g.nsub + (j - 1)) * g.npix + base;
-        float zr = 0.f, zi = 0.f, e1 = 0.f, e2 = 0.f;
-#pragma unroll 4
-        for (int q = lane; q < g.patch_npix; q += 32) {
-            const float2 a = B1[q], c = B2[q];
-            zr = fmaf(a.x, c.x, fmaf(a.y, c.y, zr));
-            zi = fmaf(a.y, c.x, fmaf(-a.x, c.y, zi));
-            e1 = fmaf(a.x, a.x, fmaf(a.y, a.y, e1));
-            e2 = fmaf(c.x, c.x, fmaf(c.y, c.y, e2));
-        }
-        zr = warp_sum(zr); zi = warp_sum(zi); e1 = warp_sum(e1); e2 = warp_sum(e2);
+        const cmpe::PairTerms t = cmpe::pair_terms(B, g.nsub, g.npix, base, g.patch_npix, k, lane);
         if (lane == 0) {
-            // float epilogue (the sums are float); sqrt of each energy avoids overflow
-            const float den = sqrtf(e1) * sqrtf(e2);
-            const float rho = den > 0.0f ? hypotf(zr, zi) / den : 0.0f;
-            const int m = rho >= g.rho_thresh;
+            const int m = t.rho >= g.rho_thresh;
             const long o = (long)P * g.npair + k;
-            z[o] = make_float2(zr, zi);
+            z[o] = make_float2(t.zr, t.zi);
             mask[o] = (uint8_t)m;
             if (m) {
-                lsum += (double)fabsf(atan2f(zi, zr));
+                lsum += (double)fabsf(atan2f(t.zi, t.zr));
                 ++cnt;
             }
         }
@@ -106,6 +80,7 @@ __global__ void __launch_bounds__(256) cmpe_finalize_kernel(AfGeom g, const doub
     if (threadIdx.x == 0) {
         const int M = s_c[0];
         const double lc = s_a[0] / (M > 1 ? M : 1);
+        scal->cmpe_sum = s_a[0];
         scal->lcmpe = (float)lc;
         scal->n_active = M;
         scal->inv_m = (float)(1.0 / (M > 1 ? M : 1));
@@ -115,6 +90,35 @@ __global__ void __launch_bounds__(256) cmpe_finalize_kernel(AfGeom g, const doub
             loss[2] = scal->rtv;
             loss[3] = scal->rsv;
         }
+    }
+}
+
+// {sum m |arg z|, M} of the last forward, for callers that add them over plans
+__global__ void cmpe_totals_kernel(const AfScal *__restrict__ scal, double *__restrict__ out)
+{
+    out[0] = scal->cmpe_sum;
+    out[1] = (double)scal->n_active;
+}
+
+// Replaces the plan's CMPE normalisation by totals added over several plans (a
+// patch-sharded run): L_CMPE = sum / max(1, M) of the whole problem, which the
+// adjoint then differentiates; the loss vector is rewritten the way the finalize
+// kernel writes it (the regularisers are this plan's own).
+__global__ void cmpe_set_totals_kernel(AfGeom g, const double *__restrict__ in, AfScal *scal,
+                                       float *__restrict__ loss)
+{
+    const double sum = in[0];
+    const int M = (int)llrint(in[1]);
+    const double lc = sum / (M > 1 ? M : 1);
+    scal->cmpe_sum = sum;
+    scal->n_active = M;
+    scal->lcmpe = (float)lc;
+    scal->inv_m = (float)(1.0 / (M > 1 ? M : 1));
+    if (loss) {
+        loss[0] = (float)(lc + (double)g.w1 * scal->rtv + (double)g.w2 * scal->rsv);
+        loss[1] = (float)lc;
+        loss[2] = scal->rtv;
+        loss[3] = scal->rsv;
     }
 }
 
@@ -229,6 +233,18 @@ cudaError_t launch_cmpe_forward(af_plan_t pl, float *loss)
     AfGeom g = pl->g;
     if (g.npair == 0) g.n_patch = 0;     // no terms: L_CMPE = 0
     cmpe_finalize_kernel<<<1, 256, 0, pl->stream>>>(g, pl->patch_sum, pl->patch_cnt, pl->scal, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cmpe_totals(af_plan_t pl, double *out)
+{
+    cmpe_totals_kernel<<<1, 1, 0, pl->stream>>>(pl->scal, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cmpe_set_totals(af_plan_t pl, const double *in, float *loss)
+{
+    cmpe_set_totals_kernel<<<1, 1, 0, pl->stream>>>(pl->g, in, pl->scal, loss);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,59 @@
+// The per-pair arithmetic of the common-midpoint phase error (Sec. II-D), shared
+// by the planned forward (af_cmpe.cu) and the allocation-free entry point
+// (af_noalloc.cu) so that both follow one reading of the CMPE:
+// per patch and per pair of common-midpoint subaperture images (i, j) ~
+// (i+1, j-1), with the reciprocal pair j = i + 1 skipped,
+//   z = sum_p B_ij(p) conj(B_i+1,j-1(p)),
+//   rho = |z| / sqrt(sum |B_ij|^2 sum |B_i+1,j-1|^2).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace cmpe {
+
+// pair k of a patch -> (i, j) of its first image; the second is (i+1, j-1)
+__device__ __forceinline__ void pair_ij(int k, int n, int &i, int &j)
+{
+    i = k / (n - 2);
+    int jj = k - i * (n - 2);
+    j = jj < i ? jj + 1 : jj + 2;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+struct PairTerms {
+    float zr, zi, rho;    // z and the correlation coefficient (every lane holds them)
+};
+
+// One warp: the cross term and correlation of pair k of the patch whose pixels start
+// at `base` (B is [nsub * nsub][npix] complex, lanes stride over the patch's pixels).
+__device__ __forceinline__ PairTerms pair_terms(const float2 *__restrict__ B, int nsub, int npix, int base,
+                                               int patch_npix, int k, int lane)
+{
+    int i, j;
+    pair_ij(k, nsub, i, j);
+    const float2 *B1 = B + (long)(i * nsub + j) * npix + base;
+    const float2 *B2 = B + (long)((i + 1) * nsub + (j - 1)) * npix + base;
+    float zr = 0.f, zi = 0.f, e1 = 0.f, e2 = 0.f;
+#pragma unroll 4
+    for (int q = lane; q < patch_npix; q += 32) {
+        const float2 a = B1[q], c = B2[q];
+        zr = fmaf(a.x, c.x, fmaf(a.y, c.y, zr));
+        zi = fmaf(a.y, c.x, fmaf(-a.x, c.y, zi));
+        e1 = fmaf(a.x, a.x, fmaf(a.y, a.y, e1));
+        e2 = fmaf(c.x, c.x, fmaf(c.y, c.y, e2));
+    }
+    zr = warp_sum(zr);
+    zi = warp_sum(zi);
+    e1 = warp_sum(e1);
+    e2 = warp_sum(e2);
+    // float epilogue (the sums are float); sqrt of each energy avoids overflow
+    const float den = sqrtf(e1) * sqrtf(e2);
+    return PairTerms{zr, zi, den > 0.0f ? hypotf(zr, zi) / den : 0.0f};
+}
+
+}  // namespace cmpe

@@ -13,8 +13,8 @@ namespace {
 // deadzone D_k(x) = max(0, |x| - k)  (Sec. II-D)
 __device__ __forceinline__ float deadzone(float x, float k) { return fmaxf(fabsf(x) - k, 0.0f); }
 
-// c_med = mean(1/s) (Sec. III-A), the two regularisers of Eq. 10-11 on c = 1/s,
-// and the numeric check of the slowness map, in two steps: kStatBlocks CTAs
+// c_med = mean(1/s) (Sec. III-A), the two regularisers of Eq. 10-11 on
+// c = 1 / (c_unit s) (the speed in km/s, positions in mm), and the numeric check of the slowness map, in two steps: kStatBlocks CTAs
 // write partial sums {sum 1/s, sum of the Eq. 10 terms, sum of the Eq. 11 terms,
 // bad-value flag}, and one CTA adds them in a fixed order.
 __global__ void __launch_bounds__(256) grid_stats_partial_kernel(AfGeom g, const float *__restrict__ s,
@@ -29,16 +29,18 @@ __global__ void __launch_bounds__(256) grid_stats_partial_kernel(AfGeom g, const
         int j = k / g.nx, i = k - j * g.nx;
         float sv = s[k];
         if (!(sv > 0.0f) || !isfinite(sv)) bad = 1;
-        float c0 = 1.0f / sv;
-        const float y = c0 - pc_comp, t = pc + y;
+        const float cm = 1.0f / sv;                       // m/s, for c_med
+        const float y = cm - pc_comp, t = pc + y;
         pc_comp = (t - pc) - y;
         pc = t;
-        if (i + 1 < g.nx) pa += deadzone((1.0f / s[k + 1] - c0) / g.hx_mm, g.kx1);
-        if (j + 1 < g.nz) pa += deadzone((1.0f / s[k + g.nx] - c0) / g.hz_mm, g.kz1);
+        const float cu = g.inv_c_unit / sv;                // Eq. 10-11 units
+        auto C = [&](int q) { return g.inv_c_unit / s[q]; };
+        if (i + 1 < g.nx) pa += deadzone((C(k + 1) - cu) / g.hx_mm, g.kx1);
+        if (j + 1 < g.nz) pa += deadzone((C(k + g.nx) - cu) / g.hz_mm, g.kz1);
         if (i >= 1 && i + 1 < g.nx)
-            pb += deadzone((1.0f / s[k + 1] - 2.0f * c0 + 1.0f / s[k - 1]) / (g.hx_mm * g.hx_mm), g.kx2);
+            pb += deadzone((C(k + 1) - 2.0f * cu + C(k - 1)) / (g.hx_mm * g.hx_mm), g.kx2);
         if (j >= 1 && j + 1 < g.nz)
-            pb += deadzone((1.0f / s[k + g.nx] - 2.0f * c0 + 1.0f / s[k - g.nx]) / (g.hz_mm * g.hz_mm), g.kz2);
+            pb += deadzone((C(k + g.nx) - 2.0f * cu + C(k - g.nx)) / (g.hz_mm * g.hz_mm), g.kz2);
     }
     double acc_c = (double)pc - (double)pc_comp, acc_a = pa, acc_b = pb;
     for (int o = 16; o > 0; o >>= 1) {

@@ -39,7 +39,8 @@ __device__ __forceinline__ void stage_operand(uint8_t *dst, const __nv_bfloat16 
 __global__ void __launch_bounds__(128) gemm_bf16_kernel(const __nv_bfloat16 *__restrict__ A,
                                                         const __nv_bfloat16 *__restrict__ B,
                                                         float *__restrict__ D, int M, int N, int K,
-                                                        int a_mn, int b_mn, int *__restrict__ err)
+                                                        int a_mn, int b_mn, int *__restrict__ err,
+                                                        uint32_t wait_tries)
 {
     __shared__ __align__(1024) uint8_t sA[kTile * kChunk * 2];
     __shared__ __align__(1024) uint8_t sB[kTile * kChunk * 2];
@@ -78,9 +79,11 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const __nv_bfloat16 *__r
             }
             tc::mma_commit(&mbar);
         }
-        ok = tc::mbar_wait(&mbar, phase) && ok;
+        ok = tc::mma_wait(&mbar, phase, wait_tries) && ok;
         phase ^= 1u;
-        __syncthreads();                        // shared operands may be overwritten
+        // the products are complete (or the second wait ran out): shared operands may be
+        // overwritten; the CTA stops at the first timeout of any thread
+        if (!__syncthreads_and(ok)) { ok = false; break; }
     }
     tc::fence_after_sync();
     if (ok) {
@@ -94,7 +97,6 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const __nv_bfloat16 *__r
         }
     } else if (threadIdx.x == 0) {
         atomicExch(err, 1);
-        tc::mbar_wait(&mbar, phase);            // bounded second wait for MMAs still in flight
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -118,7 +120,7 @@ extern "C" af_status af_gemm_bf16(const void *d_A, const void *d_B, float *d_D, 
     if (a != cudaSuccess) return af_set_error(AF_ERR_CUDA, "af_gemm_bf16: %s", cudaGetErrorString(a));
     gemm_bf16_kernel<<<grid, 128, kGuardSmem, (cudaStream_t)stream>>>(
         reinterpret_cast<const __nv_bfloat16 *>(d_A), reinterpret_cast<const __nv_bfloat16 *>(d_B), d_D, M, N, K,
-        a_mn_major ? 1 : 0, b_mn_major ? 1 : 0, d_err);
+        a_mn_major ? 1 : 0, b_mn_major ? 1 : 0, d_err, af_wait_tries());
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return af_set_error(AF_ERR_CUDA, "af_gemm_bf16: %s", cudaGetErrorString(e));
     return AF_OK;

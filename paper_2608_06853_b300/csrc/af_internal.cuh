@@ -28,11 +28,13 @@ struct AfGeom {
     float cyc0;                              // frac(fd t0 / 2)
     float rho_thresh;
     float inv_nseg, inv_nseg1;               // 1/N, 1/(N+1)
-    // regularisation (Eq. 10-11), units of m/s per mm
+    // regularisation (Eq. 10-11): speed in units of c_unit m/s (km/s), positions in mm
     float w1, kx1, kz1, w2, kx2, kz2, hx_mm, hz_mm;
     float na_inv, nb_inv;                    // 1 / number of difference terms
     float fix_scale;                         // ray-adjoint fixed-point scale times max |dL/dT|
-    float c_ref, lr, beta1, beta2, omb1, omb2, eps;   // omb = 1 - beta, formed in double
+    float c_unit, inv_c_unit;                // Eq. 9-11 act on c = 1 / (c_unit s)
+    float lr, beta1, beta2, omb1, omb2, eps; // Adam on that c; omb = 1 - beta, formed in double
+    int optimizer;                           // AF_OPT_ADAM or AF_OPT_GD
 };
 
 constexpr int kStatBlocks = 64;     // CTAs of the grid-statistics partial sums
@@ -74,6 +76,7 @@ struct MlpGeom {           // sampling region and lens constants (float64)
 
 // Plan-owned device scalars.
 struct AfScal {
+    double cmpe_sum;     // sum over active CMPE terms of |arg z| (numerator of L_CMPE)
     float sbar;          // 1 / c_med, c_med = mean(1/s)  (Sec. III-A)
     float rtv, rsv;      // Eq. 10, Eq. 11
     float lcmpe;         // CMPE loss
@@ -219,12 +222,17 @@ __device__ __forceinline__ void keys_weights2(float2 t, float2 (&w)[4])
 // records the message returned by af_last_error() and returns st
 af_status af_set_error(af_status st, const char *fmt, ...);
 
+// tries of the first tensor-core completion wait (af_set_wait_limit; default about a second)
+uint32_t af_wait_tries();
+
 // ---- launchers (each in its own .cu file) ----
 cudaError_t launch_grid_stats(af_plan_t pl, const float *s);
 cudaError_t launch_delays(af_plan_t pl, const float *s);
 cudaError_t launch_das_forward(af_plan_t pl);
 cudaError_t launch_cmpe_forward(af_plan_t pl, float *loss);
 cudaError_t launch_cmpe_backward(af_plan_t pl);
+cudaError_t launch_cmpe_totals(af_plan_t pl, double *out);
+cudaError_t launch_cmpe_set_totals(af_plan_t pl, const double *in, float *loss);
 cudaError_t launch_das_adjoint(af_plan_t pl);
 cudaError_t launch_ray_adjoint(af_plan_t pl, const float *s, float *grad);
 cudaError_t launch_adam(af_plan_t pl, const float *grad, float *s, float *m, float *v, int step);

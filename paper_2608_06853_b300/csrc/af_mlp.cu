@@ -104,13 +104,13 @@ __device__ __forceinline__ void mma_tile(uint32_t tmem, const uint8_t *A, int a_
 
 // all threads: make shared writes visible to the tensor core, run one product, wait
 __device__ __forceinline__ bool run_mma(uint32_t tmem, const uint8_t *A, int a_mn, const uint8_t *B, int b_mn,
-                                        uint64_t *mbar, uint32_t &phase)
+                                        uint64_t *mbar, uint32_t &phase, uint32_t wait_tries)
 {
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     if (threadIdx.x == 0) mma_tile(tmem, A, a_mn, B, b_mn, mbar);
-    const bool ok = tc::mbar_wait(mbar, phase);
+    const bool ok = tc::mma_wait(mbar, phase, wait_tries);
     phase ^= 1u;
     tc::fence_after_sync();
     return ok;
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const float4 *__restr
                                                            const __nv_bfloat16 *__restrict__ W2b,
                                                            const __nv_bfloat16 *__restrict__ W3b,
                                                            float *__restrict__ gpart, float *__restrict__ lpart,
-                                                           int *__restrict__ err)
+                                                           int *__restrict__ err, uint32_t wait_tries)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sW2 = smem, *sW3 = smem + TB, *sH1 = smem + 2 * TB, *sH2 = smem + 3 * TB, *sH3 = smem + 4 * TB;
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const float4 *__restr
     const int row = 32 * warp + lane;                      // == b
 
     // layer 2: Z2 = H1 W2^T
-    ok = run_mma(tmem, sH1, 0, sW2, 0, &mbar, phase) && ok;
+    ok = run_mma(tmem, sH1, 0, sW2, 0, &mbar, phase, wait_tries) && ok;
     for (int c = 0; c < HID; c += 32) {
         float v[32];
         row_chunk(tmem, c, v);
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const float4 *__restr
         store_row32(sH2, row, c, v);
     }
     // layer 3: Z3 = H2 W3^T; layer 4 in the epilogue
-    ok = run_mma(tmem, sH2, 0, sW3, 0, &mbar, phase) && ok;
+    ok = run_mma(tmem, sH2, 0, sW3, 0, &mbar, phase, wait_tries) && ok;
     float y0 = P[OFF_B4], y1 = P[OFF_B4 + 1];
     for (int c = 0; c < HID; c += 32) {
         float v[32];
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const float4 *__restr
         if (j == 0) lpart[blockIdx.x] = sloss[0] + sloss[1] + sloss[2] + sloss[3];
     }
     // dW3 = dZ3^T H2  (A = sG as MN-major, B = sH2 as MN-major); rows of D = output feature
-    ok = run_mma(tmem, sG, 1, sH2, 1, &mbar, phase) && ok;
+    ok = run_mma(tmem, sG, 1, sH2, 1, &mbar, phase, wait_tries) && ok;
     for (int c = 0; c < HID; c += 32) {
         float v[32];
         row_chunk(tmem, c, v);
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const float4 *__restr
         for (int k = 0; k < 32; ++k) gp[OFF_W3 + row * HID + c + k] = v[k];
     }
     // dH2 = dZ3 W3 (A = sG K-major, B = sW3 as MN-major) -> dZ2 into sG
-    ok = run_mma(tmem, sG, 0, sW3, 1, &mbar, phase) && ok;
+    ok = run_mma(tmem, sG, 0, sW3, 1, &mbar, phase, wait_tries) && ok;
     __syncthreads();                                        // every read of dZ3 is done
     for (int c = 0; c < HID; c += 32) {
         float v[32];
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const float4 *__restr
         gp[OFF_B2 + j] = g2;
     }
     // dW2 = dZ2^T H1
-    ok = run_mma(tmem, sG, 1, sH1, 1, &mbar, phase) && ok;
+    ok = run_mma(tmem, sG, 1, sH1, 1, &mbar, phase, wait_tries) && ok;
     for (int c = 0; c < HID; c += 32) {
         float v[32];
         row_chunk(tmem, c, v);
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const float4 *__restr
         for (int k = 0; k < 32; ++k) gp[OFF_W2 + row * HID + c + k] = v[k];
     }
     // dH1 = dZ2 W2 -> dZ1 (f32) into sF
-    ok = run_mma(tmem, sG, 0, sW2, 1, &mbar, phase) && ok;
+    ok = run_mma(tmem, sG, 0, sW2, 1, &mbar, phase, wait_tries) && ok;
     __syncthreads();                                        // sH2 / sH3 / sG are free now
     for (int c = 0; c < HID; c += 32) {
         float v[32];
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const float4 *__restr
         gp[OFF_W1 + j * 4 + 2] = w2;
         gp[OFF_W1 + j * 4 + 3] = w3;
     }
-    if (!ok && b == 0) atomicExch(err, 1);
+    if (!ok) atomicExch(err, 1);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
@@ -412,7 +412,8 @@ __global__ void __launch_bounds__(kInferThreads) mlp_infer_kernel(AfGeom g, MlpN
                                                                   const AfScal *__restrict__ scal, float c_fixed,
                                                                   const uint8_t *__restrict__ fb,
                                                                   float *__restrict__ phi_out,
-                                                                  float *__restrict__ tl_out, int *__restrict__ err)
+                                                                  float *__restrict__ tl_out, int *__restrict__ err,
+                                                                  uint32_t wait_tries)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sW2 = smem, *sW3 = smem + TB, *sH = smem + 2 * TB;
@@ -465,7 +466,7 @@ __global__ void __launch_bounds__(kInferThreads) mlp_infer_kernel(AfGeom g, MlpN
             }
             store_row32(sH, row, c0 + cc, v);
         }
-        ok = run_mma(tmem, sH, 0, sW2, 0, &mbar, phase) && ok;
+        ok = run_mma(tmem, sH, 0, sW2, 0, &mbar, phase, wait_tries) && ok;
         __syncthreads();                                   // the MMA has consumed H1
 #pragma unroll
         for (int cc = 0; cc < kHalf; cc += 32) {
@@ -475,7 +476,7 @@ __global__ void __launch_bounds__(kInferThreads) mlp_infer_kernel(AfGeom g, MlpN
             for (int k = 0; k < 32; ++k) v[k] = tanh_fast(v[k] + sB2[c0 + cc + k]);
             store_row32(sH, row, c0 + cc, v);
         }
-        ok = run_mma(tmem, sH, 0, sW3, 0, &mbar, phase) && ok;
+        ok = run_mma(tmem, sH, 0, sW3, 0, &mbar, phase, wait_tries) && ok;
         float y0 = 0.0f, y1 = 0.0f;
 #pragma unroll
         for (int cc = 0; cc < kHalf; cc += 32) {
@@ -496,7 +497,7 @@ __global__ void __launch_bounds__(kInferThreads) mlp_infer_kernel(AfGeom g, MlpN
             if (tl_out) tl_out[idx] = n.y1_c + (b41 + y1 + q.y) * n.y1_s;
         }
     }
-    if (!ok && b == 0) atomicExch(err, 1);
+    if (!ok) atomicExch(err, 1);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, HID);
@@ -591,7 +592,7 @@ cudaError_t mlp_train_step(af_plan_t pl, const float4 *X, const float2 *Y, long 
 {
     mlp_train_kernel<<<ntiles, 128, kTrainSmem, pl->stream>>>(
         X, Y, first, 1.0f / (ntiles * TILE), pl->mlp_p, reinterpret_cast<const __nv_bfloat16 *>(pl->mlp_w2b),
-        reinterpret_cast<const __nv_bfloat16 *>(pl->mlp_w3b), gpart, lpart, &pl->scal->mlp_err);
+        reinterpret_cast<const __nv_bfloat16 *>(pl->mlp_w3b), gpart, lpart, &pl->scal->mlp_err, af_wait_tries());
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const double bc1 = 1.0 - pow(0.9, step), bc2 = 1.0 - pow(0.999, step);
@@ -607,7 +608,7 @@ cudaError_t mlp_infer(af_plan_t pl, float c_fixed, const uint8_t *fb, float *phi
     mlp_infer_kernel<<<pl->sm_count * 2, kInferThreads, kInferSmem, pl->stream>>>(
         pl->g, pl->mlp_norm, pl->mlp_p, reinterpret_cast<const __nv_bfloat16 *>(pl->mlp_w2b),
         reinterpret_cast<const __nv_bfloat16 *>(pl->mlp_w3b), pl->elem_pol, pl->pix_pol, pl->scal, c_fixed, fb,
-        phi_out, tl_out, &pl->scal->mlp_err);
+        phi_out, tl_out, &pl->scal->mlp_err, af_wait_tries());
     return cudaGetLastError();
 }
 

@@ -11,9 +11,11 @@
 // every GPU that loads the library holds until the process exits.
 //
 // Rules of use (also stated in include/af.h):
-//  - The first call on a device looks up the device address of the scratch
-//    array (cudaGetSymbolAddress) with that device current; make that first
-//    call before any stream capture.
+//  - Every call looks up the device address of the scratch array on the
+//    current device (cudaGetSymbolAddress, no allocation); the first call on a
+//    device may load the library's device code there, so make it before any
+//    stream capture.  Nothing is cached, so a device reset between calls
+//    (cudaDeviceReset) leaves the entry point usable.
 //  - Every call shares the one scratch array.  Calls that overlap on the GPU
 //    (different streams, or different host threads without ordering) race on
 //    it; order them on one stream or synchronise between them.
@@ -22,8 +24,8 @@
 //  - n_patch above AF_NOALLOC_MAX_PATCHES is rejected with
 //    AF_ERR_UNSUPPORTED; nothing here calls cudaMalloc or cudaFree.
 #include <math.h>
-#include <mutex>
 
+#include "af_cmpe.cuh"
 #include "af_internal.cuh"
 
 namespace {
@@ -36,18 +38,8 @@ struct PatchPartial {
 
 static __device__ __align__(256) PatchPartial g_patch_partials[AF_NOALLOC_MAX_PATCHES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_lock;
-PatchPartial *g_scratch[kMaxDevices] = {};
-
-__device__ __forceinline__ float warp_sum_na(float v)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// one CTA per patch, warp w takes pairs w, w + 8, ... (same reading of the
-// CMPE as the planned path: pairs (i,j) ~ (i+1, j-1), j = i + 1 skipped)
+// one CTA per patch, warp w takes pairs w, w + 8, ... (the pair arithmetic of the
+// planned path, cmpe::pair_terms)
 __global__ void __launch_bounds__(256) noalloc_patch_kernel(const float2 *__restrict__ B, int nsub,
                                                             int npix, int patch_npix, float rho_thresh,
                                                             PatchPartial *__restrict__ part)
@@ -60,28 +52,10 @@ __global__ void __launch_bounds__(256) noalloc_patch_kernel(const float2 *__rest
     double lsum = 0.0;
     int cnt = 0;
     for (int k = w; k < npair; k += 8) {
-        const int i = k / (nsub - 2), jj = k - i * (nsub - 2);
-        const int j = jj < i ? jj + 1 : jj + 2;
-        const float2 *B1 = B + (long)(i * nsub + j) * npix + base;
-        const float2 *B2 = B + (long)((i + 1) * nsub + (j - 1)) * npix + base;
-        float zr = 0.f, zi = 0.f, e1 = 0.f, e2 = 0.f;
-#pragma unroll 4
-        for (int q = lane; q < patch_npix; q += 32) {
-            const float2 a = B1[q], c = B2[q];
-            zr = fmaf(a.x, c.x, fmaf(a.y, c.y, zr));
-            zi = fmaf(a.y, c.x, fmaf(-a.x, c.y, zi));
-            e1 = fmaf(a.x, a.x, fmaf(a.y, a.y, e1));
-            e2 = fmaf(c.x, c.x, fmaf(c.y, c.y, e2));
-        }
-        zr = warp_sum_na(zr); zi = warp_sum_na(zi); e1 = warp_sum_na(e1); e2 = warp_sum_na(e2);
-        if (lane == 0) {
-            // float epilogue (the sums are float); sqrt of each energy avoids overflow
-            const float den = sqrtf(e1) * sqrtf(e2);
-            const float rho = den > 0.0f ? hypotf(zr, zi) / den : 0.0f;
-            if (rho >= rho_thresh) {
-                lsum += (double)fabsf(atan2f(zi, zr));
-                ++cnt;
-            }
+        const cmpe::PairTerms t = cmpe::pair_terms(B, nsub, npix, base, patch_npix, k, lane);
+        if (lane == 0 && t.rho >= rho_thresh) {
+            lsum += (double)fabsf(atan2f(t.zi, t.zr));
+            ++cnt;
         }
     }
     if (lane == 0) { s_sum[w] = lsum; s_cnt[w] = cnt; }
@@ -118,21 +92,14 @@ __global__ void __launch_bounds__(256) noalloc_finalize_kernel(const PatchPartia
     }
 }
 
-// device address of the scratch array on the current device (looked up once per device)
+// device address of the scratch array on the current device (looked up on every call:
+// host code cannot use the array's name as a device pointer)
 cudaError_t scratch_for_current_device(PatchPartial **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_patch_partials);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> guard(g_lock);
-    if (!g_scratch[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_patch_partials);
-        if (e != cudaSuccess) return e;
-        g_scratch[dev] = static_cast<PatchPartial *>(p);
-    }
-    *out = g_scratch[dev];
+    *out = static_cast<PatchPartial *>(p);
     return cudaSuccess;
 }
 

@@ -326,7 +326,8 @@ __device__ __forceinline__ float dz_sign(float x, float k)      // D_k'(x)
     return fabsf(x) <= k ? 0.0f : (x > 0.0f ? 1.0f : -1.0f);
 }
 
-// grad[k] = sum_c gpart[c][k] / S + d(w1 R_TV + w2 R_SV)/ds_k  (gather form on c = 1/s);
+// grad[k] = sum_c gpart[c][k] / S + d(w1 R_TV + w2 R_SV)/ds_k  (gather form on
+// c = 1 / (c_unit s), the speed in the units of Eq. 10-11);
 // also returns the ray adjoint's block counter to zero for its next launch
 __global__ void __launch_bounds__(256) reduce_grad_kernel(AfGeom g, const float *__restrict__ s,
                                                           const long long *__restrict__ gpart, int nparts,
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(256) reduce_grad_kernel(AfGeom g, const float 
     const float gmax = __int_as_float(scal->gmax_bits);
     const float acc = gmax > 0.0f ? (float)((double)tot * ((double)gmax / (double)g.fix_scale)) : 0.0f;
     const int j = k / g.nx, i = k - j * g.nx, nx = g.nx, nz = g.nz;
-    auto C = [&](int ii, int jj) { return 1.0f / s[jj * nx + ii]; };
+    auto C = [&](int ii, int jj) { return g.inv_c_unit / s[jj * nx + ii]; };
     const float hx = g.hx_mm, hz = g.hz_mm, hx2 = hx * hx, hz2 = hz * hz;
     float dc = 0.0f;   // dR/dc_k
     // Eq. 10: forward differences touching node k
@@ -365,23 +366,29 @@ __global__ void __launch_bounds__(256) reduce_grad_kernel(AfGeom g, const float 
     }
     dc += g.w2 * g.nb_inv * b;
     const float c0 = C(i, j);
-    grad[k] = acc - dc * c0 * c0;     // dc/ds = -c^2
+    grad[k] = acc - dc * (c0 * c0 * g.c_unit);     // dc/ds = -c_unit c^2
 }
 
-// Adam on u = s * c_ref (Eq. 9 with Adam moments)
+// Eq. 9 on the sound speed c = 1 / (c_unit s) (km/s): the plain gradient step as
+// printed (AF_OPT_GD) or with Adam moments; dL/dc = dL/ds ds/dc, ds/dc = -c_unit s^2
 __global__ void __launch_bounds__(256) adam_kernel(AfGeom g, const float *__restrict__ grad,
                                                    float *__restrict__ s, float *__restrict__ m,
                                                    float *__restrict__ v, float bc1, float bc2)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.ng) return;
-    const float gu = grad[k] / g.c_ref;
-    const float mk = fmaf(g.beta1, m[k], g.omb1 * gu);
-    const float vk = fmaf(g.beta2, v[k], g.omb2 * gu * gu);
+    const float sk = s[k];
+    const float gc = -grad[k] * (g.c_unit * sk * sk);
+    if (g.optimizer == AF_OPT_GD) {
+        s[k] = g.inv_c_unit / (g.inv_c_unit / sk - g.lr * gc);
+        return;
+    }
+    const float mk = fmaf(g.beta1, m[k], g.omb1 * gc);
+    const float vk = fmaf(g.beta2, v[k], g.omb2 * gc * gc);
     m[k] = mk;
     v[k] = vk;
-    const float u = s[k] * g.c_ref - g.lr * (mk / bc1) / (sqrtf(vk / bc2) + g.eps);
-    s[k] = u / g.c_ref;
+    const float c = g.inv_c_unit / sk - g.lr * (mk / bc1) / (sqrtf(vk / bc2) + g.eps);
+    s[k] = g.inv_c_unit / c;
 }
 
 }  // namespace

@@ -100,8 +100,11 @@ __device__ __forceinline__ void fence_mbar_init()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// tries of a completion wait before it gives up (about a second)
+constexpr uint32_t kWaitTries = 1u << 26;
+
 // bounded wait for the phase with the given parity; returns false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint32_t max_iter = 1u << 26)
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint32_t max_iter = kWaitTries)
 {
     const uint32_t a = smem_addr(mbar);
     for (uint32_t it = 0; it < max_iter; ++it) {
@@ -113,6 +116,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint3
             : "=r"(done) : "r"(a), "r"(parity) : "memory");
         if (done) return true;
     }
+    return false;
+}
+
+// Wait for the MMAs committed to mbar: first with `first_tries` tries (a test hook
+// may make it small); if that runs out, wait again with the default bound so that the
+// products have finished before their operands, accumulators or tensor memory are
+// touched again.  Returns false if the first wait ran out (the caller reports it).
+__device__ __forceinline__ bool mma_wait(uint64_t *mbar, uint32_t parity, uint32_t first_tries)
+{
+    if (mbar_wait(mbar, parity, first_tries)) return true;
+    mbar_wait(mbar, parity);
     return false;
 }
 

@@ -23,9 +23,12 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libsynth.so")
+_GPU_LIB_PATH = os.path.join(_HERE, "libsynth_gpu.so")
 _lib = None
+_gpu_lib = None
 
 C_REF = 1540.0  # beamforming reference speed (m/s); lambda/2 pixel spacing uses it
+C_UNIT = 1000.0  # Eq. 9-11 take the sound speed in km/s (Table II's LR and kappa values)
 
 
 def build(force: bool = False) -> str:
@@ -34,6 +37,16 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
         subprocess.check_call(["gcc", "-O3", "-fopenmp", "-shared", "-fPIC", "-o", _LIB_PATH, src, "-lm"])
     return _LIB_PATH
+
+
+def build_gpu(force: bool = False) -> str:
+    """Compile synth_gpu.cu (the GPU echo simulator) into libsynth_gpu.so for sm_103a."""
+    src = os.path.join(_HERE, "synth_gpu.cu")
+    if force or not os.path.exists(_GPU_LIB_PATH) or os.path.getmtime(_GPU_LIB_PATH) < os.path.getmtime(src):
+        nvcc = os.environ.get("NVCC", "nvcc")
+        subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo",
+                               "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-o", _GPU_LIB_PATH, src])
+    return _GPU_LIB_PATH
 
 
 class _Medium(ctypes.Structure):
@@ -61,6 +74,20 @@ def _load():
         lib.sy_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
+
+
+def _load_gpu():
+    global _gpu_lib
+    if _gpu_lib is None:
+        build_gpu()
+        lib = ctypes.CDLL(_GPU_LIB_PATH)
+        vp, d, i, ll = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_longlong
+        lib.sy_gpu_oneway_times.argtypes = [i, vp, vp, d, d, d, d, d, i, ctypes.POINTER(_Medium), ll, vp, vp, vp]
+        lib.sy_gpu_oneway_times.restype = i
+        lib.sy_gpu_echoes.argtypes = [i, ll, vp, vp, i, d, d, d, d, d, vp]
+        lib.sy_gpu_echoes.restype = i
+        _gpu_lib = lib
+    return _gpu_lib
 
 
 def f32(x):
@@ -153,7 +180,9 @@ class Problem:
     beta1: float = 0.9
     beta2: float = 0.999
     eps: float = 1e-8
-    c_ref: float = C_REF
+    c_ref: float = C_REF      # reference speed of the patch geometry (lambda/2 pixels)
+    c_unit: float = C_UNIT    # m/s per unit of the speed that Eq. 9-11 act on (km/s)
+    optimizer: int = 0        # update of Eq. 9: 0 Adam on c, 1 the plain gradient step as printed
     medium: Optional[Medium] = None
     sector_half_angle: float = 0.0    # curved array: sector half angle; linear: half width (m)
     depth_range: tuple = (0.0, 0.0)
@@ -367,9 +396,10 @@ def config_full(seed: int = 20261204, **over) -> Problem:
     ph = rng.uniform(0, 2 * np.pi)
     medium = Medium(speeds=[1600.0, 1440.0, 1560.0], base=[3e-3, 3e-3 + h_fat],
                     amp=[0.0, 3e-3], period=[0.0, 20e-3], phase=[0.0, ph])
-    # Table II in vivo column, except the learning rate: 0.05 on u = s * 1540 moves
-    # every node by up to 77 m/s per Adam step and leaves the speed range within a few
-    # iterations, so the C5-2v phantom value (0.003, ~4.6 m/s per step) is used.
+    # Table II in vivo column, except the learning rate of the default Adam update: 0.05
+    # km/s moves every node by 50 m/s per Adam step and the map leaves the speed range
+    # within a few iterations, so the C5-2v phantom value (0.003, 3 m/s per step) is used.
+    # Eq. 9 as printed (optimizer=1, a plain gradient step) runs the in vivo value.
     hyper = dict(TABLE2["invivo_c5"], lr=TABLE2["phantom_c5"]["lr"])
     kw = dict(ne=128, radius=60e-3, pitch=0.35e-3, fc=3.5e6, d_lens=1.2e-3, c_lens=1000.0,
               ns=3072, fs=14e6, nx=128, nz=128, n_ang=20, n_rad=20, patch_w=9,
@@ -457,6 +487,67 @@ def simulate(problem: Problem, n_scatterers: int, seed: int,
     x, z, a = sector_scatterers(problem, n_scatterers, seed)
     T = oneway_times(problem, x, z, medium)
     return echoes(problem, T, a)
+
+
+def oneway_times_gpu(problem: Problem, kx, kz, medium: Optional[Medium] = None):
+    """The true one-way times of `oneway_times`, computed on the current CUDA device in
+    float64; returns a torch tensor [ne][nk] (float64, device)."""
+    import torch
+    lib = _load_gpu()
+    dev = torch.device("cuda")
+    med = (medium or problem.medium or Medium(speeds=[C_REF])).to_c()
+    ex = torch.as_tensor(np.asarray(problem.elem_x, np.float64), device=dev)
+    ez = torch.as_tensor(np.asarray(problem.elem_z, np.float64), device=dev)
+    kxd = torch.as_tensor(np.asarray(kx, np.float64), device=dev)
+    kzd = torch.as_tensor(np.asarray(kz, np.float64), device=dev)
+    T = torch.empty((problem.ne, kxd.shape[0]), dtype=torch.float64, device=dev)
+    kind = {0: 1, 1: 0, 2: 2}[int(problem.lens_mode)]
+    torch.cuda.synchronize()
+    rc = lib.sy_gpu_oneway_times(problem.ne, ex.data_ptr(), ez.data_ptr(), problem.arc_cx, problem.arc_cz,
+                                 problem.lens_radius, problem.lens_z, problem.c_lens, kind, ctypes.byref(med),
+                                 kxd.shape[0], kxd.data_ptr(), kzd.data_ptr(), T.data_ptr())
+    if rc != 0:
+        raise RuntimeError(f"sy_gpu_oneway_times failed ({rc})")
+    return T
+
+
+def echoes_gpu(problem: Problem, T, amp, sigma: Optional[float] = None):
+    """`echoes` on the current CUDA device: T [ne][nk] float64 torch tensor (device),
+    amp [nk]; returns Psi [ne][ne][ns] complex64 (device)."""
+    import torch
+    lib = _load_gpu()
+    dev = torch.device("cuda")
+    ampd = torch.as_tensor(np.asarray(amp, np.float64), device=dev)
+    T = T.contiguous()
+    sig = pulse_sigma(problem.fc) if sigma is None else sigma
+    out = torch.empty((problem.ne, problem.ne, problem.ns), dtype=torch.complex64, device=dev)
+    torch.cuda.synchronize()
+    rc = lib.sy_gpu_echoes(problem.ne, T.shape[1], T.data_ptr(), ampd.data_ptr(), problem.ns, problem.fs,
+                           problem.fd, problem.t0, problem.t_ttp, sig, out.data_ptr())
+    if rc != 0:
+        raise RuntimeError(f"sy_gpu_echoes failed ({rc})")
+    return out
+
+
+def speckle_count(problem: Problem, per_cell: float = 10.0, depth=(2e-3, None)) -> int:
+    """Scatterers for `per_cell` per resolution cell (lambda^2, lambda = c_ref / fc) over
+    the area `sector_scatterers` draws from (curved arrays)."""
+    RL = problem.lens_radius
+    d1 = depth[1] if depth[1] is not None else problem.depth_range[1] + 10e-3
+    half = 1.15 * problem.sector_half_angle
+    area = half * ((RL + d1) ** 2 - (RL + depth[0]) ** 2)
+    lam = C_REF / problem.fc
+    return int(round(per_cell * area / lam ** 2))
+
+
+def simulate_gpu(problem: Problem, n_scatterers: int, seed: int, medium: Optional[Medium] = None):
+    """`simulate` on the current CUDA device (same scatterers, same physics); returns
+    Psi as a complex64 torch tensor on the device."""
+    x, z, a = sector_scatterers(problem, n_scatterers, seed)
+    T = oneway_times_gpu(problem, x, z, medium)
+    psi = echoes_gpu(problem, T, a)
+    del T
+    return psi
 
 
 def segment_time(medium: Medium, ax, az, bx, bz) -> float:

@@ -143,3 +143,28 @@ def test_batch_calls_validate_arguments_on_the_host():
     assert lib.af_batch_iterate(None, None, None, None, None, None, None, 1, None) == af.AF_ERR_ARG
     assert lib.af_batch_capture(None, None, None, None, None, None, None, None, 1, 1) == af.AF_ERR_ARG
     assert lib.af_batch_destroy(None) == af.AF_OK
+
+
+def test_noalloc_wrapper_checks_arguments_before_any_call():
+    """The allocation-free CMPE entry point reads nsub^2 * n_patch * patch_npix complex
+    values; the binding refuses tensors that do not hold exactly that many, have the
+    wrong dtype or layout, or are not on the current CUDA device, before calling it."""
+    torch = pytest.importorskip("torch")
+    nsub, n_patch, npix = 4, 3, 9
+    loss = torch.zeros(1)
+    short = torch.zeros((nsub * nsub, n_patch * npix - 1), dtype=torch.complex64)
+    with pytest.raises(ValueError, match="complex values"):
+        af.af_cmpe_loss_noalloc(short, nsub, n_patch, npix, 0.9, loss)
+    with pytest.raises(ValueError, match="complex64"):
+        af.af_cmpe_loss_noalloc(torch.zeros((nsub * nsub, n_patch * npix), dtype=torch.complex128),
+                                nsub, n_patch, npix, 0.9, loss)
+    good = torch.zeros((nsub * nsub, n_patch * npix), dtype=torch.complex64)
+    with pytest.raises(ValueError, match="contiguous"):
+        af.af_cmpe_loss_noalloc(torch.zeros((n_patch * npix, nsub * nsub), dtype=torch.complex64).t(),
+                                nsub, n_patch, npix, 0.9, loss)
+    with pytest.raises(ValueError, match="loss"):
+        af.af_cmpe_loss_noalloc(good, nsub, n_patch, npix, 0.9, torch.zeros(1, dtype=torch.float64))
+    with pytest.raises(ValueError, match="n_active"):
+        af.af_cmpe_loss_noalloc(good, nsub, n_patch, npix, 0.9, loss, torch.zeros(1, dtype=torch.int64))
+    with pytest.raises(ValueError, match="CUDA"):
+        af.af_cmpe_loss_noalloc(good, nsub, n_patch, npix, 0.9, loss)

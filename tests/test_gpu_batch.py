@@ -46,7 +46,7 @@ def test_graph_replay_matches_eager_for_uneven_batch():
     s5e, _, l5e = run(5, False)
     s5g, _, l5g = run(5, True)
     for k in range(len(problems)):
-        step = problems[k].lr / problems[k].c_ref
+        step = problems[k].lr * problems[k].c_unit / 1540.0 ** 2    # one Adam step in slowness
         d = np.abs(s5g[k] - s5e[k])
         assert np.isfinite(s5g[k]).all()
         assert d.max() <= 2.0 * step and np.median(d) <= 0.01 * step
@@ -86,7 +86,7 @@ def test_batch_members_match_single_plans(legacy_stream):
         np.testing.assert_allclose(br.loss[k].cpu().numpy(), loss.cpu().numpy(), rtol=1e-5)
         assert torch.linalg.norm(br.g[k] - g) <= 1e-4 * torch.linalg.norm(g)
         # float atomics in the DAS adjoint: near-zero gradients may flip an Adam step
-        step = p.lr / p.c_ref
+        step = p.lr * p.c_unit / 1540.0 ** 2
         d = (br.s[k] - s).abs()
         assert d.max().item() <= 4.0 * step and d.median().item() <= 0.01 * step
         # the member getters reach the batch's plan

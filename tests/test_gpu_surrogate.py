@@ -71,3 +71,62 @@ def test_surrogate_training_fallback_and_delay_error(tiny_plan):
     err = np.abs((T1 - T0).cpu().numpy())[on]
     print(f"surrogate delay error: max {err.max() * 1e9:.4f} ns, tolerance {rep['tolerance'] * 1e9:.3f} ns")
     assert err.max() <= rep["tolerance"]
+
+
+def test_surrogate_gain_over_the_exact_solver_full_size():
+    """What the trained network gains over the method without it, on the 128-element
+    workload: the same plan with the surrogate off and on, timed (CUDA events on the
+    plan's stream) for whole iterations (exit solve warm-started from the previous
+    iteration) and for cold starts (exit angles of moved pixels, as at each speed of the
+    dynamic sweep).  The gain or loss is printed, not asserted; the delay error the
+    surrogate leaves after fallback must stay within lambda/50."""
+    p = synth.config_full()
+    dev = torch.device("cuda")
+    iq = synth.simulate_gpu(p, 150_000, seed=20261203)
+    plan = af.Plan(p)
+    s = torch.from_numpy(p.initial_slowness()).to(dev)
+    g, m, v = torch.zeros_like(s), torch.zeros_like(s), torch.zeros_like(s)
+    loss = torch.zeros(4, device=dev)
+    plan.af_forward(iq, s, loss)
+    rep = plan.surrogate_train(n_samples=10_000_000, epochs=4, tiles_per_step=32, lr=2e-3, seed=1)
+
+    def timed(fn, n):
+        st = plan.stream
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        torch.cuda.synchronize()
+        a.record(st)
+        for _ in range(n):
+            fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    def iterate():
+        plan.af_iterate(iq, s, g, m, v, 1, loss)
+
+    def cold_forward():
+        plan.af_set_pixels(p.pix_x, p.pix_z)           # drops the warm start
+        plan.af_forward(iq, s, loss)
+
+    out = {}
+    for on in (False, True):
+        plan.surrogate_enable(on)
+        s.fill_(1.0 / 1540.0)
+        out[on] = (timed(iterate, 10), timed(cold_forward, 5))
+    plan.surrogate_enable(False)
+    plan.af_forward(iq, s, loss)
+    T0, a0 = plan.delays()
+    plan.surrogate_enable(True)
+    plan.af_forward(iq, s, loss)
+    T1, _ = plan.delays()
+    plan.surrogate_enable(False)
+    on = (a0 == 1).cpu().numpy()
+    err = float(np.abs((T1 - T0).cpu().numpy())[on].max())
+    print(f"surrogate gain, 128-element workload: iteration {out[False][0]:.3f} -> {out[True][0]:.3f} ms "
+          f"({1e3 / out[False][0]:.0f} -> {1e3 / out[True][0]:.0f} it/s); cold-start forward "
+          f"{out[False][1]:.3f} -> {out[True][1]:.3f} ms; max delay error {err * 1e9:.3f} ns "
+          f"(lambda/50 = {rep['tolerance'] * 1e9:.2f} ns); fallback {rep['fallback_fraction']:.4f}")
+    assert err <= rep["tolerance"]
+    assert all(np.isfinite(x) and x > 0 for x in out[False] + out[True])
+    plan.close()

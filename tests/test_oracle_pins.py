@@ -427,22 +427,44 @@ def test_cmpe_pairs_are_common_midpoint_and_skip_reciprocal():
 
 # ---------------------------------------------------------------- regularisers (Eq. 10-11)
 def test_regularizers_closed_form_linear_and_quadratic_speed():
+    """Eq. 10-11 on fields with a known derivative, with c in km/s and positions in mm
+    (the reading of "physical units" used throughout): a lateral gradient of 20 m/s per
+    mm is 0.02 km/s per mm, 0.01 above Table II's kappa; an axial curvature of 10 m/s
+    per mm^2 is 0.01 km/s per mm^2, 0.009 above kappa^(2) = 0.001."""
     p = small()
+    assert p.c_unit == 1000.0
     o = oracle.Oracle(p)
     X, Z = _grid_xy(p)
-    hx = p.dx * 1e3
-    gam = 2.0                                    # m/s per mm along x
+    gam = 20.0                                   # m/s per mm along x
     c = 1500.0 + gam * (X - p.x0) * 1e3
     rtv, rsv = o.regularizers(1.0 / c)
     nt = (p.nx - 1) * p.nz + p.nx * (p.nz - 1)
-    assert rtv == pytest.approx((p.nx - 1) * p.nz * (gam - p.kx1) / nt, rel=1e-9)
+    assert rtv == pytest.approx((p.nx - 1) * p.nz * (gam / 1000.0 - p.kx1) / nt, rel=1e-9)
     assert rsv == pytest.approx(0.0, abs=1e-9)
-    beta = 0.05                                  # c = c0 + beta x^2 (x in mm): d2c = 2 beta
+    beta = 5.0                                   # c = c0 + beta z^2 (z in mm): d2c/dz2 = 2 beta
     c2 = 1500.0 + beta * ((Z - p.z0) * 1e3) ** 2
     rtv2, rsv2 = o.regularizers(1.0 / c2)
     ns_ = (p.nx - 2) * p.nz + p.nx * (p.nz - 2)
-    assert rsv2 == pytest.approx(p.nx * (p.nz - 2) * (2 * beta - p.kz2) / ns_, rel=1e-7)
-    del hx
+    assert rsv2 == pytest.approx(p.nx * (p.nz - 2) * (2 * beta / 1000.0 - p.kz2) / ns_, rel=1e-7)
+    # a gradient inside the deadzone (5 m/s per mm < 10 m/s per mm) costs nothing
+    rtv3, _ = o.regularizers(1.0 / (1500.0 + 5.0 * (X - p.x0) * 1e3))
+    assert rtv3 == 0.0
+
+
+def test_mean_speed_is_the_mean_of_c_on_a_two_valued_map():
+    """c_med of Sec. III-A is the mean sound speed of the grid: on a map with n1 nodes at
+    c1 and n2 at c2 it is (n1 c1 + n2 c2) / n, which differs from the harmonic mean and
+    from 1 / mean(s)."""
+    p = small(nx=7, nz=5)
+    o = oracle.Oracle(p)
+    c = np.full((p.nz, p.nx), 1450.0)
+    c[:2, :] = 1600.0
+    c[4, 5] = 1600.0
+    n1, n2 = int((c == 1600.0).sum()), int((c == 1450.0).sum())
+    cmed = o.mean_speed(1.0 / c)
+    assert cmed == pytest.approx((n1 * 1600.0 + n2 * 1450.0) / (n1 + n2), rel=1e-14)
+    harmonic = (n1 + n2) / (n1 / 1600.0 + n2 / 1450.0)
+    assert abs(cmed - harmonic) > 1.0
 
 
 def test_regularizer_gradient_matches_finite_differences():
@@ -531,18 +553,38 @@ def test_full_gradient_matches_central_differences():
 
 # ---------------------------------------------------------------- optimiser (Eq. 9)
 def test_adam_first_step_is_signed_learning_rate():
-    """Step 1 of Adam: m_hat = g, v_hat = g^2, so u moves by lr * g / (|g| + eps)."""
+    """Step 1 of Adam on c (km/s): m_hat = g_c, v_hat = g_c^2, so c moves by
+    -lr * g_c / (|g_c| + eps), g_c = dL/dc = -dL/ds * 1000 s^2 (Eq. 9 up to the step
+    normalisation)."""
     o = oracle.Oracle(small())
-    s = np.full(5, 1 / 1540.0)
+    s = 1.0 / np.array([1540.0, 1450.0, 1600.0, 1500.0, 1540.0])
     g = np.array([3.0, -2.0, 1e-3, -5e4, 0.0])
     lr = 0.01
     s1, m, v = o.adam(s, g, np.zeros(5), np.zeros(5), 1, lr)
-    du = (s1 - s) * 1540.0
-    gu = g / 1540.0
-    np.testing.assert_allclose(du, -lr * gu / (np.abs(gu) + 1e-8), rtol=1e-9, atol=1e-15)
+    gc = -g * 1000.0 * s * s
+    dc = 1e-3 / s1 - 1e-3 / s                    # km/s
+    np.testing.assert_allclose(dc, -lr * gc / (np.abs(gc) + 1e-8), rtol=1e-9, atol=1e-13)
+    # a positive dL/ds (slower is worse) raises the speed by lr km/s = 10 m/s
+    assert 1.0 / s1[0] - 1540.0 == pytest.approx(10.0, rel=1e-4)   # eps = 1e-8 vs |g_c| ~ 1e-3
     # beta1 = beta2 = 0 keeps it a sign step at every iteration
     s2, _, _ = o.adam(s1, -g, m, v, 2, lr, beta1=0.0, beta2=0.0)
-    np.testing.assert_allclose((s2 - s1) * 1540.0, lr * gu / (np.abs(gu) + 1e-8), rtol=1e-9, atol=1e-15)
+    gc1 = g * 1000.0 * s1 * s1
+    np.testing.assert_allclose(1e-3 / s2 - 1e-3 / s1, -lr * gc1 / (np.abs(gc1) + 1e-8), rtol=1e-9, atol=1e-13)
+
+
+def test_plain_gradient_step_of_eq9_lands_on_the_minimum_of_a_quadratic():
+    """Eq. 9 as printed, c <- c - lr dL/dc with c in km/s: for L = k/2 (c - c*)^2 one step
+    of lr = 1/k lands on c* exactly; the gradient is handed over as dL/ds, so a wrong sign
+    or unit in the chain rule c = 1/(1000 s) misses c*."""
+    o = oracle.Oracle(small())
+    c_star = np.array([1.45, 1.56, 1.60, 1.52])               # km/s
+    c0 = np.array([1.54, 1.50, 1.55, 1.52])
+    k = 3.0
+    s0 = 1e-3 / c0
+    dLdc = k * (c0 - c_star)
+    dLds = dLdc * (-1e-3 / s0 ** 2)                     # c = 1e-3 / s: dc/ds = -1e-3 / s^2
+    s1 = o.gd(s0, dLds, 1.0 / k)
+    np.testing.assert_allclose(1e-3 / s1, c_star, rtol=1e-13)
 
 
 # ---------------------------------------------------------------- MLP reference
@@ -623,3 +665,23 @@ def test_cmcc_matches_cmpe_correlations():
         for j in range(p.nsub):
             C[i * p.nsub + j] = B[(i + j) % B.shape[0]]
     assert M.cmcc(C, p.nsub, p.n_patch, p.patch_npix) == pytest.approx(1.0, rel=1e-12)
+
+
+# ---------------------------------------------------------------- all-core build
+def test_openmp_build_matches_single_thread():
+    """The OpenMP build of the same oracle source (used for full-size checks and the
+    all-core CPU baseline) gives the single-threaded loss, images and mask bit for bit;
+    only the ray adjoint's per-node sums are reduced in another order."""
+    p = small(n_ang=3, n_rad=3, patch_w=3)
+    psi = synth.simulate(p, 600, seed=21)
+    s = 1.0 / (1540.0 + 20.0 * np.random.default_rng(3).standard_normal((p.nz, p.nx)))
+    serial = oracle.Oracle(p)
+    par = oracle.Oracle(p, parallel=True)
+    a, b = serial.loss_grad(psi, s), par.loss_grad(psi, s)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2]) and a[3] == b[3]
+    assert np.linalg.norm(a[1] - b[1]) <= 1e-12 * np.linalg.norm(a[1])
+    T, apod, _ = serial.delays(s)
+    T2, apod2, _ = par.delays(s)
+    assert np.array_equal(T, T2) and np.array_equal(apod, apod2)
+    assert np.array_equal(serial.das(psi, T, apod), par.das(psi, T, apod))
+    assert oracle.omp_threads() >= 1

@@ -48,15 +48,39 @@ def test_noalloc_cmpe_matches_planned_forward_twice(planned_forward):
         assert abs(float(out) - L_ref) <= LOSS_TOL * abs(L_ref), (call, float(out), L_ref)
 
 
+def test_noalloc_calls_leave_device_memory_unchanged(planned_forward):
+    """The point of the entry point: after a first call, further calls change neither
+    the device's free memory (cudaMemGetInfo) nor torch's allocated bytes."""
+    p, plan, B, L_ref, M_ref = planned_forward
+    dev = torch.device("cuda")
+    out = torch.zeros(1, device=dev)
+    n = torch.zeros(1, dtype=torch.int32, device=dev)
+    af.af_cmpe_loss_noalloc(B, p.nsub, p.n_patch, p.patch_npix, p.rho_thresh, out, n)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(5):
+        af.af_cmpe_loss_noalloc(B, p.nsub, p.n_patch, p.patch_npix, p.rho_thresh, out, n)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
+
+
 def test_noalloc_after_a_different_call_uses_fresh_scratch(planned_forward):
-    """A call on fewer patches leaves other scratch entries behind; the next full
-    call must not be affected by them."""
+    """A call on fewer patches gives the loss of those patches and leaves other scratch
+    entries behind; the next full call must not be affected by them."""
     p, plan, B, L_ref, M_ref = planned_forward
     dev = torch.device("cuda")
     out = torch.zeros(1, device=dev)
     half = p.n_patch // 2
     af.af_cmpe_loss_noalloc(B[:, : half * p.patch_npix].contiguous(), p.nsub, half, p.patch_npix,
                             p.rho_thresh, out)
+    torch.cuda.synchronize()
+    # the planned forward's CMPE terms of the first `half` patches
+    z, mask, _ = plan.cmpe()
+    z, mask = z.cpu().numpy()[:half], mask.cpu().numpy()[:half].astype(bool)
+    L_half = np.abs(np.angle(z[mask])).sum() / max(1, int(mask.sum()))
+    assert abs(float(out) - L_half) <= LOSS_TOL * abs(L_half)
     af.af_cmpe_loss_noalloc(B, p.nsub, p.n_patch, p.patch_npix, p.rho_thresh, out)
     torch.cuda.synchronize()
     assert abs(float(out) - L_ref) <= LOSS_TOL * abs(L_ref)
@@ -65,7 +89,8 @@ def test_noalloc_after_a_different_call_uses_fresh_scratch(planned_forward):
 def test_noalloc_rejects_sizes_beyond_its_scratch(planned_forward):
     p, plan, B, L_ref, M_ref = planned_forward
     out = torch.zeros(1, device=torch.device("cuda"))
+    big = torch.zeros((p.nsub * p.nsub, af.AF_NOALLOC_MAX_PATCHES + 1), dtype=torch.complex64, device="cuda")
     with pytest.raises(af.AfError) as ei:
-        af.af_cmpe_loss_noalloc(B, p.nsub, af.AF_NOALLOC_MAX_PATCHES + 1, 1, p.rho_thresh, out)
+        af.af_cmpe_loss_noalloc(big, p.nsub, af.AF_NOALLOC_MAX_PATCHES + 1, 1, p.rho_thresh, out)
     assert ei.value.status == af.AF_ERR_UNSUPPORTED
     assert "exceeds the fixed scratch" in str(ei.value)
