@@ -47,8 +47,10 @@ def test_two_patch_shards_equal_one_plan(maker, n_scat):
     assert int(round(float(tot[1]))) == one.counters()["n_active"] > 0
     # loss of the whole problem on the shard holding the regularisers
     np.testing.assert_allclose(losses[0].cpu().numpy(), L1.cpu().numpy(), rtol=2e-6)
-    # float atomics of the DAS adjoint: the gradients agree to rounding
-    assert float((g2 - g1).norm() / g1.norm()) <= 1e-5
+    # the ray adjoint sums in fixed point scaled by each plan's own max |dL/dT| (about
+    # 1e-5 relative; the tolerance of the ray-adjoint parity tests), and the DAS
+    # adjoint's float atomics add in any order
+    assert float((g2 - g1).norm() / g1.norm()) <= 1e-4
     # Adam normalises per node: nodes with a rounding-level gradient may move differently
     step = p.lr * p.c_unit / 1540.0 ** 2
     d = (s2 - s1).abs()
