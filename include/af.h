@@ -199,6 +199,25 @@ af_status af_batch_destroy(af_batch_t batch);
  * synchronises the plan's stream. */
 af_status af_set_pixels(af_plan_t plan, const double *pix_x, const double *pix_z);
 
+/* Global-speed sweep (Sec. II-C, III-A; Fig. 3): L_CMPE of the uniform map 1/c0
+ * for each of the n_speeds speeds in h_speeds (host, m/s), one forward pass each,
+ * all queued on the plan's stream without host round trips between speeds.
+ *  dynamic = 1: the dynamic CMPE grid.  Before the pass at c0 every patch keeps
+ *    its direction from the lens centre (its lateral position for a flat lens),
+ *    its depth below the lens surface is multiplied by k = c0 / c_ref, and its
+ *    pixels' offsets from the patch centre (the mean of its pixels) by k, so
+ *    each patch observes the same echoes at every c0.  The plan's pixels are
+ *    those of c_ref.  Every moved pixel set is validated on the host first (the
+ *    checks of af_set_pixels; the grid box must cover them).  dynamic = 0: the
+ *    plan's pixels at every speed.
+ *  d_cmpe [n_speeds] float (device): L_CMPE per speed; d_active [n_speeds] int
+ *    (device, may be NULL): active CMPE terms per speed.
+ * Afterwards the plan's pixels are restored and the next af_forward starts
+ * without an exit-angle warm start.  Needs a curved or flat lens surface for
+ * dynamic = 1 (AF_ERR_ARG otherwise). */
+af_status af_sweep(af_plan_t plan, const void *d_iq, const float *d_iq_scale, const double *h_speeds,
+                   int n_speeds, double c_ref, int dynamic, float *d_cmpe, int *d_active);
+
 /* Waits for the plan's stream and returns AF_ERR_NUMERIC if a kernel flagged
  * a non-positive or non-finite slowness since the last call, else AF_OK. */
 af_status af_sync_status(af_plan_t plan);

@@ -93,6 +93,7 @@ def _load(parallel: bool = False):
             "or_das_adjoint": (None, [G, _fp, _dp, _u8p, _dp, _dp]),
             "or_ray_adjoint": (None, [G, _dp, _dp, _u8p, _dp, _dp]),
             "or_loss_grad": (ctypes.c_double, [G, _fp, _dp, _u8p, _u8p, _dp, _dp, _dp, _u8p, _ip]),
+            "or_dynamic_pixels": (None, [G, ctypes.c_double, ctypes.c_double, _dp, _dp]),
             "or_gd": (None, [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double]),
             "or_adam": (None, [ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double,
                                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
@@ -177,6 +178,13 @@ class Oracle:
         out = [ctypes.c_double() for _ in range(3)]
         self.lib.or_exit_from_angle(self.gp, e, phi, *[ctypes.byref(o) for o in out])
         return tuple(o.value for o in out)
+
+    def dynamic_pixels(self, c0, c_ref):
+        """Pixel positions of the dynamic sweep grid at speed c0 (Sec. III-A)."""
+        x = np.empty(self.npix)
+        z = np.empty(self.npix)
+        self.lib.or_dynamic_pixels(self.gp, c0, c_ref, _d(x), _d(z))
+        return x, z
 
     def keys_weights(self, t):
         w = np.empty(4)

@@ -100,6 +100,39 @@ double or_mean_speed(const or_geom *g, const double *s)
 }
 
 /* ------------------------------------------------------------------ */
+/* Sec. III-A: dynamic grid of the global-speed sweep.  At speed c0 the echo of a
+ * reflector at depth h below the lens arrives as from depth h c0 / c_true, so
+ * the patch and its kernel spacing are stretched by c0 / c_ref about the lens
+ * surface to keep observing the same echoes. */
+void or_dynamic_pixels(const or_geom *g, double c0, double c_ref, double *px_out, double *pz_out)
+{
+    double scale = c0 / c_ref;
+    int n = g->patch_npix;
+    for (int P = 0; P < g->n_patch; ++P) {
+        const double *xs = g->px + (size_t)P * n, *zs = g->pz + (size_t)P * n;
+        double mx = 0.0, mz = 0.0;
+        for (int q = 0; q < n; ++q) { mx += xs[q]; mz += zs[q]; }
+        mx /= n;
+        mz /= n;
+        double nx, nz;                               /* moved patch centre */
+        if (g->lens_mode == 2) {
+            nx = mx;
+            nz = g->lens_z + scale * (mz - g->lens_z);
+        } else {
+            double r = sqrt((mx - g->arc_cx) * (mx - g->arc_cx) + (mz - g->arc_cz) * (mz - g->arc_cz));
+            double depth = r - g->lens_radius;
+            double r_new = g->lens_radius + scale * depth;
+            nx = g->arc_cx + (mx - g->arc_cx) * (r_new / r);
+            nz = g->arc_cz + (mz - g->arc_cz) * (r_new / r);
+        }
+        for (int q = 0; q < n; ++q) {
+            px_out[(size_t)P * n + q] = nx + scale * (xs[q] - mx);
+            pz_out[(size_t)P * n + q] = nz + scale * (zs[q] - mz);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* Eq. 8: two-layer path element -> lens surface point q(phi) -> pixel.
  * q(phi) = C + R_L (sin phi, cos phi).  With the element at polar
  * (Re, th_e) and the pixel at (rp, th_p) about the same centre C:

@@ -57,6 +57,12 @@ typedef struct {
 /* threads the library runs on: 1 for the plain build, all host cores for the
  * OpenMP build of the same source */
 int or_omp_threads(void);
+/* Sec. III-A dynamic CMPE grid for the global-speed sweep at speed c0: each
+ * patch keeps its direction from the lens centre (curved lens) or its lateral
+ * position (flat lens), its depth below the lens surface is multiplied by
+ * c0 / c_ref, and its pixels' offsets from the patch centre (the mean of its
+ * pixels) are multiplied by c0 / c_ref.  Writes n_patch * patch_npix positions. */
+void or_dynamic_pixels(const or_geom *g, double c0, double c_ref, double *px_out, double *pz_out);
 /* Eq. 3 (+ linear extrapolation at the two end elements) */
 void or_element_angles(int ne, const double *ex, const double *ez, double *theta);
 /* Eq. 2 + Eq. 4 */

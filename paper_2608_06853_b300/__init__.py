@@ -94,6 +94,8 @@ _SIGNATURES = {
     "af_batch_launch": (ctypes.c_int, [_VP]),
     "af_batch_destroy": (ctypes.c_int, [_VP]),
     "af_sync_status": (ctypes.c_int, [_VP]),
+    "af_sweep": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double,
+                                 ctypes.c_int, _VP, _VP]),
     "af_set_pixels": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "af_get_delays": (ctypes.c_int, [_VP, _VP, _VP]),
     "af_get_exit_angles": (ctypes.c_int, [_VP, _VP]),
@@ -338,6 +340,18 @@ class Plan:
 
     def af_sync_status(self) -> int:
         return self.lib.af_sync_status(self.handle)
+
+    def af_sweep(self, iq, speeds, c_ref, dynamic=True, iq_scale=None):
+        """L_CMPE and active terms of uniform maps at each speed (af_sweep); returns
+        (cmpe [n] float32, active [n] int32) device tensors, queued on the plan's stream."""
+        import torch
+        sp = np.ascontiguousarray(speeds, np.float64)
+        cm = torch.empty(len(sp), dtype=torch.float32, device=self._dev())
+        act = torch.empty(len(sp), dtype=torch.int32, device=self._dev())
+        _check(self.lib.af_sweep(self.handle, _ptr(iq_view(iq)), _ptr(iq_scale),
+                                 sp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(sp), float(c_ref),
+                                 1 if dynamic else 0, _ptr(cm), _ptr(act)), "af_sweep")
+        return cm, act
 
     def af_set_pixels(self, pix_x, pix_z):
         x = np.ascontiguousarray(pix_x, np.float64)

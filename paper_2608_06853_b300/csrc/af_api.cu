@@ -233,7 +233,9 @@ af_status af_workspace_bytes(const af_config *c, size_t *bytes)
     b += (size_t)c->n_patch * npair * (sizeof(float2) + 1);               // z, mask
     b += (size_t)c->n_patch * (sizeof(double) + sizeof(int));
     b += 148 * 8 * ng * sizeof(float);                                     // partial grids (upper bound)
-    b += sizeof(AfScal);
+    b += sizeof(AfScal) + kStatBlocks * sizeof(double4);
+    b += 4 * (size_t)AF_MLP_NPARAM * sizeof(float) + 2 * 128 * 128 * 2 + ne * npix;   // surrogate
+    b += npix * 2 * sizeof(float2) + (size_t)c->n_patch * 5 * sizeof(double) + ng * sizeof(float);   // sweep
     *bytes = b;
     return AF_OK;
 }
@@ -248,8 +250,13 @@ af_status af_destroy(af_plan_t pl)
                     pl->mlp_p, pl->mlp_m, pl->mlp_v, pl->mlp_g, pl->mlp_w2b, pl->mlp_w3b, pl->sur_fb};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    void *sweep_ptrs[] = {pl->pix_base, pl->pix_pol_base, pl->sweep_geo, pl->s_sweep};
+    for (void *p : sweep_ptrs)
+        if (p) cudaFree(p);
     delete[] pl->host_ex;
     delete[] pl->host_ez;
+    delete[] pl->host_px;
+    delete[] pl->host_pz;
     delete pl;
     return AF_OK;
 }
@@ -271,6 +278,15 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
     memcpy(pl->host_ez, c->elem_z, sizeof(double) * c->n_elem);
     pl->cfg.elem_x = pl->host_ex;
     pl->cfg.elem_z = pl->host_ez;
+    {
+        const size_t np = (size_t)c->n_patch * c->patch_npix;
+        pl->host_px = new double[np ? np : 1];
+        pl->host_pz = new double[np ? np : 1];
+        if (np) {
+            memcpy(pl->host_px, c->pix_x, sizeof(double) * np);
+            memcpy(pl->host_pz, c->pix_z, sizeof(double) * np);
+        }
+    }
     pl->cfg.pix_x = pl->cfg.pix_z = nullptr;
     pl->iq_dtype = c->iq_dtype;
     AfGeom &g = pl->g;
@@ -449,6 +465,10 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
     AF_ALLOC(pl->mlp_w2b, 128 * 128 * 2);
     AF_ALLOC(pl->mlp_w3b, 128 * 128 * 2);
     AF_ALLOC(pl->sur_fb, nep);
+    AF_ALLOC(pl->pix_base, npix * sizeof(float2));
+    AF_ALLOC(pl->pix_pol_base, npix * sizeof(float2));
+    AF_ALLOC(pl->sweep_geo, (size_t)g.n_patch * 5 * sizeof(double));
+    AF_ALLOC(pl->s_sweep, (size_t)g.ng * sizeof(float));
 #undef AF_ALLOC
     e = mlp_setup_attributes();
     if (e != cudaSuccess) return bail(cuda_fail(e, "MLP kernel attributes"));
@@ -538,6 +558,8 @@ af_status af_set_pixels(af_plan_t pl, const double *px, const double *pz)
     if (npix) {
         AF_CUDA(cudaMemcpy(pl->pix, pix.data(), npix * sizeof(float2), cudaMemcpyHostToDevice));
         AF_CUDA(cudaMemcpy(pl->pix_pol, pix_pol.data(), npix * sizeof(float2), cudaMemcpyHostToDevice));
+        memcpy(pl->host_px, px, sizeof(double) * npix);
+        memcpy(pl->host_pz, pz, sizeof(double) * npix);
     }
     pl->have_phi = false;        // exit angles of the old pixels are no warm start
     pl->have_fwd = false;

@@ -94,6 +94,7 @@ struct af_plan_s {
     AfGeom g;
     af_config cfg;       // scalar copy of the configuration (host pointers cleared)
     double *host_ex, *host_ez;   // element positions kept for re-validation
+    double *host_px, *host_pz;   // current pixel positions (re-validation, sweep)
     cudaStream_t stream;
     int device, sm_count;
     size_t smem_grid;    // bytes of the padded slowness grid in shared memory
@@ -104,6 +105,11 @@ struct af_plan_s {
     float2 *elem_pol;    // (polar angle about the arc centre, radius)
     float2 *pix;         // (x, z)
     float2 *pix_pol;     // (polar angle, radius)
+    // global-speed sweep (af_sweep): the plan's pixels while the sweep moves them,
+    // per-patch centre geometry of the dynamic grid, a uniform slowness map
+    float2 *pix_base, *pix_pol_base;
+    double *sweep_geo;   // [n_patch][5] {centre x, centre z, unit x, unit z, distance}
+    float *s_sweep;      // [ng]
     // workspaces
     float *phi;          // [ne][npix] exit angles
     float4 *D;           // [ne][npix] {sample index (int bits), fraction, Re P, Im P}
@@ -238,6 +244,10 @@ cudaError_t launch_ray_adjoint(af_plan_t pl, const float *s, float *grad);
 cudaError_t launch_adam(af_plan_t pl, const float *grad, float *s, float *m, float *v, int step);
 cudaError_t launch_export_delays(af_plan_t pl, double *T, uint8_t *apod);
 cudaError_t launch_images(af_plan_t pl, float *bmode, float *cimg);
+// host copies of the pixel positions; the centre geometry of the dynamic grid
+void sweep_patch_geometry(const af_config *c, const double *px, const double *pz, double *geo);
+void sweep_moved_pixels(const af_config *c, const double *px, const double *pz, const double *geo, double k,
+                        double *out_x, double *out_z);
 DelayShape delays_shape(size_t smem_scalar, int sm_count);
 cudaError_t mlp_setup_attributes();
 cudaError_t mlp_refresh_bf16(af_plan_t pl);

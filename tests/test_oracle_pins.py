@@ -685,3 +685,53 @@ def test_openmp_build_matches_single_thread():
     assert np.array_equal(T, T2) and np.array_equal(apod, apod2)
     assert np.array_equal(serial.das(psi, T, apod), par.das(psi, T, apod))
     assert oracle.omp_threads() >= 1
+
+
+# ---------------------------------------------------------------- dynamic sweep grid (Sec. III-A)
+def test_dynamic_grid_closed_form():
+    """At speed c0 a patch's depth below the lens and its pixel offsets are multiplied
+    by c0 / c_ref, its direction from the lens centre is kept; c0 = c_ref is the
+    identity."""
+    p = small(n_ang=3, n_rad=2, patch_w=3)
+    o = oracle.Oracle(p)
+    x1, z1 = o.dynamic_pixels(1540.0, 1540.0)
+    np.testing.assert_allclose(x1, p.pix_x, atol=1e-15)
+    np.testing.assert_allclose(z1, p.pix_z, atol=1e-15)
+    k = 1.1
+    x, z = o.dynamic_pixels(1.1 * 1540.0, 1540.0)
+    n = p.patch_npix
+    for P in range(p.n_patch):
+        sl = slice(P * n, (P + 1) * n)
+        c0 = np.array([p.pix_x[sl].mean(), p.pix_z[sl].mean()])
+        c1 = np.array([x[sl].mean(), z[sl].mean()])
+        v0, v1 = c0 - [p.arc_cx, p.arc_cz], c1 - [p.arc_cx, p.arc_cz]
+        assert np.linalg.norm(v1) - p.lens_radius == pytest.approx(k * (np.linalg.norm(v0) - p.lens_radius),
+                                                                   rel=1e-12)
+        assert v0[0] * v1[1] - v0[1] * v1[0] == pytest.approx(0.0, abs=1e-15)     # same direction
+        np.testing.assert_allclose(x[sl] - c1[0], k * (p.pix_x[sl] - c0[0]), atol=1e-15)
+        np.testing.assert_allclose(z[sl] - c1[1], k * (p.pix_z[sl] - c0[1]), atol=1e-15)
+
+
+def test_dynamic_grid_keeps_a_point_scatterer_on_its_patch_centre():
+    """What the dynamic grid is for: beamformed at a wrong uniform speed c0, a point
+    scatterer sitting on a patch's centre pixel (at the reference speed) still peaks on
+    that patch's centre pixel when the patch moves with the dynamic grid, because its
+    echo's apparent depth below the lens scales with c0; on the static grid it peaks
+    elsewhere in the patch."""
+    p = synth.config_tiny(n_ang=1, n_rad=1, patch_w=9, depth_min=20e-3)
+    c_true = 1500.0
+    p.medium = synth.Medium(speeds=[c_true])
+    centre = p.patch_npix // 2
+    T1 = synth.oneway_times(p, np.array([p.pix_x[centre]]), np.array([p.pix_z[centre]]))
+    psi = synth.echoes(p, T1, np.array([1.0]))
+    o = oracle.Oracle(p)
+    for c0 in (0.95 * c_true, 1.05 * c_true):
+        s = np.full((p.nz, p.nx), 1.0 / c0)
+        peaks = {}
+        for name, (x, z) in (("dynamic", o.dynamic_pixels(c0, c_true)), ("static", (p.pix_x, p.pix_z))):
+            q = dataclasses.replace(p, pix_x=np.asarray(x), pix_z=np.asarray(z))
+            oq = oracle.Oracle(q)
+            T, apod, _ = oq.delays(s)
+            peaks[name] = int(np.argmax(np.abs(oq.das(psi, T, apod).sum(0))))
+        assert peaks["dynamic"] == centre, (c0, peaks)
+        assert peaks["static"] != centre, (c0, peaks)
