@@ -187,11 +187,12 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------- roofline
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
-# capture of the full workload (second iteration), per kernel; None once the kernel
-# changed after the capture (see profiles/).  The adjoint stages' traffic follows
+# capture of the full workload at 10 scatterers per resolution cell (second launch of
+# each kernel, one kernel per capture), per kernel; None once the kernel changed after
+# the capture (see profiles/).  The adjoint stages' traffic follows
 # the CMPE mask of the captured iteration.
-NCU_TRAFFIC = {"das_forward": 617.4e6 + 85.0e6, "das_adjoint": 286.8e6 + 17.0e6,
-               "ray_adjoint": 26.2e6 + 1.9e6, "delays": 15.9e6 + 23.7e6}
+NCU_TRAFFIC = {"das_forward": 618.1e6 + 85.5e6, "das_adjoint": 337.7e6 + 20.1e6,
+               "ray_adjoint": 28.3e6 + 2.1e6, "delays": 15.9e6 + 23.5e6}
 
 # algorithmic FP32 lane-operations per unit, from the arithmetic of the method.
 # Ray point: position (2) + cell and fraction (4) + two Keys weight sets (2 x 10) + 16
