@@ -725,6 +725,7 @@ def main():
         b.build()
         oracle.build()
         synth.build()
+        synth.build_gpu()
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

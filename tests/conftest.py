@@ -28,3 +28,4 @@ def _built():
     b.build()
     oracle.build()
     synth.build()
+    synth.build_gpu()
