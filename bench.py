@@ -210,13 +210,19 @@ KERNELS_PER_STAGE = {"grid_stats": 2, "delays": 1, "das_forward": 1, "cmpe_forwa
 OPS_PER_GATHER = {"das_forward": 13, "das_adjoint": 23}
 
 
-def lane_peak(sm_count: int, clk, pk):
-    """FP32 lane-operation rate: SMs (queried from the device) x 128 FP32 lanes x the SM
-    clock (median sampled under load during the timed region, else the maximum)."""
+def lane_peak(sm_count: int, clk, pk, measured=None):
+    """FP32 lane-operation rate (one FMA on one lane = one lane-operation).  measured:
+    the library's FMA-loop rate on this device (af_fp32_lane_rate), used when given;
+    else derived as SMs (queried from the device) x 128 FP32 lanes x the SM clock
+    (median sampled under load during the timed region, else the maximum)."""
     mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2032.0)
     src = "median sampled during the timed region" if (clk or {}).get("sm_mhz") else "maximum SM clock"
-    return sm_count * 128 * mhz * 1e6, (f"derived: {sm_count} SMs (queried) x 128 FP32 lanes x {mhz:.0f} MHz "
-                                        f"({src}); not a measured FMA peak")
+    derived = sm_count * 128 * mhz * 1e6
+    if measured:
+        return measured, (f"measured: af_fp32_lane_rate, a dependency-free FMA loop on this GPU "
+                          f"({measured / derived:.3f} of {sm_count} SMs x 128 lanes x {mhz:.0f} MHz)")
+    return derived, (f"derived: {sm_count} SMs (queried) x 128 FP32 lanes x {mhz:.0f} MHz "
+                     f"({src}); not a measured FMA peak")
 
 
 def stage_roofline(stage, ms, launches, p, iq_bytes, pk, units, peak):
@@ -662,7 +668,9 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return
     pk = peaks()
-    peak = lane_peak(torch.cuda.get_device_properties(dev).multi_processor_count, clk, pk)
+    with torch.cuda.stream(stream):
+        measured_rate = af.fp32_lane_rate(stream)
+    peak = lane_peak(torch.cuda.get_device_properties(dev).multi_processor_count, clk, pk, measured_rate)
     ranked = sorted(((v_[0], k) for k, v_ in stages.items() if v_[1] > 0), reverse=True)
     dom = ranked[0][1]
     roof = stage_roofline(dom, stages[dom][0], stages[dom][1], p, iq_bytes, pk, units.get(dom, 0), peak)

@@ -411,6 +411,15 @@ af_status af_gemm_bf16(const void *d_A, const void *d_B, float *d_D, int M, int 
  * counterpart in the paper. */
 af_status af_set_wait_limit(int tries);
 
+/* Measured FP32 lane rate of the current device: lane-operations (one fused
+ * multiply-add on one lane) per second of a plain, dependency-free FMA loop over
+ * 8 CTAs per SM, timed with CUDA events on `stream`.  It is the denominator of
+ * the rooflines of this library's kernels, which are bound by FP32 issue.
+ * d_sink: one device float the kernel may write (it keeps the loop from being
+ * removed).  *h_rate (host) receives the rate; synchronises the stream.  No
+ * counterpart in the paper. */
+af_status af_fp32_lane_rate(float *d_sink, void *stream, double *h_rate);
+
 /* Message of the last failing call on this host thread ("" if none). */
 const char *af_last_error(void);
 

@@ -120,6 +120,7 @@ _SIGNATURES = {
     "af_gemm_bf16": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, _VP, _VP]),
     "af_set_wait_limit": (ctypes.c_int, [ctypes.c_int]),
+    "af_fp32_lane_rate": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_double)]),
     "af_set_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "af_get_stage_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]),
     "af_last_error": (ctypes.c_char_p, []),
@@ -256,6 +257,16 @@ def af_cmpe_loss_noalloc(B, nsub: int, n_patch: int, patch_npix: int, rho_thresh
                                        float(rho_thresh), _ptr(loss), _ptr(n_active), h),
            "af_cmpe_loss_noalloc")
     return loss
+
+
+def fp32_lane_rate(stream=None) -> float:
+    """Measured FP32 lane-operations per second of the current device (af_fp32_lane_rate)."""
+    import torch
+    sink = torch.zeros(1, device=torch.device("cuda", torch.cuda.current_device()))
+    h = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+    rate = ctypes.c_double()
+    _check(load().af_fp32_lane_rate(_ptr(sink), h, ctypes.byref(rate)), "af_fp32_lane_rate")
+    return rate.value
 
 
 def af_gemm_bf16(A, B, D, a_mn_major=False, b_mn_major=False, err=None, stream=None):

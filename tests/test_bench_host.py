@@ -54,3 +54,9 @@ def test_gather_stage_counts_live_gathers_and_hbm_bytes():
     assert r["hbm"]["frac"] == pytest.approx(r["hbm"]["achieved"] / 6489.0)
     adj = bench.stage_roofline("das_adjoint", 6.0, 10, p, 402_718_720, PEAKS, gathers, PEAK)
     assert adj["hbm"]["algorithmic_bytes"] == bytes_ + p.ne * p.npix * 4
+
+
+def test_lane_peak_prefers_the_measured_rate():
+    rate, src = bench.lane_peak(148, {"sm_mhz": 2032.0}, PEAKS, measured=36.0e12)
+    assert rate == 36.0e12
+    assert src.startswith("measured") and "0.935" in src
