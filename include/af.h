@@ -322,7 +322,7 @@ af_status af_get_counters(af_plan_t plan, long long *h_counters);
  * (h_count) since recording started.  Stages (AF_NSTAGES = 8):
  *  0 grid statistics (c_med, Eq. 10-11)   1 delays (Eq. 1-4, 8)
  *  2 DAS forward (Eq. 5)                   3 CMPE forward + loss
- *  4 CMPE adjoint                          5 DAS adjoint
+ *  4 (none: dL/dB is formed in stage 5)   5 DAS adjoint with dL/dB
  *  6 ray adjoint + gradient reduction      7 Adam update (Eq. 9)
  *  8 lens-surrogate inference (when enabled) */
 #define AF_NSTAGES 9

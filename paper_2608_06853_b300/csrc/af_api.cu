@@ -510,7 +510,6 @@ af_status af_adjoint(af_plan_t pl, float *grad)
     if (!pl) return fail(AF_ERR_ARG, "plan is NULL");
     if (!grad) return fail(AF_ERR_ARG, "d_grad is NULL");
     if (!pl->have_fwd) return fail(AF_ERR_STATE, "af_adjoint called before af_forward");
-    AF_CUDA(staged(pl, 4, [&] { return launch_cmpe_backward(pl); }));
     AF_CUDA(staged(pl, 5, [&] { return launch_das_adjoint(pl); }));
     AF_CUDA(staged(pl, 6, [&] { return launch_ray_adjoint(pl, pl->slowness, grad); }));
     pl->have_adj = true;
@@ -646,6 +645,8 @@ af_status af_get_image_grad(af_plan_t pl, float *G)
     const size_t n = (size_t)pl->g.nb * pl->g.npix;
     if (n == 0) return AF_OK;
     if (!G) return fail(AF_ERR_ARG, "d_G is NULL");
+    // the adjoint forms dL/dB inside the DAS adjoint without storing it: form it here
+    AF_CUDA(launch_cmpe_backward(pl));
     AF_CUDA(cudaMemcpyAsync(G, pl->G, n * sizeof(float2), cudaMemcpyDeviceToDevice, pl->stream));
     return AF_OK;
 }

@@ -17,26 +17,23 @@ namespace {
 using cmpe::pair_ij;
 using cmpe::warp_sum;
 // index of the pair whose first image is (i, j), or -1
-__device__ __forceinline__ int pair_index(int i, int j, int n)
-{
-    if (i < 0 || i > n - 2 || j < 1 || j > n - 1 || j == i + 1) return -1;
-    return i * (n - 2) + (j - 1) - (j > i + 1 ? 1 : 0);
-}
+using cmpe::pair_index;
 
-// one CTA per patch; warp w takes pairs w, w + 8, ...
-__global__ void __launch_bounds__(256) cmpe_forward_kernel(AfGeom g, const float2 *__restrict__ B,
+// one CTA of 32 warps per patch; warp w takes pairs w, w + 32, ... (the pairs are
+// latency-bound on their loads, so many warps keep more of them in flight)
+__global__ void __launch_bounds__(1024) cmpe_forward_kernel(AfGeom g, const float2 *__restrict__ B,
                                                            float2 *__restrict__ z,
                                                            uint8_t *__restrict__ mask,
                                                            double *__restrict__ patch_sum,
                                                            int *__restrict__ patch_cnt)
 {
-    __shared__ double s_sum[8];
-    __shared__ int s_cnt[8];
+    __shared__ double s_sum[32];
+    __shared__ int s_cnt[32];
     const int P = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int base = P * g.patch_npix;
     double lsum = 0.0;
     int cnt = 0;
-    for (int k = w; k < g.npair; k += 8) {
+    for (int k = w; k < g.npair; k += 32) {
         const cmpe::PairTerms t = cmpe::pair_terms(B, g.nsub, g.npix, base, g.patch_npix, k, lane);
         if (lane == 0) {
             const int m = t.rho >= g.rho_thresh;
@@ -54,7 +51,7 @@ __global__ void __launch_bounds__(256) cmpe_forward_kernel(AfGeom g, const float
     if (threadIdx.x == 0) {
         double a = 0.0;
         int c = 0;
-        for (int k = 0; k < 8; ++k) { a += s_sum[k]; c += s_cnt[k]; }
+        for (int k = 0; k < 32; ++k) { a += s_sum[k]; c += s_cnt[k]; }
         patch_sum[P] = a;
         patch_cnt[P] = c;
     }
@@ -122,16 +119,6 @@ __global__ void cmpe_set_totals_kernel(AfGeom g, const double *__restrict__ in, 
     }
 }
 
-// sign of arg z as atan2 defines it: the sign of Im z, and on the real axis
-// +pi (or -pi for Im z = -0) left of the origin, 0 right of it
-__device__ __forceinline__ float arg_sign(float2 z)
-{
-    if (z.y > 0.0f) return 1.0f;
-    if (z.y < 0.0f) return -1.0f;
-    if (z.x < 0.0f) return signbit(z.y) ? -1.0f : 1.0f;
-    return 0.0f;
-}
-
 // G[b][p] = dL_CMPE/dB_b(p): an image is the first member of at most one pair
 // ((i,j) ~ (i+1,j-1)) and the second member of at most one ((i-1,j+1) ~ (i,j)).
 //   first:  w j z B2 / |z|^2     second: -w j conj(z) B1 / |z|^2,  w = sgn(arg z) / max(1, M)
@@ -139,48 +126,13 @@ __device__ __forceinline__ float arg_sign(float2 z)
 __global__ void __launch_bounds__(256) cmpe_backward_kernel(AfGeom g, const float2 *__restrict__ B,
                                                             const float2 *__restrict__ z,
                                                             const uint8_t *__restrict__ mask,
-                                                            AfScal *scal,
+                                                            const AfScal *__restrict__ scal,
                                                             float2 *__restrict__ G)
 {
     const int n = g.nsub, b = blockIdx.y, i = b / n, j = b - i * n;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (blockIdx.x == 0 && b == 0 && threadIdx.x == 0) scal->gmax_bits = 0;   // read by the ray adjoint
     if (p >= g.npix) return;
-    const float inv_m = scal->inv_m;
-    const int P = p / g.patch_npix;
-    const int k1 = pair_index(i, j, n), k2 = pair_index(i - 1, j + 1, n);
-    float gr = 0.0f, gi = 0.0f;
-    if (k1 >= 0) {
-        const long o = (long)P * g.npair + k1;
-        if (mask[o]) {
-            const float2 zz = z[o];
-            const float mag2 = zz.x * zz.x + zz.y * zz.y;
-            const float sg = arg_sign(zz);
-            if (sg != 0.0f && mag2 > 0.0f) {
-                const float w = sg * inv_m / mag2;
-                const float2 c = B[(long)((i + 1) * n + (j - 1)) * g.npix + p];
-                const float tr = zz.x * c.x - zz.y * c.y, ti = zz.x * c.y + zz.y * c.x;
-                gr += -w * ti;
-                gi += w * tr;
-            }
-        }
-    }
-    if (k2 >= 0) {
-        const long o = (long)P * g.npair + k2;
-        if (mask[o]) {
-            const float2 zz = z[o];
-            const float mag2 = zz.x * zz.x + zz.y * zz.y;
-            const float sg = arg_sign(zz);
-            if (sg != 0.0f && mag2 > 0.0f) {
-                const float w = sg * inv_m / mag2;
-                const float2 a = B[(long)((i - 1) * n + (j + 1)) * g.npix + p];
-                const float ur = zz.x * a.x + zz.y * a.y, ui = zz.x * a.y - zz.y * a.x;
-                gr += w * ui;
-                gi += -w * ur;
-            }
-        }
-    }
-    G[(long)b * g.npix + p] = make_float2(gr, gi);
+    G[(long)b * g.npix + p] = cmpe::image_grad(B, z, mask, scal->inv_m, n, g.npix, g.npair, p / g.patch_npix, i, j, p);
 }
 
 // Full-aperture image |sum_ij B_ij(p)| (Figs. 2, 4) and the integrated CMPE
@@ -225,7 +177,7 @@ cudaError_t launch_images(af_plan_t pl, float *bmode, float *cimg)
 cudaError_t launch_cmpe_forward(af_plan_t pl, float *loss)
 {
     if (pl->g.n_patch > 0 && pl->g.npair > 0) {
-        cmpe_forward_kernel<<<pl->g.n_patch, 256, 0, pl->stream>>>(pl->g, pl->B, pl->z, pl->mask,
+        cmpe_forward_kernel<<<pl->g.n_patch, 1024, 0, pl->stream>>>(pl->g, pl->B, pl->z, pl->mask,
                                                                   pl->patch_sum, pl->patch_cnt);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -253,9 +205,7 @@ cudaError_t launch_cmpe_backward(af_plan_t pl)
     const long total = (long)pl->g.nb * pl->g.npix;
     if (total == 0) return cudaSuccess;
     if (pl->g.npair == 0) {
-        cudaError_t e = cudaMemsetAsync(pl->G, 0, total * sizeof(float2), pl->stream);
-        if (e != cudaSuccess) return e;
-        return cudaMemsetAsync(&pl->scal->gmax_bits, 0, sizeof(int), pl->stream);
+        return cudaMemsetAsync(pl->G, 0, total * sizeof(float2), pl->stream);
     }
     const dim3 blocks((pl->g.npix + 255) / 256, pl->g.nb);
     cmpe_backward_kernel<<<blocks, 256, 0, pl->stream>>>(pl->g, pl->B, pl->z, pl->mask, pl->scal, pl->G);

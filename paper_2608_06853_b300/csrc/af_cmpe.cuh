@@ -8,6 +8,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 namespace cmpe {
 
@@ -54,6 +55,67 @@ __device__ __forceinline__ PairTerms pair_terms(const float2 *__restrict__ B, in
     // float epilogue (the sums are float); sqrt of each energy avoids overflow
     const float den = sqrtf(e1) * sqrtf(e2);
     return PairTerms{zr, zi, den > 0.0f ? hypotf(zr, zi) / den : 0.0f};
+}
+
+// index of the pair whose first image is (i, j), or -1
+__device__ __forceinline__ int pair_index(int i, int j, int n)
+{
+    if (i < 0 || i > n - 2 || j < 1 || j > n - 1 || j == i + 1) return -1;
+    return i * (n - 2) + (j - 1) - (j > i + 1 ? 1 : 0);
+}
+
+// sign of arg z as atan2 defines it: the sign of Im z, and on the real axis
+// +pi (or -pi for Im z = -0) left of the origin, 0 right of it
+__device__ __forceinline__ float arg_sign(float2 z)
+{
+    if (z.y > 0.0f) return 1.0f;
+    if (z.y < 0.0f) return -1.0f;
+    if (z.x < 0.0f) return signbit(z.y) ? -1.0f : 1.0f;
+    return 0.0f;
+}
+
+// dL_CMPE/dB_ij(p) (= dL/dRe B + j dL/dIm B) with the mask held constant: image
+// (i, j) is the first member of at most one pair ((i,j) ~ (i+1,j-1)) and the second
+// member of at most one ((i-1,j+1) ~ (i,j)) of its patch P:
+//   first:  w j z B2 / |z|^2     second: -w j conj(z) B1 / |z|^2,  w = sgn(arg z) / max(1, M)
+// B is [nsub * nsub][npix]; z, mask are [n_patch][npair].
+__device__ __forceinline__ float2 image_grad(const float2 *__restrict__ B, const float2 *__restrict__ z,
+                                             const uint8_t *__restrict__ mask, float inv_m, int n, int npix,
+                                             int npair, int P, int i, int j, int p)
+{
+    const int k1 = pair_index(i, j, n), k2 = pair_index(i - 1, j + 1, n);
+    float gr = 0.0f, gi = 0.0f;
+    if (k1 >= 0) {
+        const long o = (long)P * npair + k1;
+        if (mask[o]) {
+            const float2 zz = z[o];
+            const float mag2 = zz.x * zz.x + zz.y * zz.y;
+            const float sg = arg_sign(zz);
+            if (sg != 0.0f && mag2 > 0.0f) {
+                const float w = sg * inv_m / mag2;
+                const float2 c = B[(long)((i + 1) * n + (j - 1)) * npix + p];
+                const float tr = zz.x * c.x - zz.y * c.y, ti = zz.x * c.y + zz.y * c.x;
+                gr += -w * ti;
+                gi += w * tr;
+            }
+        }
+    }
+    if (k2 >= 0) {
+        const long o = (long)P * npair + k2;
+        if (mask[o]) {
+            const float2 zz = z[o];
+            const float mag2 = zz.x * zz.x + zz.y * zz.y;
+            const float sg = arg_sign(zz);
+            if (sg != 0.0f && mag2 > 0.0f) {
+                const float w = sg * inv_m / mag2;
+                const float2 a = B[(long)((i - 1) * n + (j + 1)) * npix + p];
+                const float ur = zz.x * a.x + zz.y * a.y, ui = zz.x * a.y - zz.y * a.x;
+                gr += w * ui;
+                gi += -w * ur;
+            }
+        }
+    }
+    return make_float2(gr, gi);
 }
 
 }  // namespace cmpe

@@ -9,6 +9,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "af_cmpe.cuh"
 #include "af_internal.cuh"
 
 namespace {
@@ -238,14 +239,17 @@ __device__ __forceinline__ float adj_transmit(const AfGeom &g, const typename S:
 template <int W, int DT, bool CHECK>
 __device__ __forceinline__ void das_adjoint_blocks(const AfGeom &g, const typename Sample<DT>::T *__restrict__ psi,
                                                    const float *__restrict__ scale, const float4 *__restrict__ D,
-                                                   const float2 *__restrict__ G, float *__restrict__ gdel, int j,
+                                                   const float2 *__restrict__ B, const float2 *__restrict__ z,
+                                                   const uint8_t *__restrict__ mask, float inv_m,
+                                                   float *__restrict__ gdel, int j,
                                                    int p, bool live, const int (&nr)[W], const float (&fr)[W],
                                                    const float2 (&pr)[W], float (&gr)[W])
 {
     using S = Sample<DT>;
     float4 dnext = D[p];
     for (int i = 0; i < g.nsub; ++i) {
-        const float2 Gv = G[(long)(i * g.nsub + j) * g.npix + p];
+        // dL/dB_ij(p), formed here from the images and the CMPE terms (never stored)
+        const float2 Gv = cmpe::image_grad(B, z, mask, inv_m, g.nsub, g.npix, g.npair, p / g.patch_npix, i, j, p);
         // every term of transmit block i is weighted by conj(G_ij(p)): where the CMPE
         // mask leaves G_ij(p) = 0 the block adds exactly nothing, so it is skipped
         // (by the whole warp when no lane has a gradient, else lane by lane)
@@ -278,7 +282,10 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 4) das_adjoint_kernel(AfGeom g
                                                              const float *__restrict__ scale,
                                                              const float4 *__restrict__ D,
                                                              const int2 *__restrict__ nrange,
-                                                             const float2 *__restrict__ G,
+                                                             const float2 *__restrict__ B,
+                                                             const float2 *__restrict__ z,
+                                                             const uint8_t *__restrict__ mask,
+                                                             const AfScal *__restrict__ scal,
                                                              float *__restrict__ gdel)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -294,12 +301,13 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 4) das_adjoint_kernel(AfGeom g
     const bool live = rmask != 0u;
     const unsigned act = __activemask();
     if (!__any_sync(act, live)) return;        // adds nothing
+    const float inv_m = scal->inv_m;
 #pragma unroll
     for (int k = 0; k < W; ++k) gr[k] = 0.0f;
     if (__all_sync(act, pixel_in_trace(nrange[p], g.ns)))
-        das_adjoint_blocks<W, DT, false>(g, psi, scale, D, G, gdel, j, p, live, nr, fr, pr, gr);
+        das_adjoint_blocks<W, DT, false>(g, psi, scale, D, B, z, mask, inv_m, gdel, j, p, live, nr, fr, pr, gr);
     else
-        das_adjoint_blocks<W, DT, true>(g, psi, scale, D, G, gdel, j, p, live, nr, fr, pr, gr);
+        das_adjoint_blocks<W, DT, true>(g, psi, scale, D, B, z, mask, inv_m, gdel, j, p, live, nr, fr, pr, gr);
 #pragma unroll
     for (int k = 0; k < W; ++k)
         if (rmask >> k & 1u) atomicAdd(&gdel[(long)(j * W + k) * g.npix + p], gr[k]);
@@ -332,10 +340,12 @@ cudaError_t launch_adj_t(af_plan_t pl)
 {
     const long n = (long)pl->g.ne * pl->g.npix;
     cudaError_t e = cudaMemsetAsync(pl->gdel, 0, n * sizeof(float), pl->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&pl->scal->gmax_bits, 0, sizeof(int), pl->stream);   // read by the ray adjoint
     if (e != cudaSuccess) return e;
     const dim3 blocks((pl->g.npix + 32 * kAdjWarps - 1) / (32 * kAdjWarps), pl->g.nsub);
     das_adjoint_kernel<W, DT><<<blocks, 32 * kAdjWarps, 0, pl->stream>>>(pl->g, pl->iq, pl->iq_scale, pl->D,
-                                                                       pl->nrange, pl->G, pl->gdel);
+                                                                       pl->nrange, pl->B, pl->z, pl->mask,
+                                                                       pl->scal, pl->gdel);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     gdel_max_kernel<<<pl->sm_count * 4, 256, 0, pl->stream>>>(pl->gdel, n, &pl->scal->gmax_bits);

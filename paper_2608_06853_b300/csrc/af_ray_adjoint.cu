@@ -333,12 +333,19 @@ __global__ void __launch_bounds__(256) reduce_grad_kernel(AfGeom g, const float 
                                                           const long long *__restrict__ gpart, int nparts,
                                                           AfScal *scal, float *__restrict__ grad)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k == 0) scal->ray_next = 0;
-    if (k >= g.ng) return;
-    long long tot = 0;
+    // 64 nodes x 4 slices of the partials per CTA; the slices are added in a fixed order
+    __shared__ long long s_part[4][64];
+    const int k = blockIdx.x * 64 + (threadIdx.x & 63), slice = threadIdx.x >> 6;
+    if (k == 0 && slice == 0) scal->ray_next = 0;
+    long long part = 0;
+    if (k < g.ng) {
 #pragma unroll 8
-    for (int c = 0; c < nparts; ++c) tot += gpart[(long)c * g.ng + k];
+        for (int c = slice; c < nparts; c += 4) part += gpart[(long)c * g.ng + k];
+    }
+    s_part[slice][threadIdx.x & 63] = part;
+    __syncthreads();
+    if (slice != 0 || k >= g.ng) return;
+    const long long tot = s_part[0][threadIdx.x] + s_part[1][threadIdx.x] + s_part[2][threadIdx.x] + s_part[3][threadIdx.x];
     const float gmax = __int_as_float(scal->gmax_bits);
     const float acc = gmax > 0.0f ? (float)((double)tot * ((double)gmax / (double)g.fix_scale)) : 0.0f;
     const int j = k / g.nx, i = k - j * g.nx, nx = g.nx, nz = g.nz;
@@ -478,7 +485,7 @@ cudaError_t launch_ray_adjoint(af_plan_t pl, const float *s, float *grad)
         if (e != cudaSuccess) return e;
         nparts = sh.blocks;
     }
-    reduce_grad_kernel<<<(pl->g.ng + 255) / 256, 256, 0, pl->stream>>>(pl->g, s, pl->gpart, nparts, pl->scal,
+    reduce_grad_kernel<<<(pl->g.ng + 63) / 64, 256, 0, pl->stream>>>(pl->g, s, pl->gpart, nparts, pl->scal,
                                                                       grad);
     return cudaGetLastError();
 }

@@ -440,15 +440,15 @@ def full_case():
     return p, psi
 
 
-@pytest.mark.parametrize("dtype", [af.AF_IQ_C64, af.AF_IQ_BF16])
+@pytest.mark.parametrize("dtype", [af.AF_IQ_C64, af.AF_IQ_BF16, af.AF_IQ_F16])
 def test_full_size_end_to_end_parity(full_case, dtype):
     """The whole forward and adjoint at full size (128 x 128 x 3072 channel data, 400
     patches of 9 x 9, 128^2 grid, a layered map) against the oracle run end to end on the
     same inputs (OpenMP build of the oracle source), with the GPU's apodization bits and
     CMPE mask injected.  Float32 channel data: loss of Eq. 12 within 1e-4, dL/ds within
-    1e-3 (relative L2).  Bf16 storage with a per-transmit scale: the errors of images,
-    loss and gradient against the same float64 reference are printed and bounded by the
-    storage rounding."""
+    1e-3 (relative L2).  Bf16 and f16 storage with a per-transmit scale: the errors of
+    images, loss and gradient against the same float64 reference are printed and bounded
+    by the storage rounding (2^-8, 2^-11)."""
     p, psi = full_case
     s = layered_speed(p)
     run = Run(p, psi, s, iq_dtype=dtype)
@@ -460,7 +460,7 @@ def test_full_size_end_to_end_parity(full_case, dtype):
     e_img = rel_l2(run.B, o.das(psi, T, run.apod))
     e_loss = abs(run.L[0] - parts[0]) / abs(parts[0])
     e_grad = rel_l2(run.dLds, g)
-    name = {af.AF_IQ_C64: "float32", af.AF_IQ_BF16: "bf16"}[dtype]
+    name = {af.AF_IQ_C64: "float32", af.AF_IQ_BF16: "bf16", af.AF_IQ_F16: "f16"}[dtype]
     print(f"full size, {name} channel data vs float64 oracle: images {e_img:.2e}, loss {e_loss:.2e}, "
           f"dL/ds {e_grad:.2e} (rel L2); active CMPE terms {M}")
     if dtype == af.AF_IQ_C64:
@@ -468,8 +468,9 @@ def test_full_size_end_to_end_parity(full_case, dtype):
         assert e_loss <= LOSS_TOL
         assert e_grad <= GRAD_TOL
     else:
-        assert e_img < 2 ** -8
-        assert e_loss < 20 * 2 ** -8
+        unit = 2 ** -8 if dtype == af.AF_IQ_BF16 else 2 ** -11
+        assert e_img < unit
+        assert e_loss < 20 * unit
         assert e_grad < 0.1
 
 
