@@ -214,7 +214,10 @@ af_status af_set_pixels(af_plan_t plan, const double *pix_x, const double *pix_z
  *    (device, may be NULL): active CMPE terms per speed.
  * Afterwards the plan's pixels are restored and the next af_forward starts
  * without an exit-angle warm start.  Needs a curved or flat lens surface for
- * dynamic = 1 (AF_ERR_ARG otherwise). */
+ * dynamic = 1 (AF_ERR_ARG otherwise).  The two extreme speeds are validated
+ * before any work is queued; a speed in between that fails stops the sweep
+ * with the error, with the plan's pixels restored and earlier speeds' results
+ * written.  Each speed's exit solve starts from the previous speed's exit angles. */
 af_status af_sweep(af_plan_t plan, const void *d_iq, const float *d_iq_scale, const double *h_speeds,
                    int n_speeds, double c_ref, int dynamic, float *d_cmpe, int *d_active);
 

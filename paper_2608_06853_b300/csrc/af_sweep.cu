@@ -124,17 +124,20 @@ extern "C" af_status af_sweep(af_plan_t pl, const void *d_iq, const float *d_iq_
     if (dyn && c.lens_mode != AF_LENS_PLANAR && !(c.lens_radius > 0))
         return af_set_error(AF_ERR_ARG, "af_sweep: the dynamic grid needs a lens surface (lens_radius > 0)");
     std::vector<double> geo(dyn ? (size_t)c.n_patch * 5 : 1), mx(dyn ? npix : 1), mz(dyn ? npix : 1);
+    // every moved pixel set must pass the plan's validation (grid box, lens)
+    auto validate = [&](int k) -> af_status {
+        sweep_moved_pixels(&c, pl->host_px, pl->host_pz, geo.data(), h_speeds[k] / c_ref, mx.data(), mz.data());
+        af_config m = c;
+        m.pix_x = mx.data();
+        m.pix_z = mz.data();
+        return af_check_config(&m);
+    };
     if (dyn) {
-        // every moved pixel set must pass the plan's validation (grid box, lens)
         sweep_patch_geometry(&c, pl->host_px, pl->host_pz, geo.data());
-        for (int k = 0; k < n_speeds; ++k) {
-            sweep_moved_pixels(&c, pl->host_px, pl->host_pz, geo.data(), h_speeds[k] / c_ref, mx.data(), mz.data());
-            af_config m = c;
-            m.pix_x = mx.data();
-            m.pix_z = mz.data();
-            const af_status st = af_check_config(&m);
-            if (st != AF_OK) return st;
-        }
+        // the extreme speeds first, so that a sweep leaving the grid box fails before any work
+        af_status v = validate(0);
+        if (v == AF_OK && n_speeds > 1) v = validate(n_speeds - 1);
+        if (v != AF_OK) return v;
     }
     cudaStream_t st = pl->stream;
 #define SW_CUDA(call)                                                                                    \
@@ -154,12 +157,26 @@ extern "C" af_status af_sweep(af_plan_t pl, const void *d_iq, const float *d_iq_
     pl->slowness = pl->s_sweep;
     const int ng = pl->g.ng;
     for (int k = 0; k < n_speeds; ++k) {
+        // the speeds in between are validated while the device runs the earlier ones
+        if (dyn && k > 0 && k < n_speeds - 1) {
+            const af_status v = validate(k);
+            if (v != AF_OK) {
+                // put the plan's pixels back before reporting
+                cudaMemcpyAsync(pl->pix, pl->pix_base, npix * sizeof(float2), cudaMemcpyDeviceToDevice, st);
+                cudaMemcpyAsync(pl->pix_pol, pl->pix_pol_base, npix * sizeof(float2), cudaMemcpyDeviceToDevice, st);
+                pl->have_phi = false;
+                pl->have_fwd = pl->have_adj = false;
+                return v;
+            }
+        }
         if (dyn) {
             sweep_pixels_kernel<<<(npix + 255) / 256, 256, 0, st>>>(npix, c.patch_npix, c.arc_cx, c.arc_cz,
                                                                     h_speeds[k] / c_ref, pl->pix_base,
                                                                     pl->sweep_geo, pl->pix, pl->pix_pol);
             SW_CUDA(cudaGetLastError());
-            pl->have_phi = false;                // moved pixels: no exit-angle warm start
+            // the previous speed's exit angles start the (bracketed) exit solve: the
+            // pixels moved little, and any start inside the bracket converges
+            pl->have_phi = pl->have_phi && k > 0;
         }
         fill_kernel<<<(ng + 255) / 256, 256, 0, st>>>(pl->s_sweep, ng, (float)(1.0 / h_speeds[k]));
         SW_CUDA(cudaGetLastError());
