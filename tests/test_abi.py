@@ -168,3 +168,16 @@ def test_noalloc_wrapper_checks_arguments_before_any_call():
         af.af_cmpe_loss_noalloc(good, nsub, n_patch, npix, 0.9, loss, torch.zeros(1, dtype=torch.int64))
     with pytest.raises(ValueError, match="CUDA"):
         af.af_cmpe_loss_noalloc(good, nsub, n_patch, npix, 0.9, loss)
+
+
+def test_new_entry_points_refuse_null_arguments_without_a_gpu():
+    """af_sweep, af_cmpe_totals, af_set_cmpe_totals and af_fp32_lane_rate check their
+    arguments on the host before any CUDA call."""
+    lib = af.load()
+    sp = (ctypes.c_double * 2)(1500.0, 1540.0)
+    assert lib.af_sweep(None, None, None, sp, 2, 1540.0, 1, None, None) == af.AF_ERR_ARG
+    assert lib.af_cmpe_totals(None, None) == af.AF_ERR_ARG
+    assert lib.af_set_cmpe_totals(None, None, None) == af.AF_ERR_ARG
+    rate = ctypes.c_double()
+    assert lib.af_fp32_lane_rate(None, None, ctypes.byref(rate)) == af.AF_ERR_ARG
+    assert lib.af_set_wait_limit(-1) == af.AF_OK
