@@ -329,17 +329,25 @@ def _time_iterations(plan, iq, scale, p, stream, dev, steps, warmup):
     loss = torch.zeros(4, device=dev)
     for it in range(1, warmup + 1):
         plan.af_iterate(iq, s, g, m, v, it, loss, scale)
+    state0 = [x.clone() for x in (s, m, v)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    plan.set_timing(True)
     torch.cuda.synchronize()
     e0.record(stream)
     for it in range(warmup + 1, warmup + steps + 1):
         plan.af_iterate(iq, s, g, m, v, it, loss, scale)
     e1.record(stream)
     torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    # stage times from a replay of the same iterations with the per-stage events on
+    with torch.cuda.stream(stream):
+        for x, x0 in zip((s, m, v), state0):
+            x.copy_(x0)
+    plan.set_timing(True)
+    for it in range(warmup + 1, warmup + steps + 1):
+        plan.af_iterate(iq, s, g, m, v, it, loss, scale)
+    torch.cuda.synchronize()
     stages = plan.stage_times()
     plan.set_timing(False)
-    ms = e0.elapsed_time(e1) / steps
     return ms, {k: v_[0] / max(v_[1], 1) for k, v_ in stages.items()}, loss.cpu().numpy().tolist()
 
 
@@ -571,8 +579,14 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
 
     clocks = ClockSampler(local_rank) if rank == 0 else None
-    state0 = [x.clone() for x in (s, m, v)]        # for the untimed recount of live units
-    plan.set_timing(True)
+    state0 = [x.clone() for x in (s, m, v)]        # the timed iterations are replayed from here
+
+    def restore():
+        with torch.cuda.stream(stream):
+            for x, x0 in zip((s, m, v), state0):
+                x.copy_(x0)
+        stream.synchronize()
+
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
@@ -583,21 +597,26 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1)
-    stages = plan.stage_times()
-    plan.set_timing(False)
     clk = clocks.stop() if clocks else None
     final_loss = loss.cpu().numpy().tolist()
     counters = plan.counters()
     counters["numeric_ok"] = plan.af_sync_status() == af.AF_OK
+    # stage times: the same iterations replayed with the library's event pairs around
+    # each stage (kept out of the timed pass above, whose launches they would slow)
+    restore()
+    plan.set_timing(True)
+    for it in range(args.warmup + 1, args.warmup + args.steps + 1):
+        iterate(iq, s, g, m, v, it, loss, scale)
+    stream.synchronize()
+    stages = plan.stage_times()
+    plan.set_timing(False)
     # Live units, averaged over the timed iterations: the same iterations are run again
     # untimed from the saved state and counted after each.  Forward gathers: sum over
     # pixels of (elements that see the pixel)^2; adjoint gathers: only those of images
     # whose gradient is non-zero (the kernel skips the rest, whose terms are exactly
     # zero).  Rays: the delay kernel sums those of apodized-in pairs, the ray adjoint
     # those whose dL/dT is non-zero.
-    with torch.cuda.stream(stream):
-        for x, x0 in zip((s, m, v), state0):
-            x.copy_(x0)
+    restore()
     acc = {"das_forward": 0, "das_adjoint": 0, "delays": 0, "ray_adjoint": 0}
     for it in range(args.warmup + 1, args.warmup + args.steps + 1):
         iterate(iq, s, g, m, v, it, loss, scale)
@@ -622,21 +641,27 @@ def run_ours(args, rank, world, local_rank):
 
     # End to end: a stream of autofocus jobs, one per acquisition.  A job is the upload of
     # the acquisition and the initial map from pinned host memory, N_i = 100 iterations,
-    # and the read back of the final map and loss.  The next job's channel data goes up
-    # on a copy stream into the other of two device buffers while the current job
-    # iterates; a buffer is refilled only after the job that read it has finished.
+    # and the read back of the final map and loss into pinned memory.  The next job's
+    # channel data goes up on a copy stream into the other of two device buffers while
+    # the current job iterates; a buffer is refilled only after the job that read it has
+    # finished.  The host enqueues job after job and waits once, for the last read-back,
+    # inside the timed region.
     n_iter = 100
     h_iq = torch.view_as_real(torch.from_numpy(psi)).pin_memory() if dtype == af.AF_IQ_C64 else iq.cpu().pin_memory()
     h_scale = scale.cpu().pin_memory() if scale is not None else None
     h_s0 = torch.from_numpy(p.initial_slowness()).pin_memory()
-    h_out = torch.empty_like(h_s0).pin_memory()
-    h_loss = torch.empty(4).pin_memory()
+    # one read-back buffer per job: the host does not wait between jobs
+    h_out = [torch.empty_like(h_s0).pin_memory() for _ in range(max(args.e2e_jobs, 1))]
+    h_loss = [torch.empty(4).pin_memory() for _ in range(max(args.e2e_jobs, 1))]
     d_iq = [torch.empty(h_iq.shape, dtype=h_iq.dtype, device=dev) for _ in range(2)]
     d_scale = [torch.empty(h_scale.shape, device=dev) for _ in range(2)] if h_scale is not None else None
     h2d = h_iq.numel() * h_iq.element_size() + h_s0.numel() * 4 + (h_scale.numel() * 4 if h_scale is not None else 0)
-    d2h = h_out.numel() * 4 + 16
+    d2h = h_out[0].numel() * 4 + 16
     copy_stream = torch.cuda.Stream(device=dev)
     up_done = [torch.cuda.Event() for _ in range(2)]
+    setup_done = torch.cuda.Event()
+    up_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(args.e2e_jobs)]
     job_done = [torch.cuda.Event() for _ in range(2)]
 
     def upload(k):
@@ -644,34 +669,58 @@ def run_ours(args, rank, world, local_rank):
         with torch.cuda.stream(copy_stream):
             if k >= 2:
                 copy_stream.wait_event(job_done[b])
+            if k >= 1:
+                copy_stream.wait_event(setup_done)     # the current job's initial map goes first
+            up_ev[k][0].record(copy_stream)
             d_iq[b].copy_(h_iq, non_blocking=True)
             if d_scale is not None:
                 d_scale[b].copy_(h_scale, non_blocking=True)
+            up_ev[k][1].record(copy_stream)
             up_done[b].record(copy_stream)
 
+    # device time of each job's iterations, to separate the iteration mix of a whole job
+    # from what the host and the copies add
+    it_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(args.e2e_jobs)]
+    e2e_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    e2e_ev[0].record(stream)
+    host_ms = []
     if args.e2e_jobs:
         upload(0)
     for job in range(args.e2e_jobs):
+        th = time.perf_counter()
         b = job % 2
-        if job + 1 < args.e2e_jobs:
-            upload(job + 1)
         with torch.cuda.stream(stream):
             stream.wait_event(up_done[b])
             s.copy_(h_s0, non_blocking=True)
             m.zero_()
             v.zero_()
+            it_ev[job][0].record(stream)
+            setup_done.record(stream)
+        # the next acquisition's upload goes to the copy engine after this job's
+        # initial map, which would otherwise queue behind its 400 MB
+        if job + 1 < args.e2e_jobs:
+            upload(job + 1)
         iq_arg = torch.view_as_complex(d_iq[b]) if dtype == af.AF_IQ_C64 else d_iq[b]
         for it in range(1, n_iter + 1):
             iterate(iq_arg, s, g, m, v, it, loss, d_scale[b] if d_scale is not None else None)
+        host_ms.append((time.perf_counter() - th) * 1e3)     # host time to enqueue the job
         with torch.cuda.stream(stream):
+            it_ev[job][1].record(stream)
             job_done[b].record(stream)
-            h_out.copy_(s, non_blocking=True)
-            h_loss.copy_(loss, non_blocking=True)
-        stream.synchronize()
+            h_out[job].copy_(s, non_blocking=True)
+            h_loss[job].copy_(loss, non_blocking=True)
+    e2e_ev[1].record(stream)
+    stream.synchronize()
     e2e_s = time.perf_counter() - t0
+    e2e_iter_ms = [a.elapsed_time(z) for a, z in it_ev]
+    e2e_upload_ms = [a.elapsed_time(z) for a, z in up_ev]
+    e2e_gap_ms = ([e2e_ev[0].elapsed_time(it_ev[0][0])] +
+                  [it_ev[j][1].elapsed_time(it_ev[j + 1][0]) for j in range(args.e2e_jobs - 1)]
+                  if args.e2e_jobs else [])
     del d_iq, d_scale
     e2e_value, _ = (combine_ranks(e2e_s, args.e2e_jobs * n_iter, world, dev, independent=not sharded)
                     if args.e2e_jobs else (0.0, 0.0))
@@ -728,7 +777,12 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": "iterations/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h),
                 "step": f"one autofocus job of a stream of {args.e2e_jobs}: upload + {n_iter} iterations + read "
-                        "back; the next job's upload runs on a copy stream during this job's iterations"},
+                        "back; the next job's upload runs on a copy stream during this job's iterations",
+                "device_iter_ms_per_job": [round(x, 3) for x in e2e_iter_ms],
+                "upload_ms_per_job": [round(x, 3) for x in e2e_upload_ms],
+                "device_gap_ms_before_job": [round(x, 3) for x in e2e_gap_ms],
+                "host_enqueue_ms_per_job": [round(x, 3) for x in host_ms],
+                "device_iter_its": (n_iter * len(e2e_iter_ms) / (sum(e2e_iter_ms) * 1e-3)) if e2e_iter_ms else 0.0},
     }
     if ref is not None:
         n_patches = 40
