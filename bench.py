@@ -639,89 +639,22 @@ def run_ours(args, rank, world, local_rank):
     value, t_max = combine_ranks(ms * 1e-3, args.steps, world, dev, independent=not sharded)
     ms_max = t_max * 1e3
 
-    # End to end: a stream of autofocus jobs, one per acquisition.  A job is the upload of
-    # the acquisition and the initial map from pinned host memory, N_i = 100 iterations,
-    # and the read back of the final map and loss into pinned memory.  The next job's
-    # channel data goes up on a copy stream into the other of two device buffers while
-    # the current job iterates; a buffer is refilled only after the job that read it has
-    # finished.  The host enqueues job after job and waits once, for the last read-back,
-    # inside the timed region.
+    # End to end: a stream of autofocus jobs, one per acquisition, from pinned host
+    # memory: the upload of the acquisition and the initial map, N_i = 100 iterations
+    # and the read back of the final map and loss, inside the timed region.
     n_iter = 100
     h_iq = torch.view_as_real(torch.from_numpy(psi)).pin_memory() if dtype == af.AF_IQ_C64 else iq.cpu().pin_memory()
     h_scale = scale.cpu().pin_memory() if scale is not None else None
     h_s0 = torch.from_numpy(p.initial_slowness()).pin_memory()
-    # one read-back buffer per job: the host does not wait between jobs
-    h_out = [torch.empty_like(h_s0).pin_memory() for _ in range(max(args.e2e_jobs, 1))]
-    h_loss = [torch.empty(4).pin_memory() for _ in range(max(args.e2e_jobs, 1))]
-    d_iq = [torch.empty(h_iq.shape, dtype=h_iq.dtype, device=dev) for _ in range(2)]
-    d_scale = [torch.empty(h_scale.shape, device=dev) for _ in range(2)] if h_scale is not None else None
     h2d = h_iq.numel() * h_iq.element_size() + h_s0.numel() * 4 + (h_scale.numel() * 4 if h_scale is not None else 0)
-    d2h = h_out[0].numel() * 4 + 16
-    copy_stream = torch.cuda.Stream(device=dev)
-    up_done = [torch.cuda.Event() for _ in range(2)]
-    setup_done = torch.cuda.Event()
-    up_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-             for _ in range(args.e2e_jobs)]
-    job_done = [torch.cuda.Event() for _ in range(2)]
-
-    def upload(k):
-        b = k % 2
-        with torch.cuda.stream(copy_stream):
-            if k >= 2:
-                copy_stream.wait_event(job_done[b])
-            if k >= 1:
-                copy_stream.wait_event(setup_done)     # the current job's initial map goes first
-            up_ev[k][0].record(copy_stream)
-            d_iq[b].copy_(h_iq, non_blocking=True)
-            if d_scale is not None:
-                d_scale[b].copy_(h_scale, non_blocking=True)
-            up_ev[k][1].record(copy_stream)
-            up_done[b].record(copy_stream)
-
-    # device time of each job's iterations, to separate the iteration mix of a whole job
-    # from what the host and the copies add
-    it_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-             for _ in range(args.e2e_jobs)]
-    e2e_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e2e_ev[0].record(stream)
-    host_ms = []
-    if args.e2e_jobs:
-        upload(0)
-    for job in range(args.e2e_jobs):
-        th = time.perf_counter()
-        b = job % 2
-        with torch.cuda.stream(stream):
-            stream.wait_event(up_done[b])
-            s.copy_(h_s0, non_blocking=True)
-            m.zero_()
-            v.zero_()
-            it_ev[job][0].record(stream)
-            setup_done.record(stream)
-        # the next acquisition's upload goes to the copy engine after this job's
-        # initial map, which would otherwise queue behind its 400 MB
-        if job + 1 < args.e2e_jobs:
-            upload(job + 1)
-        iq_arg = torch.view_as_complex(d_iq[b]) if dtype == af.AF_IQ_C64 else d_iq[b]
-        for it in range(1, n_iter + 1):
-            iterate(iq_arg, s, g, m, v, it, loss, d_scale[b] if d_scale is not None else None)
-        host_ms.append((time.perf_counter() - th) * 1e3)     # host time to enqueue the job
-        with torch.cuda.stream(stream):
-            it_ev[job][1].record(stream)
-            job_done[b].record(stream)
-            h_out[job].copy_(s, non_blocking=True)
-            h_loss[job].copy_(loss, non_blocking=True)
-    e2e_ev[1].record(stream)
-    stream.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_iter_ms = [a.elapsed_time(z) for a, z in it_ev]
-    e2e_upload_ms = [a.elapsed_time(z) for a, z in up_ev]
-    e2e_gap_ms = ([e2e_ev[0].elapsed_time(it_ev[0][0])] +
-                  [it_ev[j][1].elapsed_time(it_ev[j + 1][0]) for j in range(args.e2e_jobs - 1)]
-                  if args.e2e_jobs else [])
-    del d_iq, d_scale
+    d2h = h_s0.numel() * 4 + 16
+    if not args.e2e_jobs:
+        e2e_s, e2e_diag = 0.0, {}
+    elif sharded:
+        e2e_s, e2e_diag = e2e_host_loop(args, iterate, stream, dev, barrier, h_iq, h_scale, h_s0, s, g, m, v,
+                                        loss, dtype, n_iter)
+    else:
+        e2e_s, e2e_diag = e2e_jobs(args, plan, stream, barrier, h_iq, h_scale, h_s0, n_iter)
     e2e_value, _ = (combine_ranks(e2e_s, args.e2e_jobs * n_iter, world, dev, independent=not sharded)
                     if args.e2e_jobs else (0.0, 0.0))
 
@@ -778,11 +711,7 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": int(d2h),
                 "step": f"one autofocus job of a stream of {args.e2e_jobs}: upload + {n_iter} iterations + read "
                         "back; the next job's upload runs on a copy stream during this job's iterations",
-                "device_iter_ms_per_job": [round(x, 3) for x in e2e_iter_ms],
-                "upload_ms_per_job": [round(x, 3) for x in e2e_upload_ms],
-                "device_gap_ms_before_job": [round(x, 3) for x in e2e_gap_ms],
-                "host_enqueue_ms_per_job": [round(x, 3) for x in host_ms],
-                "device_iter_its": (n_iter * len(e2e_iter_ms) / (sum(e2e_iter_ms) * 1e-3)) if e2e_iter_ms else 0.0},
+                **e2e_diag},
     }
     if ref is not None:
         n_patches = 40
@@ -796,6 +725,92 @@ def run_ours(args, rank, world, local_rank):
                                         f"({100 * frac:.0f} % of pixels, {dt:.1f} s), scaled by the pixel fraction"}}
         line["error_vs_fp64_oracle"] = {k: v_ for k, v_ in ref.items() if k.startswith("fp32")}
     print(json.dumps(line), flush=True)
+
+
+def e2e_jobs(args, plan, stream, barrier, h_iq, h_scale, h_s0, n_iter):
+    """A stream of jobs through af_job_submit (host buffers in, host buffers out): the
+    library uploads each acquisition on its copy stream under the previous job's
+    iterations; the host submits job after job and waits once, in af_job_wait."""
+    import torch
+    jobs = args.e2e_jobs
+    h_out = [torch.empty_like(h_s0).pin_memory() for _ in range(jobs)]
+    h_loss = [torch.empty(4).pin_memory() for _ in range(jobs)]
+    plan.job_reserve()                       # device buffers, before the timed region
+    # events on the plan's stream around each job's work there (initial map, wait for
+    # its channel data, iterations, read back)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(jobs)]
+    host_ms = []
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(jobs):
+        th = time.perf_counter()
+        ev[k][0].record(stream)
+        plan.job_submit(h_iq, h_s0, n_iter, h_out[k], h_loss[k], h_iq_scale=h_scale)
+        ev[k][1].record(stream)
+        host_ms.append((time.perf_counter() - th) * 1e3)
+    plan.job_wait()
+    e2e_s = time.perf_counter() - t0
+    job_ms = [a.elapsed_time(z) for a, z in ev]
+    if not all(np.isfinite(x.numpy()).all() for x in h_out):
+        raise RuntimeError("e2e: non-finite map read back")
+    return e2e_s, {"api": "af_job_submit / af_job_wait (host buffers)",
+                   "device_ms_per_job": [round(x, 3) for x in job_ms],
+                   "host_submit_ms_per_job": [round(x, 3) for x in host_ms],
+                   "device_its_after_first": (n_iter * (jobs - 1) / (sum(job_ms[1:]) * 1e-3)) if jobs > 1 else 0.0}
+
+
+def e2e_host_loop(args, iterate, stream, dev, barrier, h_iq, h_scale, h_s0, s, g, m, v, loss, dtype, n_iter):
+    """The same stream of jobs for a patch-sharded acquisition, whose iterations need
+    collectives between stages: torch copies on a copy stream and the per-stage calls."""
+    import torch
+
+    import paper_2608_06853_b300 as af
+    jobs = args.e2e_jobs
+    h_out = [torch.empty_like(h_s0).pin_memory() for _ in range(jobs)]
+    h_loss = [torch.empty(4).pin_memory() for _ in range(jobs)]
+    d_iq = [torch.empty(h_iq.shape, dtype=h_iq.dtype, device=dev) for _ in range(2)]
+    d_scale = [torch.empty(h_scale.shape, device=dev) for _ in range(2)] if h_scale is not None else None
+    copy_stream = torch.cuda.Stream(device=dev)
+    up_done = [torch.cuda.Event() for _ in range(2)]
+    job_done = [torch.cuda.Event() for _ in range(2)]
+    setup_done = torch.cuda.Event()
+
+    def upload(k):
+        b = k % 2
+        with torch.cuda.stream(copy_stream):
+            if k >= 2:
+                copy_stream.wait_event(job_done[b])
+            if k >= 1:
+                copy_stream.wait_event(setup_done)     # the current job's initial map goes first
+            d_iq[b].copy_(h_iq, non_blocking=True)
+            if d_scale is not None:
+                d_scale[b].copy_(h_scale, non_blocking=True)
+            up_done[b].record(copy_stream)
+
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    upload(0)
+    for job in range(jobs):
+        b = job % 2
+        with torch.cuda.stream(stream):
+            stream.wait_event(up_done[b])
+            s.copy_(h_s0, non_blocking=True)
+            m.zero_()
+            v.zero_()
+            setup_done.record(stream)
+        if job + 1 < jobs:
+            upload(job + 1)
+        iq_arg = torch.view_as_complex(d_iq[b]) if dtype == af.AF_IQ_C64 else d_iq[b]
+        for it in range(1, n_iter + 1):
+            iterate(iq_arg, s, g, m, v, it, loss, d_scale[b] if d_scale is not None else None)
+        with torch.cuda.stream(stream):
+            job_done[b].record(stream)
+            h_out[job].copy_(s, non_blocking=True)
+            h_loss[job].copy_(loss, non_blocking=True)
+    stream.synchronize()
+    return time.perf_counter() - t0, {"api": "per-stage calls with collectives (patch split), torch copies"}
 
 
 def main():

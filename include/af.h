@@ -161,7 +161,40 @@ af_status af_iterate(af_plan_t plan, const void *d_iq, const float *d_iq_scale,
                      float *d_slowness, float *d_grad, float *d_adam_m,
                      float *d_adam_v, int step, float *d_loss);
 
-/* Release the plan's device memory.  NULL is accepted. */
+/* ---- autofocus jobs from host memory (Sec. III-A: N_i iterations per acquisition) ----
+ * A job uploads one acquisition's channel data and initial map, runs n_iter
+ * af_iterate steps (Adam step index 1..n_iter, moments starting at zero) and reads
+ * back the final map and loss.  af_job_submit only enqueues: the upload goes on a
+ * copy stream owned by the plan, into one of two device buffers (the one the job
+ * before last used, once that job has finished), and the rest on the plan's stream,
+ * so a job submitted while another runs has its channel data uploaded under the
+ * running job's iterations.  Each job's initial-map copy is ordered before the next
+ * job's channel data on the copy engine.
+ *  - Host buffers are read and written asynchronously: they must stay valid and
+ *    unchanged until af_job_wait.  Pinned memory (cudaHostAlloc / cudaHostRegister)
+ *    gives the overlap; pageable memory works but the copies then serialise.
+ *  - Device memory: af_job_reserve allocates 2 x the channel data
+ *    (n_elem^2 n_samp x 8 bytes for AF_IQ_C64, x 4 for 16-bit), 2 x n_elem floats,
+ *    4 grids of nz x nx floats and 4 floats, once per plan; af_destroy frees them.
+ *  - Errors: argument errors are reported before anything is enqueued; a CUDA error
+ *    or an af_iterate error returns at once (work already enqueued stays queued).
+ *
+ * af_job_reserve: creates the job buffers, copy stream and events (idempotent;
+ *   af_job_submit calls it when needed).
+ * af_job_submit:
+ *   h_iq        Psi in host memory, layout per the plan's iq_dtype (as af_forward).
+ *   h_iq_scale  [n_elem] per-transmit scale for 16-bit dtypes (host), else NULL.
+ *   h_s0        [nz][nx] initial slowness (host), s/m.
+ *   n_iter      iterations, >= 1.
+ *   h_s_out     [nz][nx] final slowness (host), or NULL for no read back.
+ *   h_loss_out  [4] loss of the last iteration {L, L_CMPE, R_TV, R_SV} (host), or NULL.
+ * af_job_wait: waits for every submitted job and returns af_sync_status. */
+af_status af_job_reserve(af_plan_t plan);
+af_status af_job_submit(af_plan_t plan, const void *h_iq, const float *h_iq_scale, const float *h_s0,
+                        int n_iter, float *h_s_out, float *h_loss_out);
+af_status af_job_wait(af_plan_t plan);
+
+/* Release the plan's device memory (job buffers included).  NULL is accepted. */
 af_status af_destroy(af_plan_t plan);
 
 /* ---- batches of independent acquisitions (one job, one graph launch) ----

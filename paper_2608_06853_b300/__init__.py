@@ -86,6 +86,9 @@ _SIGNATURES = {
     "af_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int]),
     "af_iterate": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
     "af_destroy": (ctypes.c_int, [_VP]),
+    "af_job_reserve": (ctypes.c_int, [_VP]),
+    "af_job_submit": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
+    "af_job_wait": (ctypes.c_int, [_VP]),
     "af_batch_plan": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.POINTER(AfConfig)), _VP,
                                       ctypes.POINTER(_VP)]),
     "af_batch_plan_of": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(_VP)]),
@@ -205,6 +208,20 @@ def _ptr(t):
         raise TypeError("device tensors only (torch.Tensor on cuda)")
     if not t.is_contiguous():
         raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(t, dtype, nbytes: int, what: str):
+    """Address of a host tensor of exactly nbytes bytes (contiguous, given dtype)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{what}: host tensors only (torch.Tensor on the CPU)")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: tensor must be contiguous")
+    if dtype is not None and t.dtype not in (dtype if isinstance(dtype, tuple) else (dtype,)):
+        raise ValueError(f"{what}: dtype {t.dtype}")
+    if t.numel() * t.element_size() != nbytes:
+        raise ValueError(f"{what}: {t.numel() * t.element_size()} bytes, expected {nbytes}")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -351,6 +368,34 @@ class Plan:
 
     def af_sync_status(self) -> int:
         return self.lib.af_sync_status(self.handle)
+
+    # ---- autofocus jobs from host memory ----
+    def job_reserve(self):
+        """Device buffers, copy stream and events of af_job_submit (af_job_reserve)."""
+        _check(self.lib.af_job_reserve(self.handle), "af_job_reserve")
+
+    def job_submit(self, h_iq, h_s0, n_iter: int, h_s_out=None, h_loss=None, h_iq_scale=None):
+        """Enqueue one job: upload of h_iq and h_s0 (host tensors, pinned for overlap),
+        n_iter iterations, read back into h_s_out ([nz][nx] float32) and h_loss ([4]
+        float32).  The host tensors are kept alive until job_wait."""
+        import torch
+        ns = int(self.problem.ns)
+        ebytes = 8 if self.iq_dtype == AF_IQ_C64 else 4
+        iq_dt = (torch.complex64, torch.float32) if self.iq_dtype == AF_IQ_C64 else (torch.bfloat16, torch.float16)
+        ng = self.nx * self.nz
+        args = [_hptr(h_iq, iq_dt, self.ne * self.ne * ns * ebytes, "h_iq"),
+                None if h_iq_scale is None else _hptr(h_iq_scale, torch.float32, 4 * self.ne, "h_iq_scale"),
+                _hptr(h_s0, torch.float32, 4 * ng, "h_s0"), int(n_iter),
+                None if h_s_out is None else _hptr(h_s_out, torch.float32, 4 * ng, "h_s_out"),
+                None if h_loss is None else _hptr(h_loss, torch.float32, 16, "h_loss")]
+        self._job_refs = getattr(self, "_job_refs", []) + [h_iq, h_iq_scale, h_s0, h_s_out, h_loss]
+        _check(self.lib.af_job_submit(self.handle, *args), "af_job_submit")
+
+    def job_wait(self):
+        """Wait for every submitted job (af_job_wait); raises on an error status."""
+        st = self.lib.af_job_wait(self.handle)
+        self._job_refs = []
+        _check(st, "af_job_wait")
 
     def af_sweep(self, iq, speeds, c_ref, dynamic=True, iq_scale=None):
         """L_CMPE and active terms of uniform maps at each speed (af_sweep); returns

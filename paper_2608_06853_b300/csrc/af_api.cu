@@ -243,6 +243,7 @@ af_status af_workspace_bytes(const af_config *c, size_t *bytes)
 af_status af_destroy(af_plan_t pl)
 {
     if (!pl) return AF_OK;
+    jobs_release(pl);
     for (int k = 0; k < 2 * kTimingCap; ++k)
         if (pl->ev[k]) cudaEventDestroy(pl->ev[k]);
     void *ptrs[] = {pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->D, pl->nrange, pl->B, pl->G, pl->z,

@@ -90,6 +90,8 @@ struct AfScal {
     int ray_next;        // next item block of the ray adjoint (zero between launches)
 };
 
+struct AfJobs;          // jobs from host memory (af_job_*): staging buffers, copy stream, events
+
 struct af_plan_s {
     AfGeom g;
     af_config cfg;       // scalar copy of the configuration (host pointers cleared)
@@ -137,6 +139,7 @@ struct af_plan_s {
     MlpNorm mlp_norm;
     MlpGeom mlp_geom;
     bool use_surrogate, sur_trained;
+    AfJobs *jobs;        // created by af_job_reserve (or the first af_job_submit)
     // stage timing: a ring of (start, stop) event pairs per recorded launch
     bool timing;
     int n_rec;
@@ -230,6 +233,9 @@ af_status af_set_error(af_status st, const char *fmt, ...);
 
 // tries of the first tensor-core completion wait (af_set_wait_limit; default about a second)
 uint32_t af_wait_tries();
+
+// releases a plan's job buffers, stream and events (af_destroy)
+void jobs_release(af_plan_t pl);
 
 // ---- launchers (each in its own .cu file) ----
 cudaError_t launch_grid_stats(af_plan_t pl, const float *s);

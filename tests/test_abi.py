@@ -181,3 +181,11 @@ def test_new_entry_points_refuse_null_arguments_without_a_gpu():
     rate = ctypes.c_double()
     assert lib.af_fp32_lane_rate(None, None, ctypes.byref(rate)) == af.AF_ERR_ARG
     assert lib.af_set_wait_limit(-1) == af.AF_OK
+
+
+def test_job_entry_points_refuse_null_arguments_without_a_gpu():
+    """af_job_reserve / af_job_submit / af_job_wait check their arguments on the host."""
+    lib = af.load()
+    assert lib.af_job_reserve(None) == af.AF_ERR_ARG
+    assert lib.af_job_submit(None, None, None, None, 1, None, None) == af.AF_ERR_ARG
+    assert lib.af_job_wait(None) == af.AF_ERR_ARG
