@@ -526,8 +526,53 @@ def run_batch(args, dev, n_iter=100, n_scat=20_000):
         ms = e0.elapsed_time(e1)
         res[name] = {"iterations_per_s": len(probs) * n_iter / (ms * 1e-3), "job_ms": ms,
                      "numeric_ok": all(pl.af_sync_status() == af.AF_OK for pl in br.plans)}
+        if not sur:
+            br.reset()
+            res[name]["kernel_trace"] = trace_concurrency(lambda: br.replay(), dev)
     br.close()
     return res
+
+
+def trace_concurrency(run, dev):
+    """One run under CUDA activity tracing (torch.profiler, CUPTI): every kernel's GPU
+    start and end, graph nodes included.  Returns the span from the first kernel's
+    start to the last kernel's end, the time with no kernel running (GPU idle), the
+    mean number of kernels in flight, and the time with exactly one in flight."""
+    import torch
+    from torch.autograd import DeviceType
+    from torch.profiler import ProfilerActivity, profile
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        run()
+        torch.cuda.synchronize(dev)
+    iv = sorted((e.time_range.start, e.time_range.end) for e in prof.events()
+                if e.device_type == DeviceType.CUDA and e.time_range.end > e.time_range.start
+                and not e.name.startswith(("Memcpy", "Memset", "cudaM")))
+    out = interval_stats(iv)
+    out["kernels"] = len(iv)
+    out["span_ms"] = out.pop("span") * 1e-3
+    return dict(out, note="traced replay (CUPTI adds overhead; the timed replay above has none)")
+
+
+def interval_stats(iv):
+    """Busy-time statistics of kernel intervals [(start, end)], by a sweep over their
+    end points: span (first start to last end), the fraction of the span with no
+    interval open (idle), with exactly one open, and the mean number open."""
+    if not iv:
+        return {"span": 0.0, "idle_fraction": 0.0, "single_kernel_fraction": 0.0, "mean_kernels_in_flight": 0.0}
+    pts = sorted([(a, 1) for a, _ in iv] + [(b, -1) for _, b in iv])
+    busy = one = 0.0
+    depth, last = 0, pts[0][0]
+    for t, d in pts:
+        if depth >= 1:
+            busy += t - last
+        if depth == 1:
+            one += t - last
+        depth += d
+        last = t
+    span = max(b for _, b in iv) - min(a for a, _ in iv)
+    total = sum(b - a for a, b in iv)
+    return {"span": span, "idle_fraction": 1.0 - busy / span, "single_kernel_fraction": one / span,
+            "mean_kernels_in_flight": total / span}
 
 
 # ---------------------------------------------------------------- our arm

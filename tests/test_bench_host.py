@@ -60,3 +60,17 @@ def test_lane_peak_prefers_the_measured_rate():
     rate, src = bench.lane_peak(148, {"sm_mhz": 2032.0}, PEAKS, measured=36.0e12)
     assert rate == 36.0e12
     assert src.startswith("measured") and "0.935" in src
+
+
+def test_interval_stats_of_kernel_traces():
+    """Busy-time sweep of the batch trace: hand-made intervals with known answers."""
+    # [0, 4] and [2, 6] overlap on [2, 4]; [8, 10] after an idle gap [6, 8]
+    st = bench.interval_stats([(0.0, 4.0), (2.0, 6.0), (8.0, 10.0)])
+    assert st["span"] == 10.0
+    assert abs(st["idle_fraction"] - 0.2) < 1e-12                 # [6, 8]
+    assert abs(st["single_kernel_fraction"] - 0.6) < 1e-12        # [0, 2], [4, 6], [8, 10]
+    assert abs(st["mean_kernels_in_flight"] - 1.0) < 1e-12        # (4 + 4 + 2) / 10
+    # nested and touching intervals
+    st = bench.interval_stats([(0.0, 10.0), (1.0, 2.0), (2.0, 3.0)])
+    assert st["idle_fraction"] == 0.0 and abs(st["single_kernel_fraction"] - 0.8) < 1e-12
+    assert bench.interval_stats([])["span"] == 0.0
