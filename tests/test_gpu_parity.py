@@ -204,7 +204,7 @@ def test_plain_gradient_step_parity(tiny_case):
 
 
 def test_ragged_and_variant_shapes():
-    """Pixel count not a multiple of 32, no lens, sub_width 2 and 8, printed Eq. 4; one
+    """Pixel count not a multiple of 32, no lens, sub_width 1, 2, 8 and 16, printed Eq. 4; one
     CTA's pixels spread over the whole depth range; an odd trace length; samples
     outside the trace for some pixels; the Eq. 6 conventional lens model and non-zero
     t_ttp / t0."""
@@ -225,6 +225,8 @@ def test_ragged_and_variant_shapes():
         dict(n_ang=5, n_rad=2, patch_w=5, lens_mode=1),         # straight rays, 250 pixels
         dict(n_ang=2, n_rad=3, patch_w=3, sub_width=2),         # 16 subapertures
         dict(n_ang=2, n_rad=2, patch_w=4, sub_width=8),         # 4 subapertures
+        dict(n_ang=2, n_rad=2, patch_w=3, sub_width=1),         # 32 one-element subapertures, 1024 images
+        dict(n_ang=2, n_rad=2, patch_w=3, sub_width=16),        # 2 subapertures: images only, no CMPE pair
         dict(n_ang=3, n_rad=2, patch_w=3, apod_mode=1, hyper=dict(synth.TABLE2["phantom_c5"], fnum=3.0)),
     ]
     for kw in cases:
