@@ -12,8 +12,6 @@
 // The copy engine therefore takes a job's small initial-map copy before the
 // next job's channel data, and a buffer is refilled only after the job that
 // read it has finished.
-#include <vector>
-
 #include "af_internal.cuh"
 
 struct AfJobs {
@@ -108,7 +106,12 @@ extern "C" af_status af_job_submit(af_plan_t pl, const void *h_iq, const float *
     for (int it = 1; it <= n_iter; ++it) {
         const af_status s = af_iterate(pl, j->iq[b], half ? j->scale[b] : nullptr, j->s, j->grad, j->m, j->v, it,
                                        j->loss);
-        if (s != AF_OK) return s;
+        if (s != AF_OK) {
+            // whatever this job enqueued still reads buffer b: a later upload into it
+            // must wait for that work too
+            cudaEventRecord(j->done[b], st);
+            return s;
+        }
     }
     if (h_s_out) JOB_CUDA(cudaMemcpyAsync(h_s_out, j->s, ng * sizeof(float), cudaMemcpyDeviceToHost, st));
     if (h_loss_out) JOB_CUDA(cudaMemcpyAsync(h_loss_out, j->loss, 4 * sizeof(float), cudaMemcpyDeviceToHost, st));
