@@ -561,3 +561,36 @@ def test_bmode_and_integrated_cmpe_images(tiny_case):
     patch = slice(P * q.patch_npix, (P + 1) * q.patch_npix)
     assert int(np.argmax(b1[patch])) == q.patch_npix // 2
     assert c1[centre] < 1e-3
+
+
+def test_seeded_random_configurations():
+    """Sixteen seeded random small problems drawn over element count, subaperture width
+    (1-8), patch layout and width, trace length (some traces end before the deepest
+    pixels), grid size, depth range, lens model (bent ray or Eq. 6), f-number rule,
+    t0 and t_ttp: delays, images, loss and dL/ds (regularisers off, so the ray
+    adjoint is not hidden) against the oracle at the usual tolerances."""
+    rng = np.random.default_rng(20261204)
+    ran = 0
+    for case in range(16):
+        ne = int(rng.choice([16, 24, 32, 40]))
+        sub = int(rng.choice([w for w in (1, 2, 4, 8) if ne % w == 0 and ne // w >= 2]))
+        d0 = float(rng.uniform(6e-3, 15e-3))
+        kw = dict(ne=ne, sub_width=sub, n_ang=int(rng.integers(1, 5)), n_rad=int(rng.integers(1, 5)),
+                  patch_w=int(rng.integers(2, 7)), ns=int(rng.integers(600, 1400)),
+                  nx=int(rng.integers(8, 41)), nz=int(rng.integers(8, 41)),
+                  depth_min=d0, depth_max=d0 + float(rng.uniform(5e-3, 40e-3)),
+                  lens_mode=int(rng.choice([0, 0, 1])), apod_mode=int(rng.integers(0, 2)),
+                  t0=float(rng.choice([0.0, 2e-6])), t_ttp=float(rng.choice([0.0, 5e-7])))
+        p = ray_only(synth.config_tiny(**kw))
+        if af.check_config(p) != af.AF_OK:
+            continue
+        psi = synth.simulate(p, 400, seed=100 + case)
+        run, o, ref = full_parity(p, psi, smooth_speed(p, 30 + case))
+        on = run.apod == 1
+        if on.any():
+            assert np.abs(run.T - ref["T"])[on].max() <= DELAY_TOL, kw
+        assert rel_l2(run.B, ref["B"]) <= IMG_TOL, kw
+        assert abs(run.L[0] - ref["parts"][0]) <= LOSS_TOL * max(abs(ref["parts"][0]), 1e-12), kw
+        assert rel_l2(run.dLds, ref["grad"]) <= GRAD_TOL, kw
+        ran += 1
+    assert ran >= 12
