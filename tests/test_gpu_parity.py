@@ -594,3 +594,34 @@ def test_seeded_random_configurations():
         assert rel_l2(run.dLds, ref["grad"]) <= GRAD_TOL, kw
         ran += 1
     assert ran >= 12
+
+
+@pytest.mark.parametrize("lens_mode", [af.AF_LENS_PLANAR, af.AF_LENS_NONE])
+def test_seeded_random_linear_configurations(lens_mode):
+    """Six seeded random linear-array problems per lens model (the flat-lens bent ray
+    of Eq. 8, and the Eq. 6 straight ray with t_ttp): element count, subaperture
+    width, patch layout, trace length, grid and depth drawn at random; delays,
+    images, loss and dL/ds (regularisers off) against the oracle."""
+    rng = np.random.default_rng(20261205 + lens_mode)
+    ran = 0
+    for case in range(6):
+        ne = int(rng.choice([16, 24, 32]))
+        sub = int(rng.choice([w for w in (1, 2, 4, 8) if ne % w == 0 and ne // w >= 2]))
+        d0 = float(rng.uniform(3e-3, 8e-3))
+        kw = dict(ne=ne, sub_width=sub, lens_mode=lens_mode, n_lat=int(rng.integers(1, 5)),
+                  n_ax=int(rng.integers(1, 5)), patch_w=int(rng.integers(2, 7)), ns=int(rng.integers(500, 1100)),
+                  nx=int(rng.integers(8, 33)), nz=int(rng.integers(8, 33)),
+                  depth_min=d0, depth_max=d0 + float(rng.uniform(4e-3, 16e-3)))
+        p = ray_only(synth.config_linear_tiny(**kw))
+        if af.check_config(p) != af.AF_OK:
+            continue
+        psi = synth.simulate(p, 400, seed=200 + case)
+        run, o, ref = full_parity(p, psi, smooth_speed(p, 50 + case))
+        on = run.apod == 1
+        if on.any():
+            assert np.abs(run.T - ref["T"])[on].max() <= DELAY_TOL, kw
+        assert rel_l2(run.B, ref["B"]) <= IMG_TOL, kw
+        assert abs(run.L[0] - ref["parts"][0]) <= LOSS_TOL * max(abs(ref["parts"][0]), 1e-12), kw
+        assert rel_l2(run.dLds, ref["grad"]) <= GRAD_TOL, kw
+        ran += 1
+    assert ran >= 4
