@@ -465,6 +465,30 @@ def run_sweep_images(p, iq32, plan32, stream, dev):
             plan32.bmode()
         e1.record(stream)
     torch.cuda.synchronize(dev)
+    # a full-sector B-mode frame (Figs. 2 and 4): a second plan whose pixels are a dense
+    # polar grid, 256 lines x 512 depths from 10 to 140 mm below the lens (one "patch"
+    # per depth row); one forward at the map and the envelope, CUDA events over 5 frames
+    q = synth.image_grid_problem(p, 256, 512, (10e-3, 140e-3))
+    fov = None
+    if af.check_config(q) == af.AF_OK:
+        pl_img = af.Plan(q, stream=stream)
+        with torch.cuda.stream(stream):
+            loss_i = torch.zeros(4, device=dev)
+            pl_img.af_forward(iq32, s0, loss_i)
+            pl_img.bmode()
+        torch.cuda.synchronize(dev)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            f0.record(stream)
+            for _ in range(5):
+                pl_img.af_forward(iq32, s0, loss_i)
+                env, _ = pl_img.bmode()
+            f1.record(stream)
+        torch.cuda.synchronize(dev)
+        fov = {"lines": 256, "depths": 512, "pixels": int(q.n_patch * q.patch_npix),
+               "depth_mm": [10.0, 140.0], "ms_per_frame": f0.elapsed_time(f1) / 5,
+               "finite": bool(torch.isfinite(env).all())}
+        del pl_img
     # image metrics of that forward: target = pixels inside the medium's cysts, background
     # = every other pixel (host wall time: scratch allocation, kernels and read back)
     inside = np.zeros(p.npix, bool)
@@ -477,7 +501,7 @@ def run_sweep_images(p, iq32, plan32, stream, dev):
     t_met = time.perf_counter() - t1
     return {"sweep_speeds": len(speeds), "sweep_ms": t_sweep * 1e3, "sweep_ms_per_speed": t_sweep * 1e3 / len(speeds),
             "sweep_best_mps": best, "sweep_cmpe_min": float(cmpe.min()), "sweep_cmpe_max": float(cmpe.max()),
-            "images_ms": e0.elapsed_time(e1) / 10, "metrics_ms": t_met * 1e3,
+            "images_ms": e0.elapsed_time(e1) / 10, "metrics_ms": t_met * 1e3, "full_fov_bmode": fov,
             "metrics": {k: met[k] for k in ("cf_mean", "loc", "cmcc", "contrast_db", "gcnr", "n_in")},
             "note": "sweep: wall time incl. host pixel moves and per-speed readback; images: CUDA events"}
 
