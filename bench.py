@@ -734,8 +734,9 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu_baseline and dtype == af.AF_IQ_C64:
         ref = oracle_reference(p, psi, plan, iq, stream, dev)
 
+    # the variants are reported by rank 0 only (no collective follows them)
     variants = None
-    if not args.no_variants and dtype == af.AF_IQ_C64 and not sharded:
+    if rank == 0 and not args.no_variants and dtype == af.AF_IQ_C64 and not sharded:
         variants = run_variants(args, p, psi, plan, iq, stream, dev, ms_max / args.steps, ref)
 
     if rank != 0:
