@@ -110,6 +110,14 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU oracle
+def oracle_step(o, problem, s, grad):
+    """The oracle's update of Eq. 9 by the problem's rule: the plain gradient step, or
+    Adam's first step."""
+    if problem.optimizer == 1:
+        return o.gd(s, grad, problem.lr, problem.c_unit)
+    return o.adam(s, grad, np.zeros_like(s), np.zeros_like(s), 1, problem.lr, c_unit=problem.c_unit)[0]
+
+
 def oracle_sample(problem, psi, s, n_patches, seed=0, parallel=False):
     """One forward + adjoint + Adam step of the FP64 oracle on n_patches of the
     workload's patches (all of them if n_patches >= n_patch); returns (seconds,
@@ -131,7 +139,7 @@ def oracle_sample(problem, psi, s, n_patches, seed=0, parallel=False):
     sd = s.astype(np.float64)
     t0 = time.perf_counter()
     parts, g, _, _ = o.loss_grad(psi, sd)
-    o.adam(sd, g, np.zeros_like(sd), np.zeros_like(sd), 1, problem.lr, c_unit=problem.c_unit)
+    oracle_step(o, problem, sd, g)
     dt = time.perf_counter() - t0
     return dt, n_patches / problem.n_patch
 
@@ -300,7 +308,7 @@ def oracle_reference(p, psi, plan, iq, stream, dev):
     sd = s0.astype(np.float64)
     t0 = time.perf_counter()
     parts, grad, _, _ = o.loss_grad(psi, sd, apod_in=apod, mask_in=mask)
-    o.adam(sd, grad, np.zeros_like(sd), np.zeros_like(sd), 1, p.lr, c_unit=p.c_unit)
+    oracle_step(o, p, sd, grad)
     dt = time.perf_counter() - t0
     T, _, _ = o.delays(sd, apod_in=apod)
     B_or = o.das(psi, T, apod)
