@@ -7,6 +7,8 @@ forward pass and must give the CMPE loss and active-term count of that pass
 (loss within the parity tolerance of the other tests), without a plan.  This
 file is collected last so that a run stopping at the first failure has
 already run every other test; it also passes on its own in a fresh process."""
+import gc
+
 import numpy as np
 import pytest
 
@@ -50,20 +52,28 @@ def test_noalloc_cmpe_matches_planned_forward_twice(planned_forward):
 
 def test_noalloc_calls_leave_device_memory_unchanged(planned_forward):
     """The point of the entry point: after a first call, further calls change neither
-    the device's free memory (cudaMemGetInfo) nor torch's allocated bytes."""
+    the device's free memory (cudaMemGetInfo) nor torch's allocated bytes.  Garbage
+    left by earlier tests (reference cycles holding device tensors) is collected
+    first, and the collector stays off while the calls are measured, so that only
+    the entry point can change the counts."""
     p, plan, B, L_ref, M_ref = planned_forward
     dev = torch.device("cuda")
     out = torch.zeros(1, device=dev)
     n = torch.zeros(1, dtype=torch.int32, device=dev)
     af.af_cmpe_loss_noalloc(B, p.nsub, p.n_patch, p.patch_npix, p.rho_thresh, out, n)
     torch.cuda.synchronize()
-    free0, _ = torch.cuda.mem_get_info()
-    alloc0 = torch.cuda.memory_allocated()
-    for _ in range(5):
-        af.af_cmpe_loss_noalloc(B, p.nsub, p.n_patch, p.patch_npix, p.rho_thresh, out, n)
-    torch.cuda.synchronize()
-    assert torch.cuda.mem_get_info()[0] == free0
-    assert torch.cuda.memory_allocated() == alloc0
+    gc.collect()
+    gc.disable()
+    try:
+        free0, _ = torch.cuda.mem_get_info()
+        alloc0 = torch.cuda.memory_allocated()
+        for _ in range(5):
+            af.af_cmpe_loss_noalloc(B, p.nsub, p.n_patch, p.patch_npix, p.rho_thresh, out, n)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert torch.cuda.memory_allocated() == alloc0
+    finally:
+        gc.enable()
 
 
 def test_noalloc_after_a_different_call_uses_fresh_scratch(planned_forward):
