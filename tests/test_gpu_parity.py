@@ -349,7 +349,7 @@ def test_autograd_function_matches_adjoint(tiny_case):
     plan.af_adjoint(g)
     # float atomics make the two adjoint runs differ in the last bits only
     torch.testing.assert_close(s.grad, 2.0 * g, rtol=1e-4, atol=1e-6 * float(g.abs().max()))
-    assert float(L) == pytest.approx(float(loss[0]))
+    assert float(L.detach()) == pytest.approx(float(loss[0]))
 
 
 def test_error_statuses():
