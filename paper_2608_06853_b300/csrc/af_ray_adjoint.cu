@@ -302,7 +302,10 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
                     v += acci[rg.base_b + j * rg.pb + i];
                     acci[rg.base_b + j * rg.pb + i] = 0;
                 }
-                if (v != 0) mypad[j * P + i] += v;
+                // the CTA's own accumulator: an uncontended integer add the thread does
+                // not wait for (an exact sum in any order)
+                if (v != 0) atomicAdd(reinterpret_cast<unsigned long long *>(mypad + j * P + i),
+                                      (unsigned long long)(long long)v);
             }
             __syncthreads();
         }
