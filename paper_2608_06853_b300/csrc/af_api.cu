@@ -232,7 +232,7 @@ af_status af_workspace_bytes(const af_config *c, size_t *bytes)
     b += 2 * nb * npix * sizeof(float2);                                  // B, G
     b += (size_t)c->n_patch * npair * (sizeof(float2) + 1);               // z, mask
     b += (size_t)c->n_patch * (sizeof(double) + sizeof(int));
-    b += 148 * 8 * ng * sizeof(float);                                     // partial grids (upper bound)
+    b += (size_t)(c->nx + 5) * (c->nz + 4) * sizeof(long long);            // ray-adjoint integer grid
     b += sizeof(AfScal) + kStatBlocks * sizeof(double4);
     b += 4 * (size_t)AF_MLP_NPARAM * sizeof(float) + 2 * 128 * 128 * 2 + ne * npix;   // surrogate
     b += npix * 2 * sizeof(float2) + (size_t)c->n_patch * 5 * sizeof(double) + ng * sizeof(float);   // sweep
@@ -247,7 +247,7 @@ af_status af_destroy(af_plan_t pl)
     for (int k = 0; k < 2 * kTimingCap; ++k)
         if (pl->ev[k]) cudaEventDestroy(pl->ev[k]);
     void *ptrs[] = {pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->D, pl->nrange, pl->B, pl->G, pl->z,
-                    pl->mask, pl->patch_sum, pl->patch_cnt, pl->gdel, pl->gpart, pl->gpad, pl->scal, pl->stat_part,
+                    pl->mask, pl->patch_sum, pl->patch_cnt, pl->gdel, pl->gpad, pl->scal, pl->stat_part,
                     pl->mlp_p, pl->mlp_m, pl->mlp_v, pl->mlp_g, pl->mlp_w2b, pl->mlp_w3b, pl->sur_fb};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -457,8 +457,7 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
     pl->smem_grid = padded_grid_bytes(c);
     pl->delay = delays_shape(pl->smem_grid, pl->sm_count);
     pl->rayadj = rayadj_shape(c->nx, c->nz, g.pitch, pl->sm_count);
-    AF_ALLOC(pl->gpart, (size_t)pl->rayadj.blocks * g.ng * sizeof(long long));
-    AF_ALLOC(pl->gpad, (size_t)pl->rayadj.blocks * (pl->smem_grid / sizeof(float)) * sizeof(long long));
+    AF_ALLOC(pl->gpad, (pl->smem_grid / sizeof(float)) * sizeof(long long));
     AF_ALLOC(pl->mlp_p, AF_MLP_NPARAM * sizeof(float));
     AF_ALLOC(pl->mlp_m, AF_MLP_NPARAM * sizeof(float));
     AF_ALLOC(pl->mlp_v, AF_MLP_NPARAM * sizeof(float));

@@ -122,8 +122,7 @@ struct af_plan_s {
     double *patch_sum;   // [n_patch] sum m |arg z|
     int *patch_cnt;      // [n_patch] sum m
     float *gdel;         // [ne][npix] dL/dT
-    long long *gpart;    // [rayadj.blocks][ng] per-CTA partial gradients (fixed point)
-    long long *gpad;     // [rayadj.blocks][padded grid] per-CTA fixed-point accumulators
+    long long *gpad;     // [padded grid] fixed-point accumulator of the ray adjoint (all CTAs)
     AfScal *scal;
     double4 *stat_part;  // [kStatBlocks] partial sums of the grid statistics
     float *loss_out;     // last caller loss buffer

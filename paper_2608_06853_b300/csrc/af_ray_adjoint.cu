@@ -4,11 +4,11 @@
 // dL/ds_node = sum_{e,p} dL/dT[e][p] |q - r_p| / (N + 1) sum_k W_node(x_k)
 //            + w1 dR_TV/ds + w2 dR_SV/ds.
 // Each persistent CTA scatters its rays' bicubic weights into a private,
-// padded copy of the grid in shared memory (shared-memory atomics only), folds
-// the padding back onto the edge nodes and writes one partial grid; a second
-// kernel sums the partials in a fixed order and adds the regulariser gradient.
-// The padded row pitch is odd, so consecutive grid rows start in different
-// shared-memory banks.
+// padded copy of the grid in shared memory (shared-memory atomics only) and
+// adds it, block by block, into one padded integer grid in global memory; a
+// second kernel folds the padding back onto the edge nodes and adds the
+// regulariser gradient.  The padded row pitch is odd, so consecutive grid rows
+// start in different shared-memory banks.
 #include <math.h>
 
 #include "af_internal.cuh"
@@ -40,10 +40,10 @@ namespace {
 // faster than float ones); one ray adds at most max|dL/dT| (5 cell diagonals +
 // L/(N+1)) to a node and fix_scale is set on the host so that kRayFlushRays
 // rays stay below 2^30, so after whole blocks of at most kRayItemsPerFlush items
-// the integer grids are added into the CTA's int64 accumulator in global memory
-// and cleared.  All
-// sums are integer sums up to the final conversion, so the result does not
-// depend on which CTA took which block.  Rounding adds 1.5 * 2^23 in the last
+// the integer grids are added into the int64 padded grid in global memory, by
+// integer atomic adds no thread waits for, and cleared.  All sums are integer
+// sums up to the final conversion, so the result depends neither on which CTA
+// took which block nor on the order of the adds.  Rounding adds 1.5 * 2^23 in the last
 // FMA of a value (|value| < 2^22), so each partial sum is rounded to an integer.
 struct RayGrid {
     int width, rows;        // padded grid: nx + 4 columns, nz + 4 rows
@@ -114,8 +114,7 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
                                                                  const float *__restrict__ phi,
                                                                  const float *__restrict__ gdel,
                                                                  AfScal *__restrict__ scal,
-                                                                 long long *__restrict__ gpad,
-                                                                 long long *__restrict__ gpart)
+                                                                 long long *__restrict__ gpad)
 {
     constexpr int T = WARPS * 32;                    // threads = items per block
     constexpr int kQueue = 96;                       // < 32 carried + 2 x 32 new
@@ -126,11 +125,9 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
     __shared__ int fq[WARPS][kQueue];                // queued points
     __shared__ int wcount[WARPS];
     __shared__ long s_blk;
-    const int P = g.pitch, npad = P * rg.rows;
+    const int P = g.pitch;
     const int nacc = DUAL ? rg.base_b + rg.pb * rg.rows : rg.pa * rg.rows;
     for (int k = threadIdx.x; k < nacc; k += T) acci[k] = 0;
-    long long *mypad = gpad + (long)blockIdx.x * npad;
-    for (int k = threadIdx.x; k < npad; k += T) mypad[k] = 0;
     const float gmax = __int_as_float(scal->gmax_bits);
     const float S = gmax > 0.0f ? g.fix_scale / gmax : 0.0f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -302,25 +299,12 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
                     v += acci[rg.base_b + j * rg.pb + i];
                     acci[rg.base_b + j * rg.pb + i] = 0;
                 }
-                // the CTA's own accumulator: an uncontended integer add the thread does
-                // not wait for (an exact sum in any order)
-                if (v != 0) atomicAdd(reinterpret_cast<unsigned long long *>(mypad + j * P + i),
+                // an integer add the thread does not wait for (exact in any order)
+                if (v != 0) atomicAdd(reinterpret_cast<unsigned long long *>(gpad + j * P + i),
                                       (unsigned long long)(long long)v);
             }
             __syncthreads();
         }
-    }
-    __syncthreads();
-    // fold the padding onto the clamped edge nodes and write this CTA's partial grid
-    long long *out = gpart + (long)blockIdx.x * g.ng;
-    for (int q = threadIdx.x; q < g.ng; q += T) {
-        const int j = q / g.nx, i = q - j * g.nx;
-        const int ilo = i == 0 ? 0 : i + 2, ihi = i == g.nx - 1 ? g.nx + 3 : i + 2;
-        const int jlo = j == 0 ? 0 : j + 2, jhi = j == g.nz - 1 ? g.nz + 3 : j + 2;
-        long long v = 0;
-        for (int jj = jlo; jj <= jhi; ++jj)
-            for (int ii = ilo; ii <= ihi; ++ii) v += mypad[jj * P + ii];
-        out[q] = v;
     }
 }
 
@@ -329,29 +313,28 @@ __device__ __forceinline__ float dz_sign(float x, float k)      // D_k'(x)
     return fabsf(x) <= k ? 0.0f : (x > 0.0f ? 1.0f : -1.0f);
 }
 
-// grad[k] = sum_c gpart[c][k] / S + d(w1 R_TV + w2 R_SV)/ds_k  (gather form on
+// grad[k] = (folded integer grid)[k] / S + d(w1 R_TV + w2 R_SV)/ds_k  (gather form on
 // c = 1 / (c_unit s), the speed in the units of Eq. 10-11);
 // also returns the ray adjoint's block counter to zero for its next launch
 __global__ void __launch_bounds__(256) reduce_grad_kernel(AfGeom g, const float *__restrict__ s,
-                                                          const long long *__restrict__ gpart, int nparts,
+                                                          const long long *__restrict__ gpad, int have_rays,
                                                           AfScal *scal, float *__restrict__ grad)
 {
-    // 64 nodes x 4 slices of the partials per CTA; the slices are added in a fixed order
-    __shared__ long long s_part[4][64];
-    const int k = blockIdx.x * 64 + (threadIdx.x & 63), slice = threadIdx.x >> 6;
-    if (k == 0 && slice == 0) scal->ray_next = 0;
-    long long part = 0;
-    if (k < g.ng) {
-#pragma unroll 8
-        for (int c = slice; c < nparts; c += 4) part += gpart[(long)c * g.ng + k];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) scal->ray_next = 0;
+    if (k >= g.ng) return;
+    const int j = k / g.nx, i = k - j * g.nx, nx = g.nx, nz = g.nz;
+    // fold the padding of the integer grid onto the clamped edge nodes
+    long long tot = 0;
+    if (have_rays) {
+        const int P = g.pitch;
+        const int ilo = i == 0 ? 0 : i + 2, ihi = i == nx - 1 ? nx + 3 : i + 2;
+        const int jlo = j == 0 ? 0 : j + 2, jhi = j == nz - 1 ? nz + 3 : j + 2;
+        for (int jj = jlo; jj <= jhi; ++jj)
+            for (int ii = ilo; ii <= ihi; ++ii) tot += gpad[jj * P + ii];
     }
-    s_part[slice][threadIdx.x & 63] = part;
-    __syncthreads();
-    if (slice != 0 || k >= g.ng) return;
-    const long long tot = s_part[0][threadIdx.x] + s_part[1][threadIdx.x] + s_part[2][threadIdx.x] + s_part[3][threadIdx.x];
     const float gmax = __int_as_float(scal->gmax_bits);
     const float acc = gmax > 0.0f ? (float)((double)tot * ((double)gmax / (double)g.fix_scale)) : 0.0f;
-    const int j = k / g.nx, i = k - j * g.nx, nx = g.nx, nz = g.nz;
     auto C = [&](int ii, int jj) { return g.inv_c_unit / s[jj * nx + ii]; };
     const float hx = g.hx_mm, hz = g.hz_mm, hx2 = hx * hx, hz2 = hz * hz;
     float dc = 0.0f;   // dR/dc_k
@@ -471,25 +454,28 @@ RayAdjShape rayadj_shape(int nx, int nz, int pitch, int sm_count)
 
 cudaError_t launch_ray_adjoint(af_plan_t pl, const float *s, float *grad)
 {
-    int nparts = 0;
+    int have_rays = 0;
     if ((long)pl->g.ne * pl->g.npix > 0) {
         const RayAdjShape &sh = pl->rayadj;
         const RayGrid rg = ray_grid_layout(pl->g.nx, pl->g.nz, sh.dual, pl->g.pitch);
+        cudaError_t ez = cudaMemsetAsync(pl->gpad, 0, (size_t)pl->g.pitch * (pl->g.nz + 4) * sizeof(long long),
+                                         pl->stream);
+        if (ez != cudaSuccess) return ez;
         if (sh.dual && sh.threads == 768)
             ray_adjoint_kernel<24, true><<<sh.blocks, 768, sh.smem, pl->stream>>>(
-                pl->g, rg, pl->elem, pl->pix, pl->phi, pl->gdel, pl->scal, pl->gpad, pl->gpart);
+                pl->g, rg, pl->elem, pl->pix, pl->phi, pl->gdel, pl->scal, pl->gpad);
         else if (sh.dual)
             ray_adjoint_kernel<16, true><<<sh.blocks, 512, sh.smem, pl->stream>>>(
-                pl->g, rg, pl->elem, pl->pix, pl->phi, pl->gdel, pl->scal, pl->gpad, pl->gpart);
+                pl->g, rg, pl->elem, pl->pix, pl->phi, pl->gdel, pl->scal, pl->gpad);
         else
             ray_adjoint_kernel<8, false><<<sh.blocks, 256, sh.smem, pl->stream>>>(
-                pl->g, rg, pl->elem, pl->pix, pl->phi, pl->gdel, pl->scal, pl->gpad, pl->gpart);
+                pl->g, rg, pl->elem, pl->pix, pl->phi, pl->gdel, pl->scal, pl->gpad);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        nparts = sh.blocks;
+        have_rays = 1;
     }
-    reduce_grad_kernel<<<(pl->g.ng + 63) / 64, 256, 0, pl->stream>>>(pl->g, s, pl->gpart, nparts, pl->scal,
-                                                                      grad);
+    reduce_grad_kernel<<<(pl->g.ng + 255) / 256, 256, 0, pl->stream>>>(pl->g, s, pl->gpad, have_rays, pl->scal,
+                                                                        grad);
     return cudaGetLastError();
 }
 
