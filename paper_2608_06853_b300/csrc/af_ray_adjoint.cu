@@ -19,7 +19,8 @@ namespace {
 // consecutive pixels (for a 9 x 9 patch, a third of one patch row); their
 // rays run side by side, so at one step k their points usually fall in the
 // same grid cell.  A CTA takes blocks of one item per thread from a device
-// counter (blocks differ in work because of the apodization), compacts the
+// counter (blocks differ in work because of the apodization; a block's inputs
+// are loaded while the block before it is scattered), compacts the
 // items with a non-zero dL/dT into a table, and spreads the flattened
 // (item, step) list over all its threads (lane = consecutive step along a
 // ray).  A thread sums, in registers, the 4 x 4 stencils of the item's points
@@ -141,6 +142,25 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
     __syncthreads();
     long blk = s_blk;
     int since_flush = 0;
+    // the raw inputs of a thread's item (dL/dT, exit angle or exit x, pixel) for the
+    // block it processes next, loaded while the current block is scattered
+    float rg_v[kRayGroup], rg_ph[kRayGroup];
+    float2 rg_px[kRayGroup];
+    auto load_raw = [&](long b) {
+        const long it = b * T + threadIdx.x;
+        const bool ok = b < nblk && it < nitems;
+        const int e = ok ? (int)(it / ngroups) : 0, grp = ok ? (int)(it - (long)e * ngroups) : 0;
+#pragma unroll
+        for (int m = 0; m < kRayGroup; ++m) {
+            const int p = grp * kRayGroup + m;
+            const bool on = ok && p < g.npix;
+            const long idx = (long)e * g.npix + p;
+            rg_v[m] = on ? gdel[idx] : 0.0f;
+            rg_ph[m] = on && g.lens_mode != AF_LENS_NONE ? phi[idx] : 0.0f;
+            rg_px[m] = on ? pix[p] : make_float2(0.0f, 0.0f);
+        }
+    };
+    load_raw(blk);
     while (blk < nblk) {
         const long item = blk * T + threadIdx.x;
         float c[kRayGroup];
@@ -152,22 +172,20 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
             rp[m] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         if (item < nitems) {
-            const int e = (int)(item / ngroups), grp = (int)(item - (long)e * ngroups);
+            const int e = (int)(item / ngroups);
 #pragma unroll
             for (int m = 0; m < kRayGroup; ++m) {
-                const int p = grp * kRayGroup + m;
-                const long idx = (long)e * g.npix + p;
-                const float gv = p < g.npix ? gdel[idx] : 0.0f;
+                const float gv = rg_v[m];
                 if (gv == 0.0f) continue;
-                const float2 px = pix[p];
+                const float2 px = rg_px[m];
                 float qx, qz;
                 if (g.lens_mode == AF_LENS_BENT_RAY) {
                     float sn, cs;
-                    sincosf(phi[idx], &sn, &cs);
+                    sincosf(rg_ph[m], &sn, &cs);
                     qx = fmaf(g.RL, sn, g.arc_cx);
                     qz = fmaf(g.RL, cs, g.arc_cz);
                 } else if (g.lens_mode == AF_LENS_PLANAR) {
-                    qx = phi[idx];          // exit x on the lens line
+                    qx = rg_ph[m];          // exit x on the lens line
                     qz = g.lens_z;
                 } else {
                     const float4 el = elem[e];
@@ -211,6 +229,7 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
         }
         if (threadIdx.x == 0) s_blk = atomicAdd(&scal->ray_next, 1);
         __syncthreads();
+        load_raw(s_blk);                             // the next block's inputs, in flight during the scatter
         const int npt_total = nlive * npts;
         int nq = 0;                                  // queued points of this warp (warp-uniform)
         // flat index q = r * npts + k of this lane, advanced by T per pass without division
