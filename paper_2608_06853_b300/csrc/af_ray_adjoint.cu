@@ -162,6 +162,9 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
     };
     load_raw(blk);
     while (blk < nblk) {
+        // the next block's index, claimed now and needed only after the table fill
+        long nxt = 0;
+        if (threadIdx.x == 0) nxt = atomicAdd(&scal->ray_next, 1);
         const long item = blk * T + threadIdx.x;
         float c[kRayGroup];
         float4 rp[kRayGroup];
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
             const bool right_down = rl.z * rl.w >= 0.0f;
             rayb[slot] = DUAL && !right_down ? 1 : 0;
         }
-        if (threadIdx.x == 0) s_blk = atomicAdd(&scal->ray_next, 1);
+        if (threadIdx.x == 0) s_blk = nxt;
         __syncthreads();
         load_raw(s_blk);                             // the next block's inputs, in flight during the scatter
         const int npt_total = nlive * npts;
