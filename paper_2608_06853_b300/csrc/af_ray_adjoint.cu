@@ -142,11 +142,11 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
     __syncthreads();
     long blk = s_blk;
     int since_flush = 0;
-    // the raw inputs of a thread's item (dL/dT, exit angle or exit x, pixel) for the
-    // block it processes next, loaded while the current block is scattered
-    float rg_v[kRayGroup], rg_ph[kRayGroup];
-    float2 rg_px[kRayGroup];
-    auto load_raw = [&](long b) {
+    // the inputs of this thread's item (dL/dT, exit angle or exit x, pixel), loaded
+    // one block ahead: the next block's are in flight while this one is scattered
+    float in_gv[kRayGroup], in_ph[kRayGroup];
+    float2 in_px[kRayGroup];
+    auto load_inputs = [&](long b) {
         const long it = b * T + threadIdx.x;
         const bool ok = b < nblk && it < nitems;
         const int e = ok ? (int)(it / ngroups) : 0, grp = ok ? (int)(it - (long)e * ngroups) : 0;
@@ -155,12 +155,12 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
             const int p = grp * kRayGroup + m;
             const bool on = ok && p < g.npix;
             const long idx = (long)e * g.npix + p;
-            rg_v[m] = on ? gdel[idx] : 0.0f;
-            rg_ph[m] = on && g.lens_mode != AF_LENS_NONE ? phi[idx] : 0.0f;
-            rg_px[m] = on ? pix[p] : make_float2(0.0f, 0.0f);
+            in_gv[m] = on ? gdel[idx] : 0.0f;
+            in_ph[m] = on && g.lens_mode != AF_LENS_NONE ? phi[idx] : 0.0f;
+            in_px[m] = on ? pix[p] : make_float2(0.0f, 0.0f);
         }
     };
-    load_raw(blk);
+    load_inputs(blk);
     while (blk < nblk) {
         // the next block's index, claimed now and needed only after the table fill
         long nxt = 0;
@@ -178,17 +178,17 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
             const int e = (int)(item / ngroups);
 #pragma unroll
             for (int m = 0; m < kRayGroup; ++m) {
-                const float gv = rg_v[m];
+                const float gv = in_gv[m];
                 if (gv == 0.0f) continue;
-                const float2 px = rg_px[m];
+                const float2 px = in_px[m];
                 float qx, qz;
                 if (g.lens_mode == AF_LENS_BENT_RAY) {
                     float sn, cs;
-                    sincosf(rg_ph[m], &sn, &cs);
+                    sincosf(in_ph[m], &sn, &cs);
                     qx = fmaf(g.RL, sn, g.arc_cx);
                     qz = fmaf(g.RL, cs, g.arc_cz);
                 } else if (g.lens_mode == AF_LENS_PLANAR) {
-                    qx = rg_ph[m];          // exit x on the lens line
+                    qx = in_ph[m];          // exit x on the lens line
                     qz = g.lens_z;
                 } else {
                     const float4 el = elem[e];
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
         }
         if (threadIdx.x == 0) s_blk = nxt;
         __syncthreads();
-        load_raw(s_blk);                             // the next block's inputs, in flight during the scatter
+        load_inputs(s_blk);                          // the next block's, in flight during the scatter
         const int npt_total = nlive * npts;
         int nq = 0;                                  // queued points of this warp (warp-uniform)
         // flat index q = r * npts + k of this lane, advanced by T per pass without division
