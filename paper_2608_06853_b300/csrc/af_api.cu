@@ -233,7 +233,7 @@ af_status af_workspace_bytes(const af_config *c, size_t *bytes)
     b += (size_t)c->n_patch * npair * (sizeof(float2) + 1);               // z, mask
     b += (size_t)c->n_patch * (sizeof(double) + sizeof(int));
     b += (size_t)(c->nx + 5) * (c->nz + 4) * sizeof(long long);            // ray-adjoint integer grid
-    b += sizeof(AfScal) + kStatBlocks * sizeof(double4);
+    b += sizeof(AfScal) + kStatBlocks * sizeof(StatPart);
     b += 4 * (size_t)AF_MLP_NPARAM * sizeof(float) + 2 * 128 * 128 * 2 + ne * npix;   // surrogate
     b += npix * 2 * sizeof(float2) + (size_t)c->n_patch * 5 * sizeof(double) + ng * sizeof(float);   // sweep
     *bytes = b;
@@ -453,7 +453,7 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
     AF_ALLOC(pl->patch_sum, g.n_patch * sizeof(double));
     AF_ALLOC(pl->patch_cnt, g.n_patch * sizeof(int));
     AF_ALLOC(pl->scal, sizeof(AfScal));
-    AF_ALLOC(pl->stat_part, kStatBlocks * sizeof(double4));
+    AF_ALLOC(pl->stat_part, kStatBlocks * sizeof(StatPart));
     pl->smem_grid = padded_grid_bytes(c);
     pl->delay = delays_shape(pl->smem_grid, pl->sm_count);
     pl->rayadj = rayadj_shape(c->nx, c->nz, g.pitch, pl->sm_count);

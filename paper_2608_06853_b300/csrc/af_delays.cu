@@ -18,7 +18,7 @@ __device__ __forceinline__ float deadzone(float x, float k) { return fmaxf(fabsf
 // write partial sums {sum 1/s, sum of the Eq. 10 terms, sum of the Eq. 11 terms,
 // bad-value flag}, and one CTA adds them in a fixed order.
 __global__ void __launch_bounds__(256) grid_stats_partial_kernel(AfGeom g, const float *__restrict__ s,
-                                                                 double4 *__restrict__ part)
+                                                                 StatPart *__restrict__ part)
 {
     __shared__ double red[3][8];
     // per-thread partial sums in float (float64 throughput is low on this GPU); the
@@ -55,21 +55,21 @@ __global__ void __launch_bounds__(256) grid_stats_partial_kernel(AfGeom g, const
     if (threadIdx.x == 0) {
         double c = 0.0, a = 0.0, b = 0.0;
         for (int k = 0; k < 8; ++k) { c += red[0][k]; a += red[1][k]; b += red[2][k]; }
-        part[blockIdx.x] = make_double4(c, a, b, bad ? 1.0 : 0.0);
+        part[blockIdx.x] = StatPart{c, a, b, bad ? 1.0 : 0.0};
     }
 }
 
 // one warp: lane l adds partials l, l + 32, ..., then a fixed xor tree
-__global__ void __launch_bounds__(32) grid_stats_final_kernel(AfGeom g, const double4 *__restrict__ part,
+__global__ void __launch_bounds__(32) grid_stats_final_kernel(AfGeom g, const StatPart *__restrict__ part,
                                                               int nparts, AfScal *scal)
 {
     double c = 0.0, a = 0.0, b = 0.0, bad = 0.0;
     for (int k = threadIdx.x; k < nparts; k += 32) {
-        const double4 v = part[k];
-        c += v.x;
-        a += v.y;
-        b += v.z;
-        bad += v.w;
+        const StatPart v = part[k];
+        c += v.c;
+        a += v.a;
+        b += v.b;
+        bad += v.bad;
     }
     for (int o = 16; o > 0; o >>= 1) {
         c += __shfl_xor_sync(0xffffffffu, c, o);

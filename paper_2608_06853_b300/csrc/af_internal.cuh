@@ -38,6 +38,10 @@ struct AfGeom {
 };
 
 constexpr int kStatBlocks = 64;     // CTAs of the grid-statistics partial sums
+// partial sums of one grid-statistics CTA: {sum 1/s, Eq. 10 terms, Eq. 11 terms, bad-value flag}
+struct alignas(32) StatPart {
+    double c, a, b, bad;
+};
 constexpr int kTimingCap = 4096;   // recorded stage launches per timing window
 constexpr size_t kMaxGridSmemBytes = 200 * 1024;   // largest padded slowness grid held in shared memory
 
@@ -124,7 +128,7 @@ struct af_plan_s {
     float *gdel;         // [ne][npix] dL/dT
     long long *gpad;     // [padded grid] fixed-point accumulator of the ray adjoint (all CTAs)
     AfScal *scal;
-    double4 *stat_part;  // [kStatBlocks] partial sums of the grid statistics
+    StatPart *stat_part; // [kStatBlocks] partial sums of the grid statistics
     float *loss_out;     // last caller loss buffer
     const void *iq;      // last forward's inputs (kept for the adjoint)
     const float *iq_scale;
