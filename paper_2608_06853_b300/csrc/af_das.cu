@@ -33,18 +33,16 @@ template <> struct Sample<AF_IQ_F16> {
 // slot on sooner (0.30 ms against 0.33 ms with 8-warp CTAs, 128 elements).
 constexpr int kAdjWarps = 4;
 
-// Forward launch per sample type: warps per CTA, CTAs per SM and transmit-loop
-// unroll, measured on the 128-element workload (forward ms; 8-warp CTAs unless
-// stated):
-//   complex64: 2 CTAs, unroll 2: 0.64; 3 CTAs, unroll 2: 0.70; 4 CTAs, none: 0.61;
-//              4-warp CTAs, 8 per SM, none: 0.59
-//   bf16:      2 CTAs, unroll 2: 0.65; 3 CTAs, none: 0.52;     4 CTAs, none: 0.93;
-//              4-warp CTAs, 6 per SM, none: 0.50
-//   f16:       2 CTAs, unroll 2: 0.64; 3 CTAs, none: 0.65;     4 CTAs, none: 1.06;
-//              4-warp CTAs, 4 per SM, unroll 2: 0.55
-template <int DT> struct FwdLaunch { static constexpr int kWarps = 4, kMinBlocks = 4, kUnroll = 2; };
-template <> struct FwdLaunch<AF_IQ_C64> { static constexpr int kWarps = 4, kMinBlocks = 8, kUnroll = 1; };
-template <> struct FwdLaunch<AF_IQ_BF16> { static constexpr int kWarps = 4, kMinBlocks = 6, kUnroll = 1; };
+// Forward launch: warps per CTA, CTAs per SM and transmit-loop unroll, the same
+// for every sample type.  Measured on the 128-element workload (forward ms):
+//   complex64: 8-warp CTAs, 2 per SM, unroll 2: 0.64; 4 per SM, none: 0.61;
+//              4-warp CTAs, 8 per SM, none: 0.59; 7 per SM: 0.98; 6 per SM: 0.66
+//   bf16:      4-warp CTAs, 6 per SM, none: 0.61; 7 per SM: 0.80; 8 per SM: 0.54
+//   f16:       4-warp CTAs, 4 per SM, unroll 2: 0.55; 8 per SM, unroll 2: 0.90;
+//              8 per SM, none: 0.51
+// At 8 CTAs per SM (64 registers) the compiler spills a few bytes; every
+// shape that fits without spilling runs slower.
+template <int DT> struct FwdLaunch { static constexpr int kWarps = 4, kMinBlocks = 8, kUnroll = 1; };
 
 // Gather of one transmit for the W receivers held by a lane: all 2W loads are
 // issued before any is used, so a warp keeps 2W loads in flight.  CHECK: the
