@@ -200,7 +200,7 @@ def run_reference(args, rank, world):
 # the capture (see profiles/).  The adjoint stages' traffic follows
 # the CMPE mask of the captured iteration.
 NCU_TRAFFIC = {"das_forward": 618.1e6 + 85.5e6, "das_adjoint": 281.1e6 + 18.1e6,
-               "ray_adjoint": 33.57e6 + 0.0, "delays": 15.9e6 + 23.5e6}
+               "ray_adjoint": 33.57e6 + 0.0, "delays": 16.20e6 + 24.89e6}
 
 # algorithmic FP32 lane-operations per unit, from the arithmetic of the method.
 # Ray point: position (2) + cell and fraction (4) + two Keys weight sets (2 x 10) + 16
