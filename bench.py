@@ -199,7 +199,7 @@ def run_reference(args, rank, world):
 # each kernel, one kernel per capture), per kernel; None once the kernel changed after
 # the capture (see profiles/).  The adjoint stages' traffic follows
 # the CMPE mask of the captured iteration.
-NCU_TRAFFIC = {"das_forward": 618.1e6 + 85.5e6, "das_adjoint": 281.1e6 + 18.1e6,
+NCU_TRAFFIC = {"das_forward": 618.1e6 + 85.5e6, "das_adjoint": 282.58e6 + 18.45e6,
                "ray_adjoint": 33.57e6 + 0.0, "delays": 16.20e6 + 24.89e6}
 
 # algorithmic FP32 lane-operations per unit, from the arithmetic of the method.

@@ -28,10 +28,14 @@ template <> struct Sample<AF_IQ_F16> {
     static __device__ __forceinline__ float2 load(const T *p) { return __half22float2(__ldg(p)); }
 };
 
-// The adjoint's CTAs hold 4 warps (4 CTAs per SM): a warp whose transmit blocks
-// all have a zero image gradient finishes at once, and a small CTA hands its
-// slot on sooner (0.30 ms against 0.33 ms with 8-warp CTAs, 128 elements).
+// The adjoint's CTAs hold 4 warps: a warp whose transmit blocks all have a zero
+// image gradient finishes at once, and a small CTA hands its slot on sooner
+// (0.30 ms against 0.33 ms with 8-warp CTAs, 128 elements).  Five CTAs per SM
+// (96 registers, no spill) against four (128 registers): 0.397 against 0.400 ms
+// for complex64, 0.378 against 0.410 for bf16, 0.364 against 0.406 for f16;
+// six or eight per SM spill and run slower (0.415, 0.421 ms for complex64).
 constexpr int kAdjWarps = 4;
+constexpr int kAdjMinBlocks = 5;
 
 // Forward launch: warps per CTA, CTAs per SM and transmit-loop unroll, the same
 // for every sample type.  Measured on the 128-element workload (forward ms):
@@ -276,7 +280,7 @@ __device__ __forceinline__ void das_adjoint_blocks(const AfGeom &g, const typena
 }
 
 template <int W, int DT>
-__global__ void __launch_bounds__(32 * kAdjWarps, 4) das_adjoint_kernel(AfGeom g, const void *__restrict__ iq,
+__global__ void __launch_bounds__(32 * kAdjWarps, kAdjMinBlocks) das_adjoint_kernel(AfGeom g, const void *__restrict__ iq,
                                                              const float *__restrict__ scale,
                                                              const float4 *__restrict__ D,
                                                              const int2 *__restrict__ nrange,
