@@ -320,9 +320,17 @@ __global__ void __launch_bounds__(32 * kAdjWarps, kAdjMinBlocks) das_adjoint_ker
 __global__ void __launch_bounds__(256) gdel_max_kernel(const float *__restrict__ gdel, long n,
                                                        int *__restrict__ gmax_bits)
 {
+    // float4 loads (the table is a device allocation, so 16-byte aligned), then the
+    // tail; a maximum does not depend on the order
     float amax = 0.0f;
-    for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x)
-        amax = fmaxf(amax, fabsf(gdel[k]));
+    const long n4 = n >> 2, stride = (long)gridDim.x * blockDim.x, first = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const float4 *__restrict__ g4 = reinterpret_cast<const float4 *>(gdel);
+#pragma unroll 4
+    for (long k = first; k < n4; k += stride) {
+        const float4 v = g4[k];
+        amax = fmaxf(fmaxf(amax, fabsf(v.x)), fmaxf(fmaxf(fabsf(v.y), fabsf(v.z)), fabsf(v.w)));
+    }
+    for (long k = (n4 << 2) + first; k < n; k += stride) amax = fmaxf(amax, fabsf(gdel[k]));
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     if ((threadIdx.x & 31) == 0 && amax > 0.0f) atomicMax(gmax_bits, __float_as_int(amax));
 }
