@@ -25,14 +25,56 @@ using cmpe::pair_index;
 // workload, where 16-warp CTAs of all 400 patches are resident at once)
 constexpr int kCmpeWarps = 16;
 
+// fixed-order sums over patches (256 strided partial sums, then a halving tree);
+// loss = {L, L_CMPE, R_TV, R_SV}.  Called by every thread of a block of at least
+// 256 threads; the partials are read from L2, where other CTAs wrote them.
+__device__ void cmpe_fold(const AfGeom &g, const double *patch_sum, const int *patch_cnt, AfScal *scal,
+                          float *loss)
+{
+    __shared__ double s_a[256];
+    __shared__ int s_c[256];
+    const int t = threadIdx.x;
+    if (t < 256) {
+        double a = 0.0;
+        int c = 0;
+        for (int P = t; P < g.n_patch; P += 256) { a += __ldcg(patch_sum + P); c += __ldcg(patch_cnt + P); }
+        s_a[t] = a;
+        s_c[t] = c;
+    }
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (t < o) { s_a[t] += s_a[t + o]; s_c[t] += s_c[t + o]; }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const int M = s_c[0];
+        const double lc = s_a[0] / (M > 1 ? M : 1);
+        scal->cmpe_sum = s_a[0];
+        scal->lcmpe = (float)lc;
+        scal->n_active = M;
+        scal->inv_m = (float)(1.0 / (M > 1 ? M : 1));
+        scal->cmpe_done = 0;
+        if (loss) {
+            loss[0] = (float)(lc + (double)g.w1 * scal->rtv + (double)g.w2 * scal->rsv);
+            loss[1] = (float)lc;
+            loss[2] = scal->rtv;
+            loss[3] = scal->rsv;
+        }
+    }
+}
+
+// The CTA that finishes last (counted in scal->cmpe_done, which it sets back to
+// zero) folds all patches' sums, so the loss needs no second launch.
 __global__ void __launch_bounds__(32 * kCmpeWarps) cmpe_forward_kernel(AfGeom g, const float2 *__restrict__ B,
                                                            float2 *__restrict__ z,
                                                            uint8_t *__restrict__ mask,
                                                            double *__restrict__ patch_sum,
-                                                           int *__restrict__ patch_cnt)
+                                                           int *__restrict__ patch_cnt, AfScal *scal,
+                                                           float *__restrict__ loss)
 {
     __shared__ double s_sum[kCmpeWarps];
     __shared__ int s_cnt[kCmpeWarps];
+    __shared__ int s_last;
     const int P = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int base = P * g.patch_npix;
     double lsum = 0.0;
@@ -58,40 +100,20 @@ __global__ void __launch_bounds__(32 * kCmpeWarps) cmpe_forward_kernel(AfGeom g,
         for (int k = 0; k < kCmpeWarps; ++k) { a += s_sum[k]; c += s_cnt[k]; }
         patch_sum[P] = a;
         patch_cnt[P] = c;
+        __threadfence();                               // the sums are visible before the count
+        s_last = atomicAdd(&scal->cmpe_done, 1u) == gridDim.x - 1;
+        __threadfence();
     }
+    __syncthreads();
+    if (s_last) cmpe_fold(g, patch_sum, patch_cnt, scal, loss);
 }
 
-// fixed-order sums over patches; loss = {L, L_CMPE, R_TV, R_SV}
+// the fold alone, for plans without CMPE terms (L_CMPE = 0)
 __global__ void __launch_bounds__(256) cmpe_finalize_kernel(AfGeom g, const double *__restrict__ patch_sum,
                                                             const int *__restrict__ patch_cnt,
                                                             AfScal *scal, float *__restrict__ loss)
 {
-    __shared__ double s_a[256];
-    __shared__ int s_c[256];
-    double a = 0.0;
-    int c = 0;
-    for (int P = threadIdx.x; P < g.n_patch; P += 256) { a += patch_sum[P]; c += patch_cnt[P]; }
-    s_a[threadIdx.x] = a;
-    s_c[threadIdx.x] = c;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) { s_a[threadIdx.x] += s_a[threadIdx.x + o]; s_c[threadIdx.x] += s_c[threadIdx.x + o]; }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const int M = s_c[0];
-        const double lc = s_a[0] / (M > 1 ? M : 1);
-        scal->cmpe_sum = s_a[0];
-        scal->lcmpe = (float)lc;
-        scal->n_active = M;
-        scal->inv_m = (float)(1.0 / (M > 1 ? M : 1));
-        if (loss) {
-            loss[0] = (float)(lc + (double)g.w1 * scal->rtv + (double)g.w2 * scal->rsv);
-            loss[1] = (float)lc;
-            loss[2] = scal->rtv;
-            loss[3] = scal->rsv;
-        }
-    }
+    cmpe_fold(g, patch_sum, patch_cnt, scal, loss);
 }
 
 // {sum m |arg z|, M} of the last forward, for callers that add them over plans
@@ -103,8 +125,8 @@ __global__ void cmpe_totals_kernel(const AfScal *__restrict__ scal, double *__re
 
 // Replaces the plan's CMPE normalisation by totals added over several plans (a
 // patch-sharded run): L_CMPE = sum / max(1, M) of the whole problem, which the
-// adjoint then differentiates; the loss vector is rewritten the way the finalize
-// kernel writes it (the regularisers are this plan's own).
+// adjoint then differentiates; the loss vector is rewritten the way the patch
+// fold writes it (the regularisers are this plan's own).
 __global__ void cmpe_set_totals_kernel(AfGeom g, const double *__restrict__ in, AfScal *scal,
                                        float *__restrict__ loss)
 {
@@ -182,12 +204,11 @@ cudaError_t launch_cmpe_forward(af_plan_t pl, float *loss)
 {
     if (pl->g.n_patch > 0 && pl->g.npair > 0) {
         cmpe_forward_kernel<<<pl->g.n_patch, 32 * kCmpeWarps, 0, pl->stream>>>(pl->g, pl->B, pl->z, pl->mask,
-                                                                  pl->patch_sum, pl->patch_cnt);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+                                                                  pl->patch_sum, pl->patch_cnt, pl->scal, loss);
+        return cudaGetLastError();
     }
     AfGeom g = pl->g;
-    if (g.npair == 0) g.n_patch = 0;     // no terms: L_CMPE = 0
+    g.n_patch = 0;                       // no terms: L_CMPE = 0
     cmpe_finalize_kernel<<<1, 256, 0, pl->stream>>>(g, pl->patch_sum, pl->patch_cnt, pl->scal, loss);
     return cudaGetLastError();
 }

@@ -16,11 +16,44 @@ __device__ __forceinline__ float deadzone(float x, float k) { return fmaxf(fabsf
 // c_med = mean(1/s) (Sec. III-A), the two regularisers of Eq. 10-11 on
 // c = 1 / (c_unit s) (the speed in km/s, positions in mm), and the numeric check of the slowness map, in two steps: kStatBlocks CTAs
 // write partial sums {sum 1/s, sum of the Eq. 10 terms, sum of the Eq. 11 terms,
-// bad-value flag}, and one CTA adds them in a fixed order.
-__global__ void __launch_bounds__(256) grid_stats_partial_kernel(AfGeom g, const float *__restrict__ s,
-                                                                 StatPart *__restrict__ part)
+// bad-value flag}, and the CTA that finishes last adds them in a fixed order.
+// one warp: lane l adds partials l, l + 32, ..., then a fixed xor tree; the
+// partials are read from L2, where other CTAs wrote them
+__device__ __forceinline__ void grid_stats_fold(const AfGeom &g, const StatPart *part, int nparts, AfScal *scal)
+{
+    double c = 0.0, a = 0.0, b = 0.0, bad = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += 32) {
+        const double2 ca = __ldcg(reinterpret_cast<const double2 *>(part + k));
+        const double2 bb = __ldcg(reinterpret_cast<const double2 *>(part + k) + 1);
+        c += ca.x;
+        a += ca.y;
+        b += bb.x;
+        bad += bb.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if (threadIdx.x != 0) return;
+    const double cmed = c / g.ng;
+    scal->sbar = (float)(1.0 / cmed);
+    scal->rtv = (float)(a * g.na_inv);
+    scal->rsv = (float)(b * g.nb_inv);
+    scal->fp64_solves = 0;
+    scal->n_apod = 0;
+    scal->stat_done = 0;
+    if (bad > 0.0) scal->numeric_flag = 1;
+}
+
+// The CTA that finishes last (counted in scal->stat_done, which the fold sets
+// back to zero) folds the gridDim.x partials with its first warp.
+__global__ void __launch_bounds__(256, 4) grid_stats_partial_kernel(AfGeom g, const float *__restrict__ s,
+                                                                 StatPart *__restrict__ part, AfScal *scal)
 {
     __shared__ double red[3][8];
+    __shared__ int s_last;
     // per-thread partial sums in float (float64 throughput is low on this GPU); the
     // sum of 1/s, which sets c_med and with it every delay, is compensated (Kahan)
     float pc = 0.0f, pc_comp = 0.0f, pa = 0.0f, pb = 0.0f;
@@ -56,35 +89,12 @@ __global__ void __launch_bounds__(256) grid_stats_partial_kernel(AfGeom g, const
         double c = 0.0, a = 0.0, b = 0.0;
         for (int k = 0; k < 8; ++k) { c += red[0][k]; a += red[1][k]; b += red[2][k]; }
         part[blockIdx.x] = StatPart{c, a, b, bad ? 1.0 : 0.0};
+        __threadfence();                               // the partial is visible before the count
+        s_last = atomicAdd(&scal->stat_done, 1u) == gridDim.x - 1;
+        __threadfence();
     }
-}
-
-// one warp: lane l adds partials l, l + 32, ..., then a fixed xor tree
-__global__ void __launch_bounds__(32) grid_stats_final_kernel(AfGeom g, const StatPart *__restrict__ part,
-                                                              int nparts, AfScal *scal)
-{
-    double c = 0.0, a = 0.0, b = 0.0, bad = 0.0;
-    for (int k = threadIdx.x; k < nparts; k += 32) {
-        const StatPart v = part[k];
-        c += v.c;
-        a += v.a;
-        b += v.b;
-        bad += v.bad;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        c += __shfl_xor_sync(0xffffffffu, c, o);
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-        bad += __shfl_xor_sync(0xffffffffu, bad, o);
-    }
-    if (threadIdx.x != 0) return;
-    const double cmed = c / g.ng;
-    scal->sbar = (float)(1.0 / cmed);
-    scal->rtv = (float)(a * g.na_inv);
-    scal->rsv = (float)(b * g.nb_inv);
-    scal->fp64_solves = 0;
-    scal->n_apod = 0;
-    if (bad > 0.0) scal->numeric_flag = 1;
+    __syncthreads();
+    if (s_last && threadIdx.x < 32) grid_stats_fold(g, part, gridDim.x, scal);
 }
 
 // Padded grid in shared memory: scalar v[jj][ii], or (PAIRS) the node pairs
@@ -383,10 +393,7 @@ DelayShape delays_shape(size_t smem_scalar, int sm_count)
 
 cudaError_t launch_grid_stats(af_plan_t pl, const float *s)
 {
-    grid_stats_partial_kernel<<<kStatBlocks, 256, 0, pl->stream>>>(pl->g, s, pl->stat_part);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    grid_stats_final_kernel<<<1, 32, 0, pl->stream>>>(pl->g, pl->stat_part, kStatBlocks, pl->scal);
+    grid_stats_partial_kernel<<<kStatBlocks, 256, 0, pl->stream>>>(pl->g, s, pl->stat_part, pl->scal);
     return cudaGetLastError();
 }
 

@@ -92,6 +92,8 @@ struct AfScal {
     int gmax_bits;       // max |dL/dT| of the last adjoint (float bits, >= 0)
     int mlp_err;         // a tensor-core completion wait of the MLP timed out
     int ray_next;        // next item block of the ray adjoint (zero between launches)
+    unsigned stat_done;  // CTAs of the grid statistics done (zero between launches)
+    unsigned cmpe_done;  // CTAs of the CMPE forward done (zero between launches)
 };
 
 struct AfJobs;          // jobs from host memory (af_job_*): staging buffers, copy stream, events
