@@ -48,6 +48,16 @@ constexpr int kAdjMinBlocks = 5;
 // shape that fits without spilling runs slower.
 template <int DT> struct FwdLaunch { static constexpr int kWarps = 4, kMinBlocks = 8, kUnroll = 1; };
 
+// Each (pixel tile, receive block) is split into pieces of consecutive transmit
+// blocks, one CTA per piece; grid.y = piece * nsub + j, so all CTAs of one piece
+// are issued before the next piece's.  Whole tiles made CTAs of ~150 us that ran
+// in 3.4 waves of 1184 resident CTAs; the last wave left SMs part-empty for
+// ~150 us.  Shorter CTAs shorten that tail, and more CTAs cost more issue
+// overhead (128 elements, ms): forward 0.590 whole, 0.534 in 2 pieces, 0.523 in
+// 4, 0.538 in 8; adjoint 0.395, 0.367, 0.386, 0.441.  Pieces are independent:
+// each writes its own B_ij, and the adjoint adds into dL/dT atomically anyway.
+constexpr int kFwdSplit = 4, kAdjSplit = 2;
+
 // Gather of one transmit for the W receivers held by a lane: all 2W loads are
 // issued before any is used, so a warp keeps 2W loads in flight.  CHECK: the
 // indices are clamped into the trace and out-of-range samples get weight 0;
@@ -140,16 +150,16 @@ __device__ __forceinline__ float2 das_transmit(const typename S::T *__restrict__
     return make_float2(sr, si);
 }
 
-// B_ij(p) for every transmit block i of one lane (receive block j)
+// B_ij(p) for the transmit blocks i0 <= i < i1 of one lane (receive block j)
 template <int W, int DT, bool CHECK>
 __device__ __forceinline__ void das_forward_blocks(const AfGeom &g, const typename Sample<DT>::T *__restrict__ psi,
                                                    const float *__restrict__ scale, const float4 *__restrict__ D,
                                                    float2 *__restrict__ B, int j, int p, const int (&nr)[W],
-                                                   const float (&fr)[W], const float2 (&pr)[W])
+                                                   const float (&fr)[W], const float2 (&pr)[W], int i0, int i1)
 {
     using S = Sample<DT>;
-    float4 dnext = D[p];
-    for (int i = 0; i < g.nsub; ++i) {
+    float4 dnext = D[(long)i0 * W * g.npix + p];
+    for (int i = i0; i < i1; ++i) {
         float ar = 0.0f, ai = 0.0f;
 #pragma unroll(FwdLaunch<DT>::kUnroll)
         for (int tt = 0; tt < W; ++tt) {
@@ -169,10 +179,11 @@ __device__ __forceinline__ void das_forward_blocks(const AfGeom &g, const typena
     }
 }
 
-// Forward: CTA = 4 or 8 warps on as many neighbouring tiles of 32 pixels (128 or
-// 256 consecutive pixels, one to three laterally adjacent patches), all with
-// the same receive block j = blockIdx.y.  The warps walk the transmits in the
-// same order, so the trace windows one warp pulls into L1 serve the others.
+// Forward: CTA = 4 warps on as many neighbouring tiles of 32 pixels (128
+// consecutive pixels, one or two laterally adjacent patches), all with the same
+// receive block j and the same piece of transmit blocks (blockIdx.y).  The warps
+// walk the transmits in the same order, so the trace windows one warp pulls into
+// L1 serve the others.
 // The gathers are latency bound; the CTA size, the CTAs per SM and the unroll
 // of the transmit loop are chosen per sample type (FwdLaunch).
 // A warp whose receive block is outside the aperture for all its pixels only
@@ -188,7 +199,8 @@ __global__ void __launch_bounds__(32 * FwdLaunch<DT>::kWarps, FwdLaunch<DT>::kMi
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int p = (blockIdx.x * FwdLaunch<DT>::kWarps + warp) * 32 + lane;
-    const int j = blockIdx.y;
+    const int j = blockIdx.y % g.nsub, piece = blockIdx.y / g.nsub;
+    const int i0 = piece * g.nsub / kFwdSplit, i1 = (piece + 1) * g.nsub / kFwdSplit;   // transmit blocks
     if (p >= g.npix) return;
     const typename Sample<DT>::T *psi = reinterpret_cast<const typename Sample<DT>::T *>(iq);
     int nr[W];
@@ -197,21 +209,21 @@ __global__ void __launch_bounds__(32 * FwdLaunch<DT>::kWarps, FwdLaunch<DT>::kMi
     const bool live = receive_side<W>(D, g.npix, j, p, nr, fr, pr) != 0u;
     const unsigned act = __activemask();
     if (!__any_sync(act, live)) {
-        for (int i = 0; i < g.nsub; ++i) B[(long)(i * g.nsub + j) * g.npix + p] = make_float2(0.0f, 0.0f);
+        for (int i = i0; i < i1; ++i) B[(long)(i * g.nsub + j) * g.npix + p] = make_float2(0.0f, 0.0f);
         return;
     }
     if (__all_sync(act, pixel_in_trace(nrange[p], g.ns)))
-        das_forward_blocks<W, DT, false>(g, psi, scale, D, B, j, p, nr, fr, pr);
+        das_forward_blocks<W, DT, false>(g, psi, scale, D, B, j, p, nr, fr, pr, i0, i1);
     else
-        das_forward_blocks<W, DT, true>(g, psi, scale, D, B, j, p, nr, fr, pr);
+        das_forward_blocks<W, DT, true>(g, psi, scale, D, B, j, p, nr, fr, pr, i0, i1);
 }
 
-// Adjoint: CTAs of kAdjWarps neighbouring pixel tiles with one receive block
-// j = blockIdx.y.  For one gather dL/dtau =
+// Adjoint: CTAs of kAdjWarps neighbouring pixel tiles with one receive block j
+// and one piece of transmit blocks (blockIdx.y).  For one gather dL/dtau =
 // Re(conj(G) exp(j 2 pi fd tau) (fs dPsi/du + j 2 pi fd Psi(u))); it is added to
 // dL/dT_t and dL/dT_r.  A lane sums the transmit role over its block's W
-// receivers and the receive role over all transmits, then adds both into the
-// zeroed dL/dT table with coalesced atomic adds (one per transmit and one per
+// receivers and the receive role over the piece's transmits, then adds both into
+// the zeroed dL/dT table with coalesced atomic adds (one per transmit and one per
 // live receiver of the block).
 template <int W, typename S, bool CHECK>
 __device__ __forceinline__ float adj_transmit(const AfGeom &g, const typename S::T *__restrict__ base, int nt,
@@ -245,11 +257,11 @@ __device__ __forceinline__ void das_adjoint_blocks(const AfGeom &g, const typena
                                                    const uint8_t *__restrict__ mask, float inv_m,
                                                    float *__restrict__ gdel, int j,
                                                    int p, bool live, const int (&nr)[W], const float (&fr)[W],
-                                                   const float2 (&pr)[W], float (&gr)[W])
+                                                   const float2 (&pr)[W], float (&gr)[W], int i0, int i1)
 {
     using S = Sample<DT>;
-    float4 dnext = D[p];
-    for (int i = 0; i < g.nsub; ++i) {
+    float4 dnext = D[(long)i0 * W * g.npix + p];
+    for (int i = i0; i < i1; ++i) {
         // dL/dB_ij(p), formed here from the images and the CMPE terms (never stored)
         const float2 Gv = cmpe::image_grad(B, z, mask, inv_m, g.nsub, g.npix, g.npair, p / g.patch_npix, i, j, p);
         // every term of transmit block i is weighted by conj(G_ij(p)): where the CMPE
@@ -292,7 +304,8 @@ __global__ void __launch_bounds__(32 * kAdjWarps, kAdjMinBlocks) das_adjoint_ker
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int p = (blockIdx.x * kAdjWarps + warp) * 32 + lane;
-    const int j = blockIdx.y;
+    const int j = blockIdx.y % g.nsub, piece = blockIdx.y / g.nsub;
+    const int i0 = piece * g.nsub / kAdjSplit, i1 = (piece + 1) * g.nsub / kAdjSplit;   // transmit blocks
     if (p >= g.npix) return;
     const typename Sample<DT>::T *psi = reinterpret_cast<const typename Sample<DT>::T *>(iq);
     int nr[W];
@@ -307,9 +320,9 @@ __global__ void __launch_bounds__(32 * kAdjWarps, kAdjMinBlocks) das_adjoint_ker
 #pragma unroll
     for (int k = 0; k < W; ++k) gr[k] = 0.0f;
     if (__all_sync(act, pixel_in_trace(nrange[p], g.ns)))
-        das_adjoint_blocks<W, DT, false>(g, psi, scale, D, B, z, mask, inv_m, gdel, j, p, live, nr, fr, pr, gr);
+        das_adjoint_blocks<W, DT, false>(g, psi, scale, D, B, z, mask, inv_m, gdel, j, p, live, nr, fr, pr, gr, i0, i1);
     else
-        das_adjoint_blocks<W, DT, true>(g, psi, scale, D, B, z, mask, inv_m, gdel, j, p, live, nr, fr, pr, gr);
+        das_adjoint_blocks<W, DT, true>(g, psi, scale, D, B, z, mask, inv_m, gdel, j, p, live, nr, fr, pr, gr, i0, i1);
 #pragma unroll
     for (int k = 0; k < W; ++k)
         if (rmask >> k & 1u) atomicAdd(&gdel[(long)(j * W + k) * g.npix + p], gr[k]);
@@ -339,7 +352,7 @@ template <int W, int DT>
 cudaError_t launch_fwd_t(af_plan_t pl)
 {
     constexpr int kW = FwdLaunch<DT>::kWarps;
-    const dim3 blocks((pl->g.npix + 32 * kW - 1) / (32 * kW), pl->g.nsub);
+    const dim3 blocks((pl->g.npix + 32 * kW - 1) / (32 * kW), pl->g.nsub * kFwdSplit);
     das_forward_kernel<W, DT><<<blocks, 32 * kW, 0, pl->stream>>>(
         pl->g, pl->iq, pl->iq_scale, pl->D, pl->nrange, pl->B);
     return cudaGetLastError();
@@ -352,7 +365,7 @@ cudaError_t launch_adj_t(af_plan_t pl)
     cudaError_t e = cudaMemsetAsync(pl->gdel, 0, n * sizeof(float), pl->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(&pl->scal->gmax_bits, 0, sizeof(int), pl->stream);   // read by the ray adjoint
     if (e != cudaSuccess) return e;
-    const dim3 blocks((pl->g.npix + 32 * kAdjWarps - 1) / (32 * kAdjWarps), pl->g.nsub);
+    const dim3 blocks((pl->g.npix + 32 * kAdjWarps - 1) / (32 * kAdjWarps), pl->g.nsub * kAdjSplit);
     das_adjoint_kernel<W, DT><<<blocks, 32 * kAdjWarps, 0, pl->stream>>>(pl->g, pl->iq, pl->iq_scale, pl->D,
                                                                        pl->nrange, pl->B, pl->z, pl->mask,
                                                                        pl->scal, pl->gdel);
