@@ -127,10 +127,11 @@ template <> struct GridTaps<true> {
     }
 };
 
-// One thread per (element e, pixel p), grid-stride over e * npix + p, with the
-// slowness deviation s - sbar staged once per CTA in shared memory, padded by
-// two edge-replicated nodes on every side so that each of the 16 taps of a
-// point inside the grid box reads the clamp-to-edge value without a branch.
+// One thread per (element e, pixel p), items e * npix + p taken by warps in
+// chunks of 32 from a counter, with the slowness deviation s - sbar staged once
+// per CTA in shared memory, padded by two edge-replicated nodes on every side so
+// that each of the 16 taps of a point inside the grid box reads the
+// clamp-to-edge value without a branch.
 template <bool PAIRS, int PF = 0>
 __global__ void __launch_bounds__(PAIRS ? 1024 : 256) delays_kernel(AfGeom g, const float *__restrict__ s,
                                                      const float4 *__restrict__ elem,
@@ -159,8 +160,17 @@ __global__ void __launch_bounds__(PAIRS ? 1024 : 256) delays_kernel(AfGeom g, co
     const ff off = {g.off_hi, g.off_lo};
     int n_apod = 0, n_fp64 = 0;
     const long total = (long)g.ne * g.npix;
-    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long)gridDim.x * blockDim.x) {
+    // warps take chunks of 32 consecutive items from a counter, the next one claimed
+    // while the current one runs, so the SMs finish together (a fixed grid stride
+    // left them finishing over ~50 us: 0.552 -> 0.542 ms, 128 elements)
+    const int lane = threadIdx.x & 31;
+    unsigned long long cn = 0;
+    if (lane == 0) cn = atomicAdd(&scal->delay_next, 32ull);
+    for (long chunk = (long)__shfl_sync(0xffffffffu, cn, 0); chunk < total;
+         chunk = (long)__shfl_sync(0xffffffffu, cn, 0)) {
+        if (lane == 0) cn = atomicAdd(&scal->delay_next, 32ull);
+        const long idx = chunk + lane;
+        if (idx >= total) continue;
         const int e = (int)(idx / g.npix), p = (int)(idx - (long)e * g.npix);
         const float4 el = elem[e];
         const float2 px = pix[p];
@@ -338,6 +348,15 @@ __global__ void __launch_bounds__(PAIRS ? 1024 : 256) delays_kernel(AfGeom g, co
     if ((threadIdx.x & 31) == 0) {
         if (n_apod) atomicAdd(&scal->n_apod, n_apod);
         if (n_fp64) atomicAdd(&scal->fp64_solves, n_fp64);
+    }
+    // the CTA that finishes last returns the item counter to zero for the next launch
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&scal->delay_done, 1u) == gridDim.x - 1) {
+            scal->delay_next = 0;
+            scal->delay_done = 0;
+        }
     }
 }
 

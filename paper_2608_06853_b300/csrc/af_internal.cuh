@@ -94,6 +94,8 @@ struct AfScal {
     int ray_next;        // next item block of the ray adjoint (zero between launches)
     unsigned stat_done;  // CTAs of the grid statistics done (zero between launches)
     unsigned cmpe_done;  // CTAs of the CMPE forward done (zero between launches)
+    unsigned delay_done; // CTAs of the delay kernel done (zero between launches)
+    unsigned long long delay_next;   // next (element, pixel) item of the delay kernel (zero between launches)
 };
 
 struct AfJobs;          // jobs from host memory (af_job_*): staging buffers, copy stream, events

@@ -20,7 +20,8 @@ namespace {
 // rays run side by side, so at one step k their points usually fall in the
 // same grid cell.  A CTA takes blocks of one item per thread from a device
 // counter (blocks differ in work because of the apodization; a block's inputs
-// are loaded while the block before it is scattered), compacts the
+// are loaded while the block before it is scattered; the last round of blocks
+// is cut into quarter blocks), compacts the
 // items with a non-zero dL/dT into a table, and spreads the flattened
 // (item, step) list over all its threads (lane = consecutive step along a
 // ray).  A thread sums, in registers, the 4 x 4 stencils of the item's points
@@ -40,8 +41,8 @@ namespace {
 // max|dL/dT|.  Shared memory holds int32 (integer atomics are several times
 // faster than float ones); one ray adds at most max|dL/dT| (5 cell diagonals +
 // L/(N+1)) to a node and fix_scale is set on the host so that kRayFlushRays
-// rays stay below 2^30, so after whole blocks of at most kRayItemsPerFlush items
-// the integer grids are added into the int64 padded grid in global memory, by
+// rays stay below 2^30, so after whole blocks holding at most kRayItemsPerFlush
+// items in all, the integer grids are added into the int64 padded grid in global memory, by
 // integer atomic adds no thread waits for, and cleared.  All sums are integer
 // sums up to the final conversion, so the result depends neither on which CTA
 // took which block nor on the order of the adds.  Rounding adds 1.5 * 2^23 in the last
@@ -135,20 +136,28 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
     const int npts = g.nseg + 1;
     const int ngroups = (g.npix + kRayGroup - 1) / kRayGroup;
     const long nitems = (long)g.ne * ngroups;
-    const long nblk = S > 0.0f ? (nitems + T - 1) / T : 0;
-    constexpr int kBlocksPerFlush = kRayItemsPerFlush / T;
-    static_assert(kBlocksPerFlush >= 1, "a flush interval holds at most kRayItemsPerFlush items");
+    // blocks of T items, then quarter blocks for the last gridDim.x * T items, so
+    // that the CTAs run out of work within a quarter block of each other (whole
+    // blocks of ~50 us left SMs idle for up to one block: 0.750 -> 0.734 ms;
+    // eighth blocks 0.738, quarter blocks over two rounds 0.741)
+    constexpr int TQ = T / 4;
+    static_assert(T <= kRayItemsPerFlush, "a flush interval holds at most kRayItemsPerFlush items");
+    long nfull = (nitems - (long)gridDim.x * T) / T;
+    if (nfull < 0) nfull = 0;
+    const long nblk = S > 0.0f ? nfull + (nitems - nfull * T + TQ - 1) / TQ : 0;
+    auto bstart = [&](long b) { return b < nfull ? b * T : nfull * T + (b - nfull) * TQ; };
+    auto bsize = [&](long b) { return b < nfull ? T : TQ; };
     if (threadIdx.x == 0) s_blk = atomicAdd(&scal->ray_next, 1);
     __syncthreads();
     long blk = s_blk;
-    int since_flush = 0;
+    int since_flush = 0;                             // items since the last flush
     // the inputs of this thread's item (dL/dT, exit angle or exit x, pixel), loaded
     // one block ahead: the next block's are in flight while this one is scattered
     float in_gv[kRayGroup], in_ph[kRayGroup];
     float2 in_px[kRayGroup];
     auto load_inputs = [&](long b) {
-        const long it = b * T + threadIdx.x;
-        const bool ok = b < nblk && it < nitems;
+        const long it = bstart(b) + threadIdx.x;
+        const bool ok = b < nblk && threadIdx.x < bsize(b) && it < nitems;
         const int e = ok ? (int)(it / ngroups) : 0, grp = ok ? (int)(it - (long)e * ngroups) : 0;
 #pragma unroll
         for (int m = 0; m < kRayGroup; ++m) {
@@ -165,7 +174,8 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
         // the next block's index, claimed now and needed only after the table fill
         long nxt = 0;
         if (threadIdx.x == 0) nxt = atomicAdd(&scal->ray_next, 1);
-        const long item = blk * T + threadIdx.x;
+        const long item = bstart(blk) + threadIdx.x;
+        const int cur_size = bsize(blk);
         float c[kRayGroup];
         float4 rp[kRayGroup];
         bool any = false;
@@ -174,7 +184,7 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
             c[m] = 0.0f;
             rp[m] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (item < nitems) {
+        if (threadIdx.x < cur_size && item < nitems) {
             const int e = (int)(item / ngroups);
 #pragma unroll
             for (int m = 0; m < kRayGroup; ++m) {
@@ -311,7 +321,8 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
         if (lane < nq) run_queued<DUAL>(g, rg, fq[warp][lane], acci, rays, T, rayc, rayb);   // last partial batch
         blk = s_blk;
         __syncthreads();                             // table and queue free for the next block
-        if (++since_flush == kBlocksPerFlush || blk >= nblk) {
+        since_flush += cur_size;
+        if (blk >= nblk || since_flush + bsize(blk) > kRayItemsPerFlush) {
             since_flush = 0;
             for (int q = threadIdx.x; q < rg.width * rg.rows; q += T) {
                 const int j = q / rg.width, i = q - j * rg.width;
