@@ -195,12 +195,12 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------- roofline
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
-# capture of the full workload at 10 scatterers per resolution cell (second launch of
-# each kernel, one kernel per capture), per kernel; None once the kernel changed after
+# capture of the full workload at 10 scatterers per resolution cell (the second
+# iteration's launch of each kernel), per kernel; None once the kernel changed after
 # the capture (see profiles/).  The adjoint stages' traffic follows
 # the CMPE mask of the captured iteration.
-NCU_TRAFFIC = {"das_forward": 618.1e6 + 85.5e6, "das_adjoint": 282.58e6 + 18.45e6,
-               "ray_adjoint": 33.57e6 + 0.0, "delays": 16.20e6 + 24.89e6}
+NCU_TRAFFIC = {"das_forward": 574.95e6 + 91.00e6, "das_adjoint": 311.86e6 + 23.11e6,
+               "ray_adjoint": 33.60e6 + 0.0, "delays": 15.91e6 + 24.75e6}
 
 # algorithmic FP32 lane-operations per unit, from the arithmetic of the method.
 # Ray point: position (2) + cell and fraction (4) + two Keys weight sets (2 x 10) + 16
