@@ -478,6 +478,9 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
     if (e == cudaSuccess && npix) e = cudaMemcpy(pl->pix_pol, pix_pol.data(), npix * sizeof(float2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(pl->scal, 0, sizeof(AfScal));
     if (e == cudaSuccess) e = cudaMemset(pl->gdel, 0, (nep ? nep : 1) * sizeof(float));
+    // the gradient reduce returns every cell it reads to zero, so the ray adjoint
+    // always starts from a zero grid
+    if (e == cudaSuccess) e = cudaMemset(pl->gpad, 0, (pl->smem_grid / sizeof(float)) * sizeof(long long));
     if (e != cudaSuccess) return bail(cuda_fail(e, "plan upload"));
     *out = pl;
     return AF_OK;

@@ -54,6 +54,7 @@ __device__ void cmpe_fold(const AfGeom &g, const double *patch_sum, const int *p
         scal->n_active = M;
         scal->inv_m = (float)(1.0 / (M > 1 ? M : 1));
         scal->cmpe_done = 0;
+        scal->gmax_bits = 0;           // max|dL/dT|, taken by the next DAS adjoint
         if (loss) {
             loss[0] = (float)(lc + (double)g.w1 * scal->rtv + (double)g.w2 * scal->rsv);
             loss[1] = (float)lc;

@@ -362,8 +362,8 @@ template <int W, int DT>
 cudaError_t launch_adj_t(af_plan_t pl)
 {
     const long n = (long)pl->g.ne * pl->g.npix;
+    // (max|dL/dT| starts from zero: the CMPE forward's fold resets it)
     cudaError_t e = cudaMemsetAsync(pl->gdel, 0, n * sizeof(float), pl->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(&pl->scal->gmax_bits, 0, sizeof(int), pl->stream);   // read by the ray adjoint
     if (e != cudaSuccess) return e;
     const dim3 blocks((pl->g.npix + 32 * kAdjWarps - 1) / (32 * kAdjWarps), pl->g.nsub * kAdjSplit);
     das_adjoint_kernel<W, DT><<<blocks, 32 * kAdjWarps, 0, pl->stream>>>(pl->g, pl->iq, pl->iq_scale, pl->D,

@@ -50,8 +50,13 @@ __device__ __forceinline__ void grid_stats_fold(const AfGeom &g, const StatPart 
 // The CTA that finishes last (counted in scal->stat_done, which the fold sets
 // back to zero) folds the gridDim.x partials with its first warp.
 __global__ void __launch_bounds__(256, 4) grid_stats_partial_kernel(AfGeom g, const float *__restrict__ s,
-                                                                 StatPart *__restrict__ part, AfScal *scal)
+                                                                 StatPart *__restrict__ part, AfScal *scal,
+                                                                 int2 *__restrict__ nrange)
 {
+    // the delay kernel, which always follows, takes the minima of the pixels' one-way
+    // sample indices (and of their negatives) into nrange
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.npix; p += gridDim.x * blockDim.x)
+        nrange[p] = make_int2(0x7F7F7F7F, 0x7F7F7F7F);
     __shared__ double red[3][8];
     __shared__ int s_last;
     // per-thread partial sums in float (float64 throughput is low on this GPU); the
@@ -412,7 +417,7 @@ DelayShape delays_shape(size_t smem_scalar, int sm_count)
 
 cudaError_t launch_grid_stats(af_plan_t pl, const float *s)
 {
-    grid_stats_partial_kernel<<<kStatBlocks, 256, 0, pl->stream>>>(pl->g, s, pl->stat_part, pl->scal);
+    grid_stats_partial_kernel<<<kStatBlocks, 256, 0, pl->stream>>>(pl->g, s, pl->stat_part, pl->scal, pl->nrange);
     return cudaGetLastError();
 }
 
@@ -420,9 +425,8 @@ cudaError_t launch_delays(af_plan_t pl, const float *s)
 {
     if ((long)pl->g.ne * pl->g.npix == 0) return cudaSuccess;
     const DelayShape &sh = pl->delay;
-    // sample-index range per pixel: both fields start at 0x7F7F7F7F (above any index)
-    cudaError_t err = cudaMemsetAsync(pl->nrange, 0x7F, (size_t)pl->g.npix * sizeof(int2), pl->stream);
-    if (err != cudaSuccess) return err;
+    // sample-index range per pixel: both fields were set to 0x7F7F7F7F (above any
+    // index) by the grid statistics, which every caller launches just before
     if (sh.pairs && pl->g.pitch == kDelayPitch128)
         delays_kernel<true, kDelayPitch128><<<sh.blocks, sh.threads, sh.smem, pl->stream>>>(
             pl->g, s, pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->have_phi ? 1 : 0,
@@ -435,7 +439,7 @@ cudaError_t launch_delays(af_plan_t pl, const float *s)
         delays_kernel<false><<<sh.blocks, sh.threads, sh.smem, pl->stream>>>(
             pl->g, s, pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->have_phi ? 1 : 0,
             pl->use_surrogate ? pl->sur_fb : nullptr, pl->D, pl->nrange, pl->scal);
-    err = cudaGetLastError();
+    const cudaError_t err = cudaGetLastError();
     if (err == cudaSuccess) pl->have_phi = true;
     return err;
 }

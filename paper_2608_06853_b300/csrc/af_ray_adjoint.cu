@@ -6,8 +6,8 @@
 // Each persistent CTA scatters its rays' bicubic weights into a private,
 // padded copy of the grid in shared memory (shared-memory atomics only) and
 // adds it, block by block, into one padded integer grid in global memory; a
-// second kernel folds the padding back onto the edge nodes and adds the
-// regulariser gradient.  The padded row pitch is odd, so consecutive grid rows
+// second kernel folds the padding back onto the edge nodes, clears the grid for
+// the next launch and adds the regulariser gradient.  The padded row pitch is odd, so consecutive grid rows
 // start in different shared-memory banks.
 #include <math.h>
 
@@ -350,21 +350,26 @@ __device__ __forceinline__ float dz_sign(float x, float k)      // D_k'(x)
 // c = 1 / (c_unit s), the speed in the units of Eq. 10-11);
 // also returns the ray adjoint's block counter to zero for its next launch
 __global__ void __launch_bounds__(256) reduce_grad_kernel(AfGeom g, const float *__restrict__ s,
-                                                          const long long *__restrict__ gpad, int have_rays,
+                                                          long long *__restrict__ gpad, int have_rays,
                                                           AfScal *scal, float *__restrict__ grad)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k == 0) scal->ray_next = 0;
     if (k >= g.ng) return;
     const int j = k / g.nx, i = k - j * g.nx, nx = g.nx, nz = g.nz;
-    // fold the padding of the integer grid onto the clamped edge nodes
+    // fold the padding of the integer grid onto the clamped edge nodes; every padded
+    // cell belongs to exactly one node, whose thread also returns it to zero for the
+    // next launch of the ray adjoint
     long long tot = 0;
     if (have_rays) {
         const int P = g.pitch;
         const int ilo = i == 0 ? 0 : i + 2, ihi = i == nx - 1 ? nx + 3 : i + 2;
         const int jlo = j == 0 ? 0 : j + 2, jhi = j == nz - 1 ? nz + 3 : j + 2;
         for (int jj = jlo; jj <= jhi; ++jj)
-            for (int ii = ilo; ii <= ihi; ++ii) tot += gpad[jj * P + ii];
+            for (int ii = ilo; ii <= ihi; ++ii) {
+                tot += gpad[jj * P + ii];
+                gpad[jj * P + ii] = 0;
+            }
     }
     const float gmax = __int_as_float(scal->gmax_bits);
     const float acc = gmax > 0.0f ? (float)((double)tot * ((double)gmax / (double)g.fix_scale)) : 0.0f;
@@ -491,9 +496,6 @@ cudaError_t launch_ray_adjoint(af_plan_t pl, const float *s, float *grad)
     if ((long)pl->g.ne * pl->g.npix > 0) {
         const RayAdjShape &sh = pl->rayadj;
         const RayGrid rg = ray_grid_layout(pl->g.nx, pl->g.nz, sh.dual, pl->g.pitch);
-        cudaError_t ez = cudaMemsetAsync(pl->gpad, 0, (size_t)pl->g.pitch * (pl->g.nz + 4) * sizeof(long long),
-                                         pl->stream);
-        if (ez != cudaSuccess) return ez;
         if (sh.dual && sh.threads == 768)
             ray_adjoint_kernel<24, true><<<sh.blocks, 768, sh.smem, pl->stream>>>(
                 pl->g, rg, pl->elem, pl->pix, pl->phi, pl->gdel, pl->scal, pl->gpad);
