@@ -76,6 +76,8 @@ __global__ void __launch_bounds__(32 * kCmpeWarps) cmpe_forward_kernel(AfGeom g,
     __shared__ double s_sum[kCmpeWarps];
     __shared__ int s_cnt[kCmpeWarps];
     __shared__ int s_last;
+    pdl_wait();
+    pdl_release();
     const int P = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int base = P * g.patch_npix;
     double lsum = 0.0;
@@ -114,6 +116,8 @@ __global__ void __launch_bounds__(256) cmpe_finalize_kernel(AfGeom g, const doub
                                                             const int *__restrict__ patch_cnt,
                                                             AfScal *scal, float *__restrict__ loss)
 {
+    pdl_wait();
+    pdl_release();
     cmpe_fold(g, patch_sum, patch_cnt, scal, loss);
 }
 
@@ -204,14 +208,13 @@ cudaError_t launch_images(af_plan_t pl, float *bmode, float *cimg)
 cudaError_t launch_cmpe_forward(af_plan_t pl, float *loss)
 {
     if (pl->g.n_patch > 0 && pl->g.npair > 0) {
-        cmpe_forward_kernel<<<pl->g.n_patch, 32 * kCmpeWarps, 0, pl->stream>>>(pl->g, pl->B, pl->z, pl->mask,
-                                                                  pl->patch_sum, pl->patch_cnt, pl->scal, loss);
-        return cudaGetLastError();
+        return launch_dependent(cmpe_forward_kernel, dim3(pl->g.n_patch), dim3(32 * kCmpeWarps), 0, pl->stream, pl->g,
+                                pl->B, pl->z, pl->mask, pl->patch_sum, pl->patch_cnt, pl->scal, loss);
     }
     AfGeom g = pl->g;
     g.n_patch = 0;                       // no terms: L_CMPE = 0
-    cmpe_finalize_kernel<<<1, 256, 0, pl->stream>>>(g, pl->patch_sum, pl->patch_cnt, pl->scal, loss);
-    return cudaGetLastError();
+    return launch_dependent(cmpe_finalize_kernel, dim3(1), dim3(256), 0, pl->stream, g, pl->patch_sum, pl->patch_cnt,
+                            pl->scal, loss);
 }
 
 cudaError_t launch_cmpe_totals(af_plan_t pl, double *out)

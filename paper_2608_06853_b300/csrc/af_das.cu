@@ -197,6 +197,8 @@ __global__ void __launch_bounds__(32 * FwdLaunch<DT>::kWarps, FwdLaunch<DT>::kMi
                                                              const int2 *__restrict__ nrange,
                                                              float2 *__restrict__ B)
 {
+    pdl_wait();
+    pdl_release();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int p = (blockIdx.x * FwdLaunch<DT>::kWarps + warp) * 32 + lane;
     const int j = blockIdx.y % g.nsub, piece = blockIdx.y / g.nsub;
@@ -302,6 +304,8 @@ __global__ void __launch_bounds__(32 * kAdjWarps, kAdjMinBlocks) das_adjoint_ker
                                                              const AfScal *__restrict__ scal,
                                                              float *__restrict__ gdel)
 {
+    pdl_wait();
+    pdl_release();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int p = (blockIdx.x * kAdjWarps + warp) * 32 + lane;
     const int j = blockIdx.y % g.nsub, piece = blockIdx.y / g.nsub;
@@ -335,6 +339,8 @@ __global__ void __launch_bounds__(256) gdel_max_kernel(const float *__restrict__
 {
     // float4 loads (the table is a device allocation, so 16-byte aligned), then the
     // tail; a maximum does not depend on the order
+    pdl_wait();
+    pdl_release();
     float amax = 0.0f;
     const long n4 = n >> 2, stride = (long)gridDim.x * blockDim.x, first = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const float4 *__restrict__ g4 = reinterpret_cast<const float4 *>(gdel);
@@ -353,9 +359,8 @@ cudaError_t launch_fwd_t(af_plan_t pl)
 {
     constexpr int kW = FwdLaunch<DT>::kWarps;
     const dim3 blocks((pl->g.npix + 32 * kW - 1) / (32 * kW), pl->g.nsub * kFwdSplit);
-    das_forward_kernel<W, DT><<<blocks, 32 * kW, 0, pl->stream>>>(
-        pl->g, pl->iq, pl->iq_scale, pl->D, pl->nrange, pl->B);
-    return cudaGetLastError();
+    return launch_dependent(das_forward_kernel<W, DT>, blocks, dim3(32 * kW), 0, pl->stream, pl->g, pl->iq,
+                            pl->iq_scale, pl->D, pl->nrange, pl->B);
 }
 
 template <int W, int DT>
@@ -366,13 +371,11 @@ cudaError_t launch_adj_t(af_plan_t pl)
     cudaError_t e = cudaMemsetAsync(pl->gdel, 0, n * sizeof(float), pl->stream);
     if (e != cudaSuccess) return e;
     const dim3 blocks((pl->g.npix + 32 * kAdjWarps - 1) / (32 * kAdjWarps), pl->g.nsub * kAdjSplit);
-    das_adjoint_kernel<W, DT><<<blocks, 32 * kAdjWarps, 0, pl->stream>>>(pl->g, pl->iq, pl->iq_scale, pl->D,
-                                                                       pl->nrange, pl->B, pl->z, pl->mask,
-                                                                       pl->scal, pl->gdel);
-    e = cudaGetLastError();
+    e = launch_dependent(das_adjoint_kernel<W, DT>, blocks, dim3(32 * kAdjWarps), 0, pl->stream, pl->g, pl->iq,
+                         pl->iq_scale, pl->D, pl->nrange, pl->B, pl->z, pl->mask, pl->scal, pl->gdel);
     if (e != cudaSuccess) return e;
-    gdel_max_kernel<<<pl->sm_count * 4, 256, 0, pl->stream>>>(pl->gdel, n, &pl->scal->gmax_bits);
-    return cudaGetLastError();
+    return launch_dependent(gdel_max_kernel, dim3(pl->sm_count * 4), dim3(256), 0, pl->stream, pl->gdel, n,
+                            &pl->scal->gmax_bits);
 }
 
 template <int DT>

@@ -53,6 +53,8 @@ __global__ void __launch_bounds__(256, 4) grid_stats_partial_kernel(AfGeom g, co
                                                                  StatPart *__restrict__ part, AfScal *scal,
                                                                  int2 *__restrict__ nrange)
 {
+    pdl_wait();
+    pdl_release();
     // the delay kernel, which always follows, takes the minima of the pixels' one-way
     // sample indices (and of their negatives) into nrange
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.npix; p += gridDim.x * blockDim.x)
@@ -149,6 +151,8 @@ __global__ void __launch_bounds__(PAIRS ? 1024 : 256) delays_kernel(AfGeom g, co
                                                      AfScal *scal)
 {
     extern __shared__ float sm[];
+    pdl_wait();
+    pdl_release();
     const float sbar = scal->sbar;
     const int P = PF ? PF : g.pitch, rows = g.nz + 4;   // PF: the pitch as a compile-time constant
     for (int k = threadIdx.x; k < P * rows; k += blockDim.x) {
@@ -417,8 +421,8 @@ DelayShape delays_shape(size_t smem_scalar, int sm_count)
 
 cudaError_t launch_grid_stats(af_plan_t pl, const float *s)
 {
-    grid_stats_partial_kernel<<<kStatBlocks, 256, 0, pl->stream>>>(pl->g, s, pl->stat_part, pl->scal, pl->nrange);
-    return cudaGetLastError();
+    return launch_dependent(grid_stats_partial_kernel, dim3(kStatBlocks), dim3(256), 0, pl->stream, pl->g, s,
+                            pl->stat_part, pl->scal, pl->nrange);
 }
 
 cudaError_t launch_delays(af_plan_t pl, const float *s)
@@ -427,19 +431,13 @@ cudaError_t launch_delays(af_plan_t pl, const float *s)
     const DelayShape &sh = pl->delay;
     // sample-index range per pixel: both fields were set to 0x7F7F7F7F (above any
     // index) by the grid statistics, which every caller launches just before
-    if (sh.pairs && pl->g.pitch == kDelayPitch128)
-        delays_kernel<true, kDelayPitch128><<<sh.blocks, sh.threads, sh.smem, pl->stream>>>(
-            pl->g, s, pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->have_phi ? 1 : 0,
-            pl->use_surrogate ? pl->sur_fb : nullptr, pl->D, pl->nrange, pl->scal);
-    else if (sh.pairs)
-        delays_kernel<true><<<sh.blocks, sh.threads, sh.smem, pl->stream>>>(
-            pl->g, s, pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->have_phi ? 1 : 0,
-            pl->use_surrogate ? pl->sur_fb : nullptr, pl->D, pl->nrange, pl->scal);
-    else
-        delays_kernel<false><<<sh.blocks, sh.threads, sh.smem, pl->stream>>>(
-            pl->g, s, pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi, pl->have_phi ? 1 : 0,
-            pl->use_surrogate ? pl->sur_fb : nullptr, pl->D, pl->nrange, pl->scal);
-    const cudaError_t err = cudaGetLastError();
+    auto kernel = sh.pairs && pl->g.pitch == kDelayPitch128 ? delays_kernel<true, kDelayPitch128>
+                  : sh.pairs                                   ? delays_kernel<true>
+                                                               : delays_kernel<false>;
+    const cudaError_t err = launch_dependent(kernel, dim3(sh.blocks), dim3(sh.threads), sh.smem, pl->stream, pl->g, s,
+                                             pl->elem, pl->elem_pol, pl->pix, pl->pix_pol, pl->phi,
+                                             pl->have_phi ? 1 : 0, pl->use_surrogate ? pl->sur_fb : nullptr, pl->D,
+                                             pl->nrange, pl->scal);
     if (err == cudaSuccess) pl->have_phi = true;
     return err;
 }

@@ -235,6 +235,34 @@ __device__ __forceinline__ void keys_weights2(float2 t, float2 (&w)[4])
     w[2] = __ffma2_rn(neg, w[1], __ffma2_rn(neg, m, one));
 }
 
+// Programmatic dependent launch.  The kernels of an iteration are launched by
+// launch_dependent(), so the GPU may schedule a kernel's CTAs while the kernel
+// before it in the stream drains, instead of after a full launch round trip.
+// Such a kernel calls pdl_wait() before its first access to global memory: it
+// returns once the kernel before has completed and its writes are visible.  It
+// then calls pdl_release(), which lets the kernel after it be scheduled once all
+// of its own CTAs have started.  Both are no-ops in a kernel launched without
+// the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                    cudaStream_t stream, Args... args)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // records the message returned by af_last_error() and returns st
 af_status af_set_error(af_status st, const char *fmt, ...);
 

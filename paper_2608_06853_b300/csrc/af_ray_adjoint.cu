@@ -129,7 +129,9 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
     __shared__ long s_blk;
     const int P = g.pitch;
     const int nacc = DUAL ? rg.base_b + rg.pb * rg.rows : rg.pa * rg.rows;
-    for (int k = threadIdx.x; k < nacc; k += T) acci[k] = 0;
+    for (int k = threadIdx.x; k < nacc; k += T) acci[k] = 0;      // shared memory only: before the wait
+    pdl_wait();
+    pdl_release();
     const float gmax = __int_as_float(scal->gmax_bits);
     const float S = gmax > 0.0f ? g.fix_scale / gmax : 0.0f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -353,6 +355,8 @@ __global__ void __launch_bounds__(256) reduce_grad_kernel(AfGeom g, const float 
                                                           long long *__restrict__ gpad, int have_rays,
                                                           AfScal *scal, float *__restrict__ grad)
 {
+    pdl_wait();
+    pdl_release();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k == 0) scal->ray_next = 0;
     if (k >= g.ng) return;
@@ -406,6 +410,8 @@ __global__ void __launch_bounds__(256) adam_kernel(AfGeom g, const float *__rest
                                                    float *__restrict__ s, float *__restrict__ m,
                                                    float *__restrict__ v, float bc1, float bc2)
 {
+    pdl_wait();
+    pdl_release();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.ng) return;
     const float sk = s[k];
@@ -496,28 +502,23 @@ cudaError_t launch_ray_adjoint(af_plan_t pl, const float *s, float *grad)
     if ((long)pl->g.ne * pl->g.npix > 0) {
         const RayAdjShape &sh = pl->rayadj;
         const RayGrid rg = ray_grid_layout(pl->g.nx, pl->g.nz, sh.dual, pl->g.pitch);
-        if (sh.dual && sh.threads == 768)
-            ray_adjoint_kernel<24, true><<<sh.blocks, 768, sh.smem, pl->stream>>>(
-                pl->g, rg, pl->elem, pl->pix, pl->phi, pl->gdel, pl->scal, pl->gpad);
-        else if (sh.dual)
-            ray_adjoint_kernel<16, true><<<sh.blocks, 512, sh.smem, pl->stream>>>(
-                pl->g, rg, pl->elem, pl->pix, pl->phi, pl->gdel, pl->scal, pl->gpad);
-        else
-            ray_adjoint_kernel<8, false><<<sh.blocks, 256, sh.smem, pl->stream>>>(
-                pl->g, rg, pl->elem, pl->pix, pl->phi, pl->gdel, pl->scal, pl->gpad);
-        cudaError_t e = cudaGetLastError();
+        auto kernel = sh.dual && sh.threads == 768 ? ray_adjoint_kernel<24, true>
+                      : sh.dual                    ? ray_adjoint_kernel<16, true>
+                                                   : ray_adjoint_kernel<8, false>;
+        const int threads = sh.dual && sh.threads == 768 ? 768 : sh.dual ? 512 : 256;
+        const cudaError_t e = launch_dependent(kernel, dim3(sh.blocks), dim3(threads), sh.smem, pl->stream, pl->g, rg,
+                                               pl->elem, pl->pix, pl->phi, pl->gdel, pl->scal, pl->gpad);
         if (e != cudaSuccess) return e;
         have_rays = 1;
     }
-    reduce_grad_kernel<<<(pl->g.ng + 255) / 256, 256, 0, pl->stream>>>(pl->g, s, pl->gpad, have_rays, pl->scal,
-                                                                        grad);
-    return cudaGetLastError();
+    return launch_dependent(reduce_grad_kernel, dim3((pl->g.ng + 255) / 256), dim3(256), 0, pl->stream, pl->g, s,
+                            pl->gpad, have_rays, pl->scal, grad);
 }
 
 cudaError_t launch_adam(af_plan_t pl, const float *grad, float *s, float *m, float *v, int step)
 {
     const double bc1 = 1.0 - pow((double)pl->g.beta1, step);
     const double bc2 = 1.0 - pow((double)pl->g.beta2, step);
-    adam_kernel<<<(pl->g.ng + 255) / 256, 256, 0, pl->stream>>>(pl->g, grad, s, m, v, (float)bc1, (float)bc2);
-    return cudaGetLastError();
+    return launch_dependent(adam_kernel, dim3((pl->g.ng + 255) / 256), dim3(256), 0, pl->stream, pl->g, grad, s, m, v,
+                            (float)bc1, (float)bc2);
 }
