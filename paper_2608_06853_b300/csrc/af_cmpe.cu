@@ -15,13 +15,12 @@
 namespace {
 
 using cmpe::pair_ij;
-using cmpe::warp_sum;
 // index of the pair whose first image is (i, j), or -1
 using cmpe::pair_index;
 
-// one CTA of kCmpeWarps warps per patch; warp w takes pairs w, w + kCmpeWarps, ...
-// (the pairs are latency-bound on their loads, so many warps keep more of them in
-// flight; 16 warps per patch: 41.0 us, 32: 42.7 us, 8: 55.6 us on the 128-element
+// one CTA of kCmpeWarps warps per patch; warp w takes the kPairsPerWarp pairs from
+// w kPairsPerWarp on, then those kCmpeWarps kPairsPerWarp further, ...
+// (16 warps per patch: 29.5 us, 32: 44.8 us, 8: 37.2 us on the 128-element
 // workload, where 16-warp CTAs of all 400 patches are resident at once)
 constexpr int kCmpeWarps = 16;
 
@@ -82,9 +81,11 @@ __global__ void __launch_bounds__(32 * kCmpeWarps) cmpe_forward_kernel(AfGeom g,
     const int base = P * g.patch_npix;
     double lsum = 0.0;
     int cnt = 0;
-    for (int k = w; k < g.npair; k += kCmpeWarps) {
-        const cmpe::PairTerms t = cmpe::pair_terms(B, g.nsub, g.npix, base, g.patch_npix, k, lane);
-        if (lane == 0) {
+    const int slot = lane / cmpe::kPairLanes, sub = lane % cmpe::kPairLanes;
+    for (int k0 = w * cmpe::kPairsPerWarp; k0 < g.npair; k0 += kCmpeWarps * cmpe::kPairsPerWarp) {
+        const int k = k0 + slot;
+        const cmpe::PairTerms t = cmpe::pair_terms(B, g.nsub, g.npix, base, g.patch_npix, k, sub, k < g.npair);
+        if (sub == 0 && k < g.npair) {
             const int m = t.rho >= g.rho_thresh;
             const long o = (long)P * g.npair + k;
             z[o] = make_float2(t.zr, t.zi);
@@ -95,6 +96,8 @@ __global__ void __launch_bounds__(32 * kCmpeWarps) cmpe_forward_kernel(AfGeom g,
             }
         }
     }
+    lsum = cmpe::group_leaders_sum(lsum);
+    cnt = cmpe::group_leaders_sum(cnt);
     if (lane == 0) { s_sum[w] = lsum; s_cnt[w] = cnt; }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -38,8 +38,9 @@ struct PatchPartial {
 
 static __device__ __align__(256) PatchPartial g_patch_partials[AF_NOALLOC_MAX_PATCHES];
 
-// one CTA per patch, warp w takes pairs w, w + 8, ... (the pair arithmetic of the
-// planned path, cmpe::pair_terms)
+// one CTA per patch, warp w takes the kPairsPerWarp pairs from w kPairsPerWarp on,
+// then those 8 kPairsPerWarp further, ... (the pair arithmetic and lane grouping
+// of the planned path, cmpe::pair_terms, so both take the same mask decisions)
 __global__ void __launch_bounds__(256) noalloc_patch_kernel(const float2 *__restrict__ B, int nsub,
                                                             int npix, int patch_npix, float rho_thresh,
                                                             PatchPartial *__restrict__ part)
@@ -51,13 +52,17 @@ __global__ void __launch_bounds__(256) noalloc_patch_kernel(const float2 *__rest
     const int base = P * patch_npix;
     double lsum = 0.0;
     int cnt = 0;
-    for (int k = w; k < npair; k += 8) {
-        const cmpe::PairTerms t = cmpe::pair_terms(B, nsub, npix, base, patch_npix, k, lane);
-        if (lane == 0 && t.rho >= rho_thresh) {
+    const int slot = lane / cmpe::kPairLanes, sub = lane % cmpe::kPairLanes;
+    for (int k0 = w * cmpe::kPairsPerWarp; k0 < npair; k0 += 8 * cmpe::kPairsPerWarp) {
+        const int k = k0 + slot;
+        const cmpe::PairTerms t = cmpe::pair_terms(B, nsub, npix, base, patch_npix, k, sub, k < npair);
+        if (sub == 0 && k < npair && t.rho >= rho_thresh) {
             lsum += (double)fabsf(atan2f(t.zi, t.zr));
             ++cnt;
         }
     }
+    lsum = cmpe::group_leaders_sum(lsum);
+    cnt = cmpe::group_leaders_sum(cnt);
     if (lane == 0) { s_sum[w] = lsum; s_cnt[w] = cnt; }
     __syncthreads();
     if (threadIdx.x == 0) {
