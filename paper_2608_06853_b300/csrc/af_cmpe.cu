@@ -76,7 +76,6 @@ __global__ void __launch_bounds__(32 * kCmpeWarps) cmpe_forward_kernel(AfGeom g,
     __shared__ int s_cnt[kCmpeWarps];
     __shared__ int s_last;
     pdl_wait();
-    pdl_release();
     const int P = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int base = P * g.patch_npix;
     double lsum = 0.0;
@@ -120,7 +119,6 @@ __global__ void __launch_bounds__(256) cmpe_finalize_kernel(AfGeom g, const doub
                                                             AfScal *scal, float *__restrict__ loss)
 {
     pdl_wait();
-    pdl_release();
     cmpe_fold(g, patch_sum, patch_cnt, scal, loss);
 }
 

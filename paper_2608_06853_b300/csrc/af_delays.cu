@@ -54,7 +54,6 @@ __global__ void __launch_bounds__(256, 4) grid_stats_partial_kernel(AfGeom g, co
                                                                  int2 *__restrict__ nrange)
 {
     pdl_wait();
-    pdl_release();
     // the delay kernel, which always follows, takes the minima of the pixels' one-way
     // sample indices (and of their negatives) into nrange
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.npix; p += gridDim.x * blockDim.x)
@@ -152,7 +151,6 @@ __global__ void __launch_bounds__(PAIRS ? 1024 : 256) delays_kernel(AfGeom g, co
 {
     extern __shared__ float sm[];
     pdl_wait();
-    pdl_release();
     const float sbar = scal->sbar;
     const int P = PF ? PF : g.pitch, rows = g.nz + 4;   // PF: the pitch as a compile-time constant
     for (int k = threadIdx.x; k < P * rows; k += blockDim.x) {

@@ -236,15 +236,15 @@ __device__ __forceinline__ void keys_weights2(float2 t, float2 (&w)[4])
 }
 
 // Programmatic dependent launch.  The kernels of an iteration are launched by
-// launch_dependent(), so the GPU may schedule a kernel's CTAs while the kernel
-// before it in the stream drains, instead of after a full launch round trip.
-// Such a kernel calls pdl_wait() before its first access to global memory: it
-// returns once the kernel before has completed and its writes are visible.  It
-// then calls pdl_release(), which lets the kernel after it be scheduled once all
-// of its own CTAs have started.  Both are no-ops in a kernel launched without
-// the attribute.
+// launch_dependent(), so the GPU prepares a kernel's launch while the kernel
+// before it in the stream is still running.  Such a kernel calls pdl_wait()
+// before its first access to global memory: it returns once the kernel before
+// has completed and its writes are visible (a no-op in a kernel launched without
+// the attribute).  The kernel before triggers the launch implicitly when it
+// completes.  An explicit trigger at the start of every CTA
+// (griddepcontrol.launch_dependents) made a step 30 us slower on the 128-element
+// workload; the implicit one makes it 12 us faster than plain launches.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,

@@ -131,7 +131,6 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
     const int nacc = DUAL ? rg.base_b + rg.pb * rg.rows : rg.pa * rg.rows;
     for (int k = threadIdx.x; k < nacc; k += T) acci[k] = 0;      // shared memory only: before the wait
     pdl_wait();
-    pdl_release();
     const float gmax = __int_as_float(scal->gmax_bits);
     const float S = gmax > 0.0f ? g.fix_scale / gmax : 0.0f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -356,7 +355,6 @@ __global__ void __launch_bounds__(256) reduce_grad_kernel(AfGeom g, const float 
                                                           AfScal *scal, float *__restrict__ grad)
 {
     pdl_wait();
-    pdl_release();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k == 0) scal->ray_next = 0;
     if (k >= g.ng) return;
@@ -411,7 +409,6 @@ __global__ void __launch_bounds__(256) adam_kernel(AfGeom g, const float *__rest
                                                    float *__restrict__ v, float bc1, float bc2)
 {
     pdl_wait();
-    pdl_release();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.ng) return;
     const float sk = s[k];
