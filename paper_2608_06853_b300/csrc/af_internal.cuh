@@ -45,9 +45,11 @@ struct alignas(32) StatPart {
 constexpr int kTimingCap = 4096;   // recorded stage launches per timing window
 constexpr size_t kMaxGridSmemBytes = 200 * 1024;   // largest padded slowness grid held in shared memory
 
-// ray adjoint: pixels per work item, items between fixed-point flushes (the
-// window the fixed-point scale is sized for), and the largest pair of integer
-// grid copies it keeps in shared memory
+// ray adjoint: pixels per work item, the window the fixed-point scale is sized
+// for (kRayItemsPerFlush items, kRayFlushRays rays, each with the largest
+// |dL/dT|; the kernel flushes when the rays since its last flush reach that
+// window by their |dL/dT|), and the largest pair of integer grid copies it keeps
+// in shared memory
 constexpr int kRayGroup = 3;
 constexpr int kRayItemsPerFlush = 1024;
 constexpr double kRayFlushRays = (double)kRayItemsPerFlush * kRayGroup;

@@ -39,14 +39,18 @@ namespace {
 //
 // Accumulation is fixed point: value = round(c w S), S = fix_scale /
 // max|dL/dT|.  Shared memory holds int32 (integer atomics are several times
-// faster than float ones); one ray adds at most max|dL/dT| (5 cell diagonals +
-// L/(N+1)) to a node and fix_scale is set on the host so that kRayFlushRays
-// rays stay below 2^30, so after whole blocks holding at most kRayItemsPerFlush
-// items in all, the integer grids are added into the int64 padded grid in global memory, by
-// integer atomic adds no thread waits for, and cleared.  All sums are integer
-// sums up to the final conversion, so the result depends neither on which CTA
-// took which block nor on the order of the adds.  Rounding adds 1.5 * 2^23 in the last
-// FMA of a value (|value| < 2^22), so each partial sum is rounded to an integer.
+// faster than float ones).  A ray with dL/dT = g adds at most |g| (5 cell
+// diagonals + L/(N+1)) to a node, and fix_scale is set on the host so that
+// kRayFlushRays rays with |g| = max|dL/dT| stay below 2^30.  Each block sums
+// |g| / max|dL/dT| over its rays; before a block is scattered whose sum would
+// take the total since the last flush past that budget, the integer grids are
+// added into the int64 padded grid in global memory, by integer atomic adds no
+// thread waits for, and cleared (and once more at the end).  Most rays carry far
+// less than the largest |dL/dT|, so a CTA flushes rarely (flushing after every
+// block of 768 items cost 0.730 against 0.700 ms).  All sums are integer sums up
+// to the final conversion, so the result depends neither on which CTA took which
+// block nor on the order of the adds.  Rounding adds 1.5 * 2^23 in the last FMA
+// of a value (|value| < 2^22), so each partial sum is rounded to an integer.
 struct RayGrid {
     int width, rows;        // padded grid: nx + 4 columns, nz + 4 rows
     int pa, pb, base_b;     // row pitch of copy A (and B), offset of copy B
@@ -55,6 +59,13 @@ struct RayGrid {
 constexpr float kRound = 12582912.0f;   // 1.5 * 2^23
 constexpr int kRoundBits = 0x4B400000;
 constexpr int kLeadRay = kRayGroup / 2; // the middle ray of an item
+// Flush budget, in rays of the largest |dL/dT|: the window kRayFlushRays that the
+// fixed-point scale is set for, kept a little below it against float rounding of
+// the running bound.  Each ray also counts kRayRoundShare of a full ray: a full
+// ray may add ~2^30 / kRayFlushRays (~3.5e5) units to a node, 1/1024 of that is
+// ~340 units, more than the <= 33 units its rounding to integers can add.
+constexpr float kRayFlushBudget = 0.999f * (float)kRayFlushRays;
+constexpr float kRayRoundShare = 1.0f / 1024.0f;
 
 // padded cell of point k of a ray (gx0, gz0, gdx, gdz), the floors of its grid
 // coordinates and its Keys weights
@@ -126,6 +137,7 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
     __shared__ int rayb[T];                          // grid copy of the item (1: copy B)
     __shared__ int fq[WARPS][kQueue];                // queued points
     __shared__ int wcount[WARPS];
+    __shared__ float wbound[WARPS];
     __shared__ long s_blk;
     const int P = g.pitch;
     const int nacc = DUAL ? rg.base_b + rg.pb * rg.rows : rg.pa * rg.rows;
@@ -133,6 +145,23 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
     pdl_wait();
     const float gmax = __int_as_float(scal->gmax_bits);
     const float S = gmax > 0.0f ? g.fix_scale / gmax : 0.0f;
+    const float inv_gmax = gmax > 0.0f ? 1.0f / gmax : 0.0f;
+    // adds the integer grids into the global one (integer adds no thread waits for,
+    // exact in any order) and clears them; called by every thread of the CTA
+    auto flush_grid = [&]() {
+        for (int q = threadIdx.x; q < rg.width * rg.rows; q += T) {
+            const int j = q / rg.width, i = q - j * rg.width;
+            int v = acci[j * rg.pa + i];
+            acci[j * rg.pa + i] = 0;
+            if (DUAL) {
+                v += acci[rg.base_b + j * rg.pb + i];
+                acci[rg.base_b + j * rg.pb + i] = 0;
+            }
+            if (v != 0) atomicAdd(reinterpret_cast<unsigned long long *>(gpad + j * P + i),
+                                  (unsigned long long)(long long)v);
+        }
+        __syncthreads();
+    };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int npts = g.nseg + 1;
     const int ngroups = (g.npix + kRayGroup - 1) / kRayGroup;
@@ -142,7 +171,8 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
     // blocks of ~50 us left SMs idle for up to one block: 0.750 -> 0.734 ms;
     // eighth blocks 0.738, quarter blocks over two rounds 0.741)
     constexpr int TQ = T / 4;
-    static_assert(T <= kRayItemsPerFlush, "a flush interval holds at most kRayItemsPerFlush items");
+    static_assert(T * kRayGroup * (1.0f + kRayRoundShare) <= kRayFlushBudget,
+                  "a single block must fit in the flush budget");
     long nfull = (nitems - (long)gridDim.x * T) / T;
     if (nfull < 0) nfull = 0;
     const long nblk = S > 0.0f ? nfull + (nitems - nfull * T + TQ - 1) / TQ : 0;
@@ -151,7 +181,7 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
     if (threadIdx.x == 0) s_blk = atomicAdd(&scal->ray_next, 1);
     __syncthreads();
     long blk = s_blk;
-    int since_flush = 0;                             // items since the last flush
+    float since_bound = 0.0f;                        // magnitude bound of the rays since the last flush
     // the inputs of this thread's item (dL/dT, exit angle or exit x, pixel), loaded
     // one block ahead: the next block's are in flight while this one is scattered
     float in_gv[kRayGroup], in_ph[kRayGroup];
@@ -180,6 +210,7 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
         float c[kRayGroup];
         float4 rp[kRayGroup];
         bool any = false;
+        float ub = 0.0f;                             // this thread's rays, in rays of the largest |dL/dT|
 #pragma unroll
         for (int m = 0; m < kRayGroup; ++m) {
             c[m] = 0.0f;
@@ -211,18 +242,25 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
                 rp[m] = make_float4((qx - g.x0) * g.inv_dx, (qz - g.z0) * g.inv_dz,
                                     lx * g.inv_dx * g.inv_nseg, lz * g.inv_dz * g.inv_nseg);
                 any = any || c[m] != 0.0f;
+                if (c[m] != 0.0f) ub += fabsf(gv) * inv_gmax + kRayRoundShare;
             }
         }
         // CTA-wide compaction of the live items
         const unsigned live = __ballot_sync(0xffffffffu, any);
-        if (lane == 0) wcount[warp] = __popc(live);
+        for (int o = 16; o > 0; o >>= 1) ub += __shfl_xor_sync(0xffffffffu, ub, o);
+        if (lane == 0) {
+            wcount[warp] = __popc(live);
+            wbound[warp] = ub;
+        }
         __syncthreads();
         int base = 0, nlive = 0;
+        float bb = 0.0f;                             // the block's bound, the same in every thread
 #pragma unroll
         for (int w = 0; w < WARPS; ++w) {
             const int n = wcount[w];
             base += w < warp ? n : 0;
             nlive += n;
+            bb += wbound[w];
         }
         if (any) {
             const int slot = base + __popc(live & ((1u << lane) - 1u));
@@ -244,6 +282,11 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
         if (threadIdx.x == 0) s_blk = nxt;
         __syncthreads();
         load_inputs(s_blk);                          // the next block's, in flight during the scatter
+        if (since_bound + bb > kRayFlushBudget) {    // this block could overflow the integer grids
+            flush_grid();
+            since_bound = 0.0f;
+        }
+        since_bound += bb;
         const int npt_total = nlive * npts;
         int nq = 0;                                  // queued points of this warp (warp-uniform)
         // flat index q = r * npts + k of this lane, advanced by T per pass without division
@@ -322,23 +365,7 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
         if (lane < nq) run_queued<DUAL>(g, rg, fq[warp][lane], acci, rays, T, rayc, rayb);   // last partial batch
         blk = s_blk;
         __syncthreads();                             // table and queue free for the next block
-        since_flush += cur_size;
-        if (blk >= nblk || since_flush + bsize(blk) > kRayItemsPerFlush) {
-            since_flush = 0;
-            for (int q = threadIdx.x; q < rg.width * rg.rows; q += T) {
-                const int j = q / rg.width, i = q - j * rg.width;
-                int v = acci[j * rg.pa + i];
-                acci[j * rg.pa + i] = 0;
-                if (DUAL) {
-                    v += acci[rg.base_b + j * rg.pb + i];
-                    acci[rg.base_b + j * rg.pb + i] = 0;
-                }
-                // an integer add the thread does not wait for (exact in any order)
-                if (v != 0) atomicAdd(reinterpret_cast<unsigned long long *>(gpad + j * P + i),
-                                      (unsigned long long)(long long)v);
-            }
-            __syncthreads();
-        }
+        if (blk >= nblk) flush_grid();
     }
 }
 
