@@ -447,6 +447,17 @@ af_status af_gemm_bf16(const void *d_A, const void *d_B, float *d_D, int M, int 
  * counterpart in the paper. */
 af_status af_set_wait_limit(int tries);
 
+/* Ray adjoint: flush window of the shared-memory fixed-point grids, in rays of
+ * the largest |dL/dT|.  A CTA adds its integer grids into the global one before
+ * a block of rays whose summed |dL/dT| / max|dL/dT| would take the total since
+ * its last flush past this window.  The default (and maximum) is the window the
+ * fixed-point scale is sized for; rays > that maximum set the maximum, 0 flushes
+ * before every block.  A smaller window only flushes more often: the integer
+ * sums, and so dL/ds, do not change (a test uses it to run the flush path on
+ * small problems).  AF_ERR_ARG for a NULL plan or rays < 0 (or NaN).  No
+ * counterpart in the paper. */
+af_status af_set_ray_flush_budget(af_plan_t plan, double rays);
+
 /* Measured FP32 lane rate of the current device: lane-operations (one fused
  * multiply-add on one lane) per second of a plain, dependency-free FMA loop over
  * 8 CTAs per SM, timed with CUDA events on `stream`.  It is the denominator of

@@ -123,6 +123,7 @@ _SIGNATURES = {
     "af_gemm_bf16": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, _VP, _VP]),
     "af_set_wait_limit": (ctypes.c_int, [ctypes.c_int]),
+    "af_set_ray_flush_budget": (ctypes.c_int, [_VP, ctypes.c_double]),
     "af_fp32_lane_rate": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_double)]),
     "af_set_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "af_get_stage_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]),
@@ -502,6 +503,11 @@ class Plan:
 
     def set_timing(self, enable: bool):
         _check(self.lib.af_set_timing(self.handle, 1 if enable else 0), "af_set_timing")
+
+    def set_ray_flush_budget(self, rays: float):
+        """Flush window of the ray adjoint's fixed-point grids, in rays of the largest
+        |dL/dT| (capped at the window the fixed-point scale is sized for)."""
+        _check(self.lib.af_set_ray_flush_budget(self.handle, float(rays)), "af_set_ray_flush_budget")
 
     def stage_times(self):
         """{stage: (total ms, launches)} recorded since set_timing(True)."""

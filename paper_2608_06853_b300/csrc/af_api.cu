@@ -357,6 +357,7 @@ af_status af_plan(const af_config *c, void *stream, af_plan_t *out)
         const double s1 = ldexp(1.0, 30) / window;
         const double s2 = ldexp(1.0, 20) * (c->nseg + 1) / lmax;
         g.fix_scale = (float)fmin(s1, s2);
+        g.ray_flush_budget = kRayFlushBudget;
     }
     g.c_unit = (float)c->c_unit;
     g.optimizer = c->optimizer;
@@ -855,6 +856,14 @@ af_status af_get_counters(af_plan_t pl, long long *h)
     h[1] = sc.fp64_solves;
     h[2] = sc.n_active;
     h[3] = pl->g.npair;
+    return AF_OK;
+}
+
+af_status af_set_ray_flush_budget(af_plan_t pl, double rays)
+{
+    if (!pl) return fail(AF_ERR_ARG, "plan is NULL");
+    if (!(rays >= 0.0)) return fail(AF_ERR_ARG, "rays must be >= 0");
+    pl->g.ray_flush_budget = rays < (double)kRayFlushBudget ? (float)rays : kRayFlushBudget;
     return AF_OK;
 }
 

@@ -32,6 +32,7 @@ struct AfGeom {
     float w1, kx1, kz1, w2, kx2, kz2, hx_mm, hz_mm;
     float na_inv, nb_inv;                    // 1 / number of difference terms
     float fix_scale;                         // ray-adjoint fixed-point scale times max |dL/dT|
+    float ray_flush_budget;                  // ray adjoint: flush window in rays of max |dL/dT| (<= kRayFlushBudget)
     float c_unit, inv_c_unit;                // Eq. 9-11 act on c = 1 / (c_unit s)
     float lr, beta1, beta2, omb1, omb2, eps; // Adam on that c; omb = 1 - beta, formed in double
     int optimizer;                           // AF_OPT_ADAM or AF_OPT_GD
@@ -53,6 +54,13 @@ constexpr size_t kMaxGridSmemBytes = 200 * 1024;   // largest padded slowness gr
 constexpr int kRayGroup = 3;
 constexpr int kRayItemsPerFlush = 1024;
 constexpr double kRayFlushRays = (double)kRayItemsPerFlush * kRayGroup;
+// Flush budget, in rays of the largest |dL/dT|: the window kRayFlushRays that the
+// fixed-point scale is set for, kept a little below it against float rounding of
+// the running bound.  Each ray also counts kRayRoundShare of a full ray: a full
+// ray may add ~2^30 / kRayFlushRays (~3.5e5) units to a node, 1/1024 of that is
+// ~340 units, more than the <= 33 units its rounding to integers can add.
+constexpr float kRayFlushBudget = 0.999f * (float)kRayFlushRays;
+constexpr float kRayRoundShare = 1.0f / 1024.0f;
 constexpr size_t kRayDualMaxBytes = 180 * 1024;
 struct DelayShape {
     bool pairs;          // grid as float2 node pairs (i, i + 2) or scalar

@@ -59,13 +59,6 @@ struct RayGrid {
 constexpr float kRound = 12582912.0f;   // 1.5 * 2^23
 constexpr int kRoundBits = 0x4B400000;
 constexpr int kLeadRay = kRayGroup / 2; // the middle ray of an item
-// Flush budget, in rays of the largest |dL/dT|: the window kRayFlushRays that the
-// fixed-point scale is set for, kept a little below it against float rounding of
-// the running bound.  Each ray also counts kRayRoundShare of a full ray: a full
-// ray may add ~2^30 / kRayFlushRays (~3.5e5) units to a node, 1/1024 of that is
-// ~340 units, more than the <= 33 units its rounding to integers can add.
-constexpr float kRayFlushBudget = 0.999f * (float)kRayFlushRays;
-constexpr float kRayRoundShare = 1.0f / 1024.0f;
 
 // padded cell of point k of a ray (gx0, gz0, gdx, gdz), the floors of its grid
 // coordinates and its Keys weights
@@ -282,7 +275,7 @@ __global__ void __launch_bounds__(WARPS * 32) ray_adjoint_kernel(AfGeom g, RayGr
         if (threadIdx.x == 0) s_blk = nxt;
         __syncthreads();
         load_inputs(s_blk);                          // the next block's, in flight during the scatter
-        if (since_bound + bb > kRayFlushBudget) {    // this block could overflow the integer grids
+        if (since_bound + bb > g.ray_flush_budget) { // this block could overflow the integer grids
             flush_grid();
             since_bound = 0.0f;
         }

@@ -171,8 +171,8 @@ def test_noalloc_wrapper_checks_arguments_before_any_call():
 
 
 def test_new_entry_points_refuse_null_arguments_without_a_gpu():
-    """af_sweep, af_cmpe_totals, af_set_cmpe_totals and af_fp32_lane_rate check their
-    arguments on the host before any CUDA call."""
+    """af_sweep, af_cmpe_totals, af_set_cmpe_totals, af_fp32_lane_rate and
+    af_set_ray_flush_budget check their arguments on the host before any CUDA call."""
     lib = af.load()
     sp = (ctypes.c_double * 2)(1500.0, 1540.0)
     assert lib.af_sweep(None, None, None, sp, 2, 1540.0, 1, None, None) == af.AF_ERR_ARG
@@ -181,6 +181,7 @@ def test_new_entry_points_refuse_null_arguments_without_a_gpu():
     rate = ctypes.c_double()
     assert lib.af_fp32_lane_rate(None, None, ctypes.byref(rate)) == af.AF_ERR_ARG
     assert lib.af_set_wait_limit(-1) == af.AF_OK
+    assert lib.af_set_ray_flush_budget(None, 10.0) == af.AF_ERR_ARG
 
 
 def test_job_entry_points_refuse_null_arguments_without_a_gpu():

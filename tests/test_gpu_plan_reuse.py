@@ -62,3 +62,31 @@ def test_reused_plan_matches_fresh_plans():
             assert not np.array_equal(got["loss"], prev["loss"])       # the map changed
             assert not np.array_equal(got["T"], prev["T"])
         prev = got
+
+
+@pytest.mark.parametrize("lens_mode", [af.AF_LENS_NONE, af.AF_LENS_BENT_RAY])
+def test_ray_adjoint_flush_window_does_not_change_the_gradient(lens_mode):
+    """The ray adjoint adds its shared-memory integer grids into the global one when
+    the rays since the last flush would pass the fixed-point window by their summed
+    |dL/dT|; on a small problem that never happens before the end.  Windows of 1,
+    0.5 and 0 rays make every CTA flush before each of its blocks after the first:
+    the integer sums, hence dL/ds, are unchanged up to the DAS adjoint's float-atomic
+    order (Eq. 1 adjoint, Sec. III-A).  The loss may move by rounding only: with the
+    lens, later passes start the exit-point solve from the previous angles."""
+    p = synth.config_tiny(lens_mode=lens_mode)
+    psi = synth.simulate(p, 1500, seed=33)
+    iq = torch.from_numpy(psi).to(torch.device("cuda"))
+    s = speed_map(p, 3, 40.0)
+    plan = af.Plan(p)
+    ref = one_pass(plan, iq, s)
+    assert np.linalg.norm(ref["grad"]) > 0
+    for window in (1.0, 0.5, 0.0):
+        plan.set_ray_flush_budget(window)
+        got = one_pass(plan, iq, s)
+        np.testing.assert_allclose(got["loss"], ref["loss"], rtol=1e-6)
+        assert np.linalg.norm(got["grad"] - ref["grad"]) <= 1e-6 * np.linalg.norm(ref["grad"]), window
+    with pytest.raises(af.AfError):
+        plan.set_ray_flush_budget(-1.0)
+    plan.set_ray_flush_budget(1e30)                      # capped at the scale's window
+    got = one_pass(plan, iq, s)
+    assert np.linalg.norm(got["grad"] - ref["grad"]) <= 1e-6 * np.linalg.norm(ref["grad"])
