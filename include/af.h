@@ -21,7 +21,10 @@
  *    the library never frees it.  The plan owns its own workspaces.
  *  - Calls are asynchronous on the plan's stream (the cudaStream_t passed to
  *    af_plan; NULL = legacy default stream).  Outputs are valid once that
- *    stream has reached the call.
+ *    stream has reached the call.  The kernels of af_forward / af_adjoint /
+ *    af_step are programmatic dependent launches: each waits on the device
+ *    for the work before it on the stream to finish before touching memory,
+ *    so stream order holds as for plain launches.
  *  - Errors are returned as af_status codes and never thrown; af_last_error()
  *    returns a message for the last failing call of the calling thread.
  *    Argument and shape errors are detected on the host before any launch.
