@@ -36,6 +36,10 @@ template <> struct Sample<AF_IQ_F16> {
 // six or eight per SM spill and run slower (0.415, 0.421 ms for complex64).
 constexpr int kAdjWarps = 4;
 constexpr int kAdjMinBlocks = 5;
+// Unroll of the adjoint's transmit loop: 4 for complex64 (0.361 -> 0.346 ms), 2 for
+// 16-bit samples (4 measured bf16 0.361 -> 0.370, f16 0.347 -> 0.354; a full unroll
+// of 8 was slower for all three), same registers (96) and no spill.
+template <int DT> struct AdjUnroll { static constexpr int k = DT == AF_IQ_C64 ? 4 : 2; };
 
 // Forward launch: warps per CTA, CTAs per SM and transmit-loop unroll, the same
 // for every sample type.  Measured on the 128-element workload (forward ms):
@@ -273,7 +277,7 @@ __device__ __forceinline__ void das_adjoint_blocks(const AfGeom &g, const typena
             if ((i + 1) * W < g.ne) dnext = D[(long)(i + 1) * W * g.npix + p];
             continue;
         }
-#pragma unroll 2
+#pragma unroll(AdjUnroll<DT>::k)
         for (int tt = 0; tt < W; ++tt) {
             const int t = i * W + tt;
             const float4 dt = dnext;
