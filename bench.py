@@ -199,7 +199,7 @@ def run_reference(args, rank, world):
 # iteration's launch of each kernel), per kernel; None once the kernel changed after
 # the capture (see profiles/).  The adjoint stages' traffic follows
 # the CMPE mask of the captured iteration.
-NCU_TRAFFIC = {"das_forward": 574.82e6 + 90.04e6, "das_adjoint": 311.84e6 + 23.26e6,
+NCU_TRAFFIC = {"das_forward": 574.82e6 + 90.04e6, "das_adjoint": 311.99e6 + 25.68e6,
                "ray_adjoint": 33.58e6 + 0.0, "delays": 15.91e6 + 25.44e6}
 
 # algorithmic FP32 lane-operations per unit, from the arithmetic of the method.
