@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(PAIRS ? 1024 : 256) delays_kernel(AfGeom g, co
         const float gx1 = fmaf(kend, gdx, gx0), gz1 = fmaf(kend, gdz, gz0);
         const bool inside = fminf(gx0, gx1) >= -1.0f && fmaxf(gx0, gx1) < (float)g.nx &&
                             fminf(gz0, gz1) >= -1.0f && fmaxf(gz0, gz1) < (float)g.nz;
-        // the N+1 endpoint values in partial sums of 4, Kahan-summed
+        // the N+1 endpoint values in partial sums of 8, Kahan-summed
         float sum = 0.0f, comp = 0.0f;
         auto kahan = [&](float v) {
             const float y = v - comp;
@@ -311,11 +311,13 @@ __global__ void __launch_bounds__(PAIRS ? 1024 : 256) delays_kernel(AfGeom g, co
                 return part;
             };
             float kf = 0.0f;
-            for (; kf + 3.0f <= kend; kf += 4.0f) {
+            // partial sums of 8 endpoints, Kahan-summed (groups of 4: 0.538 ms,
+            // of 2: 0.545 ms, of 8: 0.528 ms on the 128-element workload)
+            for (; kf + 7.0f <= kend; kf += 8.0f) {
                 float part = point(kf, 0.0f);
-                part = point(kf + 1.0f, part);
-                part = point(kf + 2.0f, part);
-                kahan(point(kf + 3.0f, part));
+#pragma unroll
+                for (int q = 1; q < 7; ++q) part = point(kf + (float)q, part);
+                kahan(point(kf + 7.0f, part));
             }
             float part = 0.0f;
             for (; kf <= kend; kf += 1.0f) part = point(kf, part);
