@@ -200,7 +200,7 @@ def run_reference(args, rank, world):
 # the capture (see profiles/).  The adjoint stages' traffic follows
 # the CMPE mask of the captured iteration.
 NCU_TRAFFIC = {"das_forward": 574.82e6 + 90.04e6, "das_adjoint": 311.99e6 + 25.68e6,
-               "ray_adjoint": 33.58e6 + 0.0, "delays": 15.91e6 + 25.44e6}
+               "ray_adjoint": 33.58e6 + 0.0, "delays": 15.96e6 + 25.35e6}
 
 # algorithmic FP32 lane-operations per unit, from the arithmetic of the method.
 # Ray point: position (2) + cell and fraction (4) + two Keys weight sets (2 x 10) + 16
